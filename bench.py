@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the per-time-step test-particle update (stream + reflect + bin +
+2->2 collide) on one GB300, in particle updates per second.
+
+Workload (default): the 1D Riemann problem of the paper's Results section scaled
+up — box 10 x 1 x 1 fm, 2000 cells along x (dx = 0.005 fm), dt = 0.0025 fm/c,
+16M test particles (left half T = 400 MeV, right half 320 MeV, density ~ T^3),
+sigma = 10 mb, FP32 state with FP64 reductions.  One bench step = one time step
+of the whole state.  The state (384 MB) is larger than L2, so no flush is needed
+between steps.
+
+Printed: one JSON line (rank 0).  Under torchrun each rank advances its own
+independent replica (seed + rank); the value is the sum over ranks divided by
+the slowest rank's time.
+
+--impl reference times the CPU oracle (the plain FP64/FP32 C definition of the
+same step) on the host cores, on a bounded sample of the workload: a strip of
+cells of the same box with the same cell occupancies, time step and N_test.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuba", choices=["cuba", "reference"])
+    ap.add_argument("--n", type=int, default=16_000_000)
+    ap.add_argument("--cells", type=int, default=2000)
+    ap.add_argument("--dt", type=float, default=0.0025)
+    ap.add_argument("--sigma-mb", type=float, default=10.0)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-cells", type=int, default=16)
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1208_0961_gb300 import workloads as W
+    cfg = W.riemann_1d(args.n, args.cells, args.dt, args.sigma_mb)
+    cfg["name"] = "riemann-1d-%dM-%dcells-%gmb" % (round(args.n / 1e6), args.cells, args.sigma_mb)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def radix_passes(ncells):
+    bits = 0
+    while bits < 32 and (ncells - 1) >> bits:
+        bits += 1
+    return (bits + 7) // 8
+
+
+def launches_per_step(ncells):
+    # stream/key, per radix pass (histogram, 3 scan kernels, scatter), gather,
+    # cell prep + 3 scan kernels, pair tile, resolve, step counter
+    p = radix_passes(ncells)
+    return 1 + 5 * p + (1 if p else 2) + 4 + 1 + 1 + 1
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_sample(args, cfg, steps):
+    """Time the oracle on a strip of cells with the workload's occupancy.
+
+    The strip keeps dx, dt, sigma, N_test and the per-cell particle numbers of
+    the left and right halves: m cells, half of them at the left occupancy and
+    half at the right one, so per-update cost matches the full workload's mix.
+    """
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1208_0961_gb300 import workloads as W
+    m = max(2, args.cpu_sample_cells - args.cpu_sample_cells % 2)
+    dx = cfg["L"][0] / cfg["n_cells"][0]
+    counts = W.region_split(cfg["n"], cfg["regions"])
+    per_l = counts[0] / (cfg["n_cells"][0] / 2)
+    per_r = counts[1] / (cfg["n_cells"][0] / 2)
+    Ls = (m * dx, cfg["L"][1], cfg["L"][2])
+    n_l = int(round(per_l * m / 2))
+    n_r = int(round(per_r * m / 2))
+    rng = np.random.default_rng(args.seed)
+    regs = [((0.0, 0.0, 0.0), (Ls[0] / 2, Ls[1], Ls[2]), cfg["T_left"]),
+            ((Ls[0] / 2, 0.0, 0.0), Ls, cfg["T_right"])]
+    st = np.concatenate([W.thermal_state(n_l, regs[:1], seed=args.seed),
+                         W.thermal_state(n_r, regs[1:], seed=args.seed + 1)], axis=1)
+    if args.precision == "fp32":
+        st = st.astype(np.float32).astype(np.float64)
+    op = O.make_params(L=Ls, n=(m, 1, 1), dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"], n_test=cfg["n_test"],
+                       fp32=args.precision == "fp32", seed=args.seed)
+    st, _, _, _ = O.sort(op, st)
+    n = st.shape[1]
+    t0 = time.perf_counter()
+    for k in range(steps):
+        st, _ = O.step(op, k, st, trace=False)
+    dt = time.perf_counter() - t0
+    sample = ("%d-cell strip of the same box (%d + %d particles at the workload's left/right cell "
+              "occupancy, same dx, dt, sigma, N_test), %d oracle steps" % (m, n_l, n_r, steps))
+    return n * steps / dt, O.threads(), sample, dt
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = workload(args)
+    from oracle import oracle as O
+    O.lib()
+    # one bounded sample per step: the bench's step count, each a 1-step strip run
+    rate_steps = max(1, args.steps)
+    times = []
+    n_upd = 0
+    for _ in range(args.warmup and 1):
+        cpu_sample(args, cfg, 1)
+    for _ in range(rate_steps):
+        r, cores, sample, dt = cpu_sample(args, cfg, 1)
+        times.append(dt)
+        n_upd += r * dt
+    tot = sum(times)
+    value = n_upd / tot
+    line = {
+        "impl": "reference", "metric": "particle-updates/s (stream+bin+collide)", "value": value,
+        "unit": "particle-updates/s", "n_gpus": world, "steps": rate_steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tot / rate_steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_particles": args.n, "n_cells": args.cells, "dt": args.dt,
+                   "sigma_mb": args.sigma_mb, "precision": args.precision},
+        "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup(args)
+    from paper_1208_0961_gb300 import cuba
+    from paper_1208_0961_gb300 import workloads as W
+    cuba.load()
+    cfg = workload(args)
+    prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
+    p = cuba.make_params(L=cfg["L"], n_cells=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
+                         n_test=cfg["n_test"], precision=prec, seed=args.seed + rank)
+    sim = cuba.Sim(p, args.n)
+    stream = torch.cuda.Stream()
+    sim.init_riemann(args.n, cfg["T_left"], cfg["T_right"], stream)
+    torch.cuda.synchronize()
+    cuba.cuba_step(sim.h, args.warmup, stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cuba.cuba_step(sim.h, args.steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, world)
+    value = args.n * args.steps * world / (ms_max / 1000.0)
+
+    # per-phase device times, kernel by kernel with events on the same stream
+    phase = cuba.cuba_step_profiled(sim.h, args.profile_steps, stream)
+    phase_names = ["stream_key", "sort_bin", "cell_prep", "pair_tile", "resolve", "advance"]
+    stats = sim.stats()
+    pk, pk_kind = peaks()
+    nsteps_total = args.warmup + args.steps + args.profile_steps
+    pairs_per_step = stats["pair_tests"] / max(1, stats["steps"])
+    pair_ms = phase[3] / max(1, args.profile_steps)
+    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    # pair tile: integer-issue bound (Philox block per 16 pairs + byte test)
+    ops_per_pair = 3.0
+    peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    achieved_tops = pairs_per_step * ops_per_pair / (pair_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32 lane-ops)",
+                "frac": achieved_tops / peak_tops, "traffic": None,
+                "kernel": "k_pair_tile", "pair_tests_per_s": pairs_per_step / (pair_ms / 1000.0),
+                "ops_per_pair": ops_per_pair, "peak_basis": "%d SMs x 128 lanes x %.0f MHz (sampled median)" % (n_sm, sm_mhz)}
+    # stream/bin phases against HBM: 56 algorithmic bytes per update (FP32)
+    bpu = 56.0 if prec == cuba.CUBA_FP32 else 104.0
+    sb_ms = (phase[0] + phase[1]) / max(1, args.profile_steps)
+    hbm = {"phases": "stream_key+sort_bin", "achieved_gbs": args.n * bpu / (sb_ms / 1000.0) / 1e9,
+           "peak_gbs": pk.get("hbm_gbs"), "bytes_per_update": bpu}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm["peak_gbs"] if hbm["peak_gbs"] else None
+
+    # end to end through the C ABI with host buffers: H2D state, one step,
+    # D2H observables, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty((6, args.n), dtype=torch.float32 if prec == cuba.CUBA_FP32 else torch.float64,
+                           pin_memory=True)
+        cuba.cuba_get_state(sim.h, host.data_ptr(), stream)
+        nc = args.cells
+        T00 = torch.empty(nc, dtype=torch.float64, pin_memory=True)
+        T0x = torch.empty(nc, dtype=torch.float64, pin_memory=True)
+        cnt = torch.empty(nc, dtype=torch.int32, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            cuba.cuba_set_state(sim.h, host.data_ptr(), args.n, stream)
+            cuba.cuba_step(sim.h, 1, stream)
+            cuba.cuba_observables(sim.h, T00.data_ptr(), T0x.data_ptr(), cnt.data_ptr(), stream)
+        t1 = time.perf_counter()
+        e2e_s = max_over_ranks(t1 - t0, world)
+        e2e = {"value": args.n * args.e2e_steps * world / e2e_s, "unit": "particle-updates/s",
+               "h2d_bytes_per_step": host.numel() * host.element_size(),
+               "d2h_bytes_per_step": nc * (8 + 8 + 4), "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, cores, sample, dt = cpu_sample(args, cfg, args.cpu_sample_steps)
+        cpu = {"value": r, "unit": "particle-updates/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": "particle-updates/s (stream+bin+collide)", "value": value, "unit": "particle-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "n_particles": args.n, "n_cells": args.cells, "dt": args.dt,
+                       "sigma_mb": args.sigma_mb, "precision": args.precision, "n_test": cfg["n_test"],
+                       "l2": "state %.0f MB > L2, no flush" % (args.n * 24 / 1e6 * (2 if prec else 1)),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": clk,
+            "gpu_launches": launches_per_step(args.cells) * args.steps,
+            "roofline": roofline,
+            "hbm_phases": hbm,
+            "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in zip(phase_names, phase)},
+            "pair_tests_per_step": pairs_per_step,
+            "accepted_per_step": stats["accepted"] / max(1, stats["steps"]),
+            "executed_per_step": stats["executed"] / max(1, stats["steps"]),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "peaks": pk_kind,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * cuba.h — C ABI of the GB300 test-particle transport library.
+ *
+ * One time step of the test-particle solution of the relativistic Boltzmann
+ * equation for massless particles (arXiv:1208.0961, "CuBA - a CUDA
+ * implementation of BAMPS"):
+ *   A1 free streaming x -> x + (p_x / E) dt                 (Sec. 2, Eq. 2)
+ *   A2 elastic reflection at the six box walls               (Sec. 2)
+ *   A3 cell key of the new position                          (Sec. 2, PIC cells)
+ *   A4 stable counting sort of the particles by cell         (Sec. 2, PIC cells)
+ *   A5 every pair i < j of a cell is accepted iff u_ij < P22,
+ *      P22 = v_rel sigma / N_test dt / V_cell,
+ *      v_rel = s / (2 E_i E_j)                               (Sec. 2, Eq. 3)
+ *   A6 conflicts: accepted pairs of a cell are executed greedily in
+ *      lexicographic (i, j) order; a particle collides at most once per step
+ *      (the paper is silent; this is the library's reading)
+ *   A7 executed pairs are boosted to their centre-of-mass frame, given an
+ *      isotropic direction and boosted back                  (Sec. 2)
+ *   A8 per-cell T^00, T^0x, counts and global totals in FP64 (Sec. 5, Figs. 2-3)
+ *
+ * Units: fm, fm/c (c = 1), GeV; cross sections in fm^2 (1 mb = 0.1 fm^2).
+ *
+ * Random numbers are Philox4x32-10 keyed by the simulation seed with counters
+ * (step, cell, i, j): a step is a pure function of the state, the seed and the
+ * step index, independent of launch shape, batch composition and GPU.
+ *
+ * Conventions for every entry point:
+ *  - Return value 0 on success or a negative CUBA_ERR_* code; the message of
+ *    the last failure on the calling thread is cuba_last_error().
+ *  - Pointers named "device" must be CUDA device (or managed) memory; pointers
+ *    named "host or device" may be either (the copy direction is inferred by
+ *    unified addressing); "host" means ordinary or pinned host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls marked "async" only enqueue work; errors raised by the
+ *    kernels themselves (list overflow) surface in the next synchronous call.
+ *  - The library owns all simulation state; callers own every buffer they
+ *    pass in.  Objects are not thread-safe: one thread at a time per object.
+ *  - The state layout is SoA, six arrays of n elements in this order:
+ *    x, y, z, px, py, pz; element type double (CUBA_FP64) or float
+ *    (CUBA_FP32), particles sorted by cell (stable within a cell).
+ */
+#ifndef CUBA_H
+#define CUBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CUBA_OK 0
+#define CUBA_ERR_INVALID (-1)  /* bad argument or parameter */
+#define CUBA_ERR_OOM (-2)      /* device or host allocation failed */
+#define CUBA_ERR_CUDA (-3)     /* a CUDA runtime call failed */
+#define CUBA_ERR_OVERFLOW (-4) /* accepted-pair list of a step overflowed; that
+                                  step's collisions are incomplete */
+#define CUBA_ERR_P22 (-5)      /* parameters give P22 > 1 (2 C > 1) */
+#define CUBA_ERR_CAPACITY (-6) /* more particles or cells than reserved */
+
+#define CUBA_FP32 0
+#define CUBA_FP64 1
+
+/* Parameters of one simulation (Sec. 2 and Sec. 5). */
+typedef struct cuba_params {
+    double L[3];          /* box edge lengths, fm; walls at 0 and L[a] */
+    int32_t n_cells[3];   /* cells per axis; V_cell = (L0/n0)(L1/n1)(L2/n2) */
+    double dt;            /* time step, fm/c; must be below every cell edge
+                             (Sec. 5: dt < dx) so a particle crosses at most
+                             one cell face per axis per step */
+    double sigma_fm2;     /* total isotropic cross section, fm^2 (>= 0) */
+    double n_test;        /* test particles per physical particle (> 0);
+                             P22 is divided by it (Sec. 2) */
+    int32_t precision;    /* CUBA_FP32 or CUBA_FP64 state and arithmetic */
+    uint64_t seed;        /* Philox key of this simulation */
+    double gamma_fp64;    /* CUBA_FP32 only: CM boosts with Lorentz factor
+                             above this run in FP64 (<= 0: library default) */
+} cuba_params;
+
+/* Thermal region for cuba_init_thermal: an axis-aligned box at temperature T. */
+typedef struct cuba_region {
+    double lo[3], hi[3]; /* fm, inside [0, L] */
+    double T;            /* GeV (> 0) */
+} cuba_region;
+
+/* Counters accumulated over all steps of a simulation. */
+typedef struct cuba_counters {
+    int64_t steps;        /* steps taken */
+    int64_t pair_tests;   /* pairs i < j tested (A5) */
+    int64_t accepted;     /* pairs with u < P22 (A5) */
+    int64_t executed;     /* pairs that collided (A6) */
+    int64_t reflections;  /* wall reflections, one per axis crossing (A2) */
+    int64_t fp64_boosts;  /* CUBA_FP32: collisions done in FP64 (A7) */
+    int64_t overflow;     /* accepted pairs dropped for lack of list space */
+    int64_t reserved;
+} cuba_counters;
+
+typedef struct cuba_sim cuba_sim;
+
+/*
+ * Create a simulation with room for up to max_particles particles.  Checks
+ * the parameters: L > 0, n_cells >= 1, 0 < dt < every cell edge, sigma >= 0,
+ * n_test > 0, precision valid, 2 C <= 1 with C = sigma dt / (n_test V_cell)
+ * (P22 <= 2 C since v_rel <= 2).  Allocates the device state on the current
+ * device.  On success *out owns it until cuba_destroy.
+ */
+int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out);
+
+/* Free everything a simulation owns (NULL is ignored). */
+void cuba_destroy(cuba_sim* sim);
+
+/*
+ * Sample n massless particles from thermal Boltzmann distributions: region r
+ * receives a share of n proportional to T_r^3 V_r (largest remainder); in
+ * it, positions are uniform and E ~ E^2 exp(-E/T) with isotropic directions.
+ * Particle g (generation order) draws Philox blocks (0xFFFFFFFF, g_lo, g_hi, 0)
+ * and (…, 1).  The state is then sorted by cell and the step counter reset
+ * to 0.  Synchronous.
+ */
+int cuba_init_thermal(cuba_sim* sim, int64_t n, const cuba_region* regions, int n_regions,
+                      void* stream);
+
+/* The 1D Riemann initial state of Sec. 5: left half of the box (x < L0/2) at
+   T_left, right half at T_right.  Same as cuba_init_thermal with two regions. */
+int cuba_init_riemann(cuba_sim* sim, int64_t n, double T_left, double T_right, void* stream);
+
+/*
+ * Load a state of n particles (SoA x, y, z, px, py, pz of the simulation's
+ * element type, host or device memory, any order); the library sorts it by
+ * cell, stably.  Positions must lie in [0, L].  Synchronous.
+ */
+int cuba_set_state(cuba_sim* sim, const void* soa, int64_t n, void* stream);
+
+/* Copy the current (cell-sorted) state, 6 n elements, to host or device
+   memory.  Synchronous. */
+int cuba_get_state(cuba_sim* sim, void* soa_out, void* stream);
+
+/* Number of particles and of cells. */
+int cuba_sizes(const cuba_sim* sim, int64_t* n_particles, int64_t* n_cells);
+
+/* Step counter: index of the next step (the first counter word of its random
+   numbers).  set_step lets a resumed run continue its random sequence. */
+int cuba_get_step(const cuba_sim* sim, uint32_t* step);
+int cuba_set_step(cuba_sim* sim, uint32_t step);
+
+/*
+ * Advance n_steps time steps A1-A7.  Async on `stream`: the work is replayed
+ * from a captured CUDA graph of one step.
+ */
+int cuba_step(cuba_sim* sim, int n_steps, void* stream);
+
+/*
+ * A8 observables of the current state, per cell c (key ix + nx (iy + ny iz)):
+ * T00[c] = sum E / (n_test V_cell), T0x[c] = sum p_x / (n_test V_cell), both
+ * summed in FP64, counts[c] = particles.  Caller-owned host or device buffers
+ * of n_cells elements; any may be NULL.  Synchronous; reports kernel errors.
+ */
+int cuba_observables(cuba_sim* sim, double* T00, double* T0x, int32_t* counts, void* stream);
+
+/* FP64 totals {E, Px, Py, Pz} (host array) and the particle count.
+   Synchronous; reports kernel errors. */
+int cuba_totals(cuba_sim* sim, double out[4], int64_t* n_particles, void* stream);
+
+/* Counters since creation (host struct).  Synchronous; reports kernel errors. */
+int cuba_stats(cuba_sim* sim, cuba_counters* out);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cuba_last_error(void);
+
+/*
+ * Parity support.  With tracing on, each step keeps: the cell key of every
+ * particle after streaming (pre-sort order), the sort permutation (sorted
+ * position -> pre-sort index), cell_start (n_cells + 1) and the accepted
+ * pairs with their executed flags.  cuba_trace_get copies them to host
+ * buffers (any may be NULL): pairs as (cell, i, j) triples in lexicographic
+ * order, executed[k] = 1 if pair k collided.  At most `cap` pairs are
+ * written; *n_pairs receives the total.  Synchronous.
+ */
+int cuba_trace_enable(cuba_sim* sim, int on);
+int cuba_trace_get(cuba_sim* sim, uint32_t* keys, uint32_t* perm, uint32_t* cell_start,
+                   uint32_t* pairs, uint8_t* executed, int64_t cap, int64_t* n_pairs);
+
+/*
+ * Advance n_steps steps like cuba_step, but launched kernel by kernel (no
+ * graph) with CUDA events between the phases; phase_ms (host, 6 doubles)
+ * receives the summed device time of each phase over the steps:
+ * [0] stream/reflect/key, [1] sort (radix passes + gather + cell_start),
+ * [2] per-cell preparation, [3] pair tile, [4] conflicts + kinematics,
+ * [5] step counter.  Synchronous.  For measurement.
+ */
+int cuba_step_profiled(cuba_sim* sim, int n_steps, double* phase_ms, void* stream);
+
+/*
+ * Philox4x32-10 of the library's device implementation for n counters
+ * (4 words each) under one key, into out (4 words each).  ctr and out are
+ * device pointers.  Async.  For verifying the generator.
+ */
+int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUBA_H */

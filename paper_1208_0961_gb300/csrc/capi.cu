@@ -1,0 +1,646 @@
+// C ABI of the library (include/cuba.h): parameter checks, device memory of a
+// simulation, the step sequence and its CUDA-graph replay, observables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cuba.h"
+#include "engine.cuh"
+
+using namespace cuba;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(CUBA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call, what)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr double kDefaultGammaFp64 = 8.0;
+
+// Validate parameters (Sec. 2, Sec. 5) and build the device descriptor.
+int make_desc(const cuba_params* p, SimDesc* S)
+{
+    if (!p) return fail(CUBA_ERR_INVALID, "params is NULL");
+    std::memset(S, 0, sizeof(*S));
+    uint64_t nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(p->L[a] > 0.0) || !std::isfinite(p->L[a])) return fail(CUBA_ERR_INVALID, "L[%d] must be > 0", a);
+        if (p->n_cells[a] < 1) return fail(CUBA_ERR_INVALID, "n_cells[%d] must be >= 1", a);
+        nc *= (uint64_t)p->n_cells[a];
+        S->L[a] = p->L[a];
+        S->n[a] = p->n_cells[a];
+        S->dx[a] = p->L[a] / (double)p->n_cells[a];
+        S->Lf[a] = (float)p->L[a];
+        S->dxf[a] = (float)S->dx[a];
+        if (!(p->dt < S->dx[a]))
+            return fail(CUBA_ERR_INVALID, "dt = %g must be below the cell edge %g on axis %d", p->dt, S->dx[a], a);
+    }
+    if (nc > (1ull << 30)) return fail(CUBA_ERR_INVALID, "too many cells (%llu)", (unsigned long long)nc);
+    if (!(p->dt > 0.0)) return fail(CUBA_ERR_INVALID, "dt must be > 0");
+    if (!(p->sigma_fm2 >= 0.0) || !std::isfinite(p->sigma_fm2)) return fail(CUBA_ERR_INVALID, "sigma must be >= 0");
+    if (!(p->n_test > 0.0) || !std::isfinite(p->n_test)) return fail(CUBA_ERR_INVALID, "n_test must be > 0");
+    if (p->precision != CUBA_FP32 && p->precision != CUBA_FP64) return fail(CUBA_ERR_INVALID, "bad precision");
+    S->ncells = (uint32_t)nc;
+    S->dt = p->dt;
+    S->dtf = (float)p->dt;
+    const double V = (S->dx[0] * S->dx[1]) * S->dx[2];
+    S->C = (p->sigma_fm2 * p->dt) / (p->n_test * V);
+    S->Cf = (float)S->C;
+    S->norm = p->n_test * V;
+    if (2.0 * S->C > 1.0) return fail(CUBA_ERR_P22, "P22 can reach 2C = %g > 1", 2.0 * S->C);
+    S->key0 = (uint32_t)p->seed;
+    S->key1 = (uint32_t)(p->seed >> 32);
+    // A top byte above thr8 proves u >= (thr8 + 1) / 256 > 2.0001 C >= P22.
+    const double pb = 2.0001 * S->C;
+    S->thr8 = (pb >= 0.5) ? 256u : (uint32_t)std::floor(pb * 256.0);
+    S->gamma_fp64 = (float)(p->gamma_fp64 > 0.0 ? p->gamma_fp64 : kDefaultGammaFp64);
+    S->step = 0;
+    return CUBA_OK;
+}
+
+template <typename P>
+int dalloc(P** ptr, size_t bytes, const char* what)
+{
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CUBA_ERR_OOM, "cudaMalloc %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    }
+    return CUBA_OK;
+}
+
+void arena_free(Arena& A)
+{
+    void* ptrs[] = {A.st[0], A.st[1], A.key[0], A.key[1], A.idx[0], A.idx[1], A.cell_start, A.cell_work,
+                    A.acc_count, A.acc, A.radix_hist, A.scan_tmp, A.counters, A.active, A.used_bits, A.stats,
+                    A.d_sims, A.trace_keys};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    A = Arena();
+}
+
+size_t scan_tmp_needed(uint32_t pcap, uint32_t ccap)
+{
+    const size_t tiles = (pcap + kSortTile - 1) / kSortTile + 1;
+    const size_t n1 = (kRadixBins * tiles + kScanTile - 1) / kScanTile;
+    const size_t n2 = ((size_t)ccap + 1 + kScanTile - 1) / kScanTile;
+    size_t need = std::max(n1 * sizeof(uint32_t), n2 * sizeof(uint2));
+    return std::max<size_t>(need, 256 * 4 * sizeof(double)) + 256;
+}
+
+int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simcap)
+{
+    A.precision = precision;
+    A.pcap = pcap;
+    A.ccap = ccap;
+    A.simcap = simcap;
+    const size_t es = precision == CUBA_FP64 ? sizeof(double) : sizeof(float);
+    const size_t pc = std::max<uint32_t>(pcap, 1);
+    int rc = CUBA_OK;
+    rc |= dalloc(&A.st[0], 6 * pc * es, "state");
+    if (!rc) rc = dalloc(&A.st[1], 6 * pc * es, "state");
+    if (!rc) rc = dalloc(&A.key[0], pc * 4, "keys");
+    if (!rc) rc = dalloc(&A.key[1], pc * 4, "keys");
+    if (!rc) rc = dalloc(&A.idx[0], pc * 4, "perm");
+    if (!rc) rc = dalloc(&A.idx[1], pc * 4, "perm");
+    if (!rc) rc = dalloc(&A.cell_start, ((size_t)ccap + 1) * 4, "cell_start");
+    if (!rc) rc = dalloc(&A.cell_work, ((size_t)ccap + 1) * sizeof(uint2), "cell_work");
+    if (!rc) rc = dalloc(&A.acc_count, (size_t)ccap * 4, "acc_count");
+    if (!rc) rc = dalloc(&A.active, (size_t)ccap * 4, "active");
+    A.radix_hist_cap = (uint32_t)(kRadixBins * ((pc + kSortTile - 1) / kSortTile + 1));
+    if (!rc) rc = dalloc(&A.radix_hist, (size_t)A.radix_hist_cap * 4, "radix_hist");
+    A.scan_tmp_bytes = scan_tmp_needed(pcap, ccap);
+    if (!rc) rc = dalloc(&A.scan_tmp, A.scan_tmp_bytes, "scan_tmp");
+    if (!rc) rc = dalloc(&A.counters, 16 * 4, "counters");
+    if (!rc) rc = dalloc(&A.used_bits, (pc / 32 + 2) * 4, "used_bits");
+    if (!rc) rc = dalloc(&A.stats, (size_t)simcap * kStatCount * 8, "stats");
+    if (!rc) rc = dalloc(&A.d_sims, (size_t)simcap * sizeof(SimDesc), "sims");
+    if (rc) {
+        arena_free(A);
+        return rc;
+    }
+    cudaMemset(A.counters, 0, 16 * 4);
+    cudaMemset(A.used_bits, 0, (pc / 32 + 2) * 4);
+    cudaMemset(A.stats, 0, (size_t)simcap * kStatCount * 8);
+    cudaMemset(A.cell_start, 0, ((size_t)ccap + 1) * 4);
+    return CUBA_OK;
+}
+
+}  // namespace
+
+struct cuba_sim {
+    cuba_params params;
+    SimDesc desc;      // host copy; the step counter lives on the device
+    Arena A;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    uint32_t graph_np = 0;            // what the graphs were captured for
+    const void* graph_acc = nullptr;
+    int graph_trace = 0;
+    double* d_obs = nullptr;  // scratch for observables: 2 n_cells doubles + n_cells ints
+    double* d_tot = nullptr;  // 4 doubles
+};
+
+namespace {
+
+void drop_graphs(cuba_sim* s)
+{
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+}
+
+// Enqueue one step A1-A7 (both for direct launch and for capture).
+int enqueue_step(Arena& A, cudaStream_t st)
+{
+    if (launch_stream_key(A, st)) return fail(CUBA_ERR_CUDA, "stream/key launch failed");
+    if (launch_sort_and_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
+    if (launch_cell_prep(A, st)) return fail(CUBA_ERR_CUDA, "cell preparation launch failed");
+    if (launch_pair_tile(A, st)) return fail(CUBA_ERR_CUDA, "pair tile launch failed");
+    if (launch_resolve(A, st)) return fail(CUBA_ERR_CUDA, "resolve launch failed");
+    if (launch_advance(A, st)) return fail(CUBA_ERR_CUDA, "advance launch failed");
+    return CUBA_OK;
+}
+
+int capture_graph(cuba_sim* s, int which)
+{
+    Arena& A = s->A;
+    const int saved_cur = A.cur;
+    A.cur = which;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int rc = enqueue_step(A, s->capture_stream);
+    cudaError_t e = cudaStreamEndCapture(s->capture_stream, &g);
+    A.cur = saved_cur;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&s->graph[which], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+    s->graph_np = A.np;
+    s->graph_acc = A.acc;
+    s->graph_trace = A.trace;
+    return CUBA_OK;
+}
+
+// Sort the freshly loaded state (keys of the unsorted positions) and size the
+// accepted-pair list from the resulting occupancy.
+int settle_state(cuba_sim* s, cudaStream_t st)
+{
+    Arena& A = s->A;
+    if (launch_keys_only(A, st)) return fail(CUBA_ERR_CUDA, "key launch failed");
+    if (launch_sort_and_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
+    if (launch_cell_prep(A, st)) return fail(CUBA_ERR_CUDA, "cell preparation failed");
+    uint2 tot;
+    CUDA_TRY(cudaMemcpyAsync(&tot, A.cell_work + A.ncells, sizeof(uint2), cudaMemcpyDeviceToHost, st), "read list size");
+    CUDA_TRY(cudaStreamSynchronize(st), "sync");
+    // Room for four times the present need plus 2^20 entries: the occupancy
+    // of cells changes as the system evolves (a shock compresses it).
+    const uint64_t want = 4ull * tot.y + (1ull << 20);
+    if (want > A.acc_capacity) {
+        if (A.acc) cudaFree(A.acc);
+        A.acc = nullptr;
+        A.acc_capacity = 0;
+        int rc = dalloc(&A.acc, want * sizeof(unsigned long long), "accepted list");
+        if (rc) return rc;
+        A.acc_capacity = want;
+    }
+    // captured graphs hold the particle count, the list buffer and the trace
+    // switch; keep them while those are unchanged
+    if (s->graph_np != A.np || s->graph_acc != A.acc || s->graph_trace != A.trace) drop_graphs(s);
+    return CUBA_OK;
+}
+
+int upload_desc(cuba_sim* s, cudaStream_t st)
+{
+    CUDA_TRY(cudaMemcpyAsync(s->A.d_sims, &s->desc, sizeof(SimDesc), cudaMemcpyHostToDevice, st), "upload descriptor");
+    return CUBA_OK;
+}
+
+int check_kernel_errors(cuba_sim* s)
+{
+    uint32_t err = 0;
+    CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
+    CUDA_TRY(cudaMemcpy(&err, s->A.counters + 1, 4, cudaMemcpyDeviceToHost), "read error flags");
+    if (err) {
+        cudaMemset(s->A.counters + 1, 0, 4);
+        if (err & kErrCapacity)
+            return fail(CUBA_ERR_OVERFLOW, "accepted-pair lists of a step exceeded the allocated list; "
+                                           "that step skipped its collisions");
+        return fail(CUBA_ERR_OVERFLOW, "a cell's accepted-pair list overflowed; some accepted pairs were dropped");
+    }
+    return CUBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cuba_last_error(void) { return g_last_error.c_str(); }
+
+int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out)
+{
+    if (!out) return fail(CUBA_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    SimDesc S;
+    int rc = make_desc(params, &S);
+    if (rc) return rc;
+    if (max_particles < 0 || max_particles > (int64_t)0x7FFFFFF0) return fail(CUBA_ERR_INVALID, "bad max_particles");
+    if (kernels_init()) return fail(CUBA_ERR_CUDA, "kernel attribute setup failed: %s",
+                                    cudaGetErrorString(cudaGetLastError()));
+    cuba_sim* s = new cuba_sim();
+    s->params = *params;
+    s->desc = S;
+    rc = arena_alloc(s->A, params->precision, (uint32_t)max_particles, S.ncells, 1);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    s->A.nsims = 1;
+    s->A.ncells = S.ncells;
+    s->A.np = 0;
+    if (cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        dalloc(&s->d_obs, (size_t)S.ncells * 20 + 64, "observables") ||
+        dalloc(&s->d_tot, 64, "totals")) {
+        cuba_destroy(s);
+        return fail(CUBA_ERR_CUDA, "stream or scratch allocation failed");
+    }
+    rc = upload_desc(s, 0);
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "create");
+    }
+    if (rc) {
+        cuba_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return CUBA_OK;
+}
+
+void cuba_destroy(cuba_sim* s)
+{
+    if (!s) return;
+    cudaDeviceSynchronize();
+    drop_graphs(s);
+    if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
+    if (s->d_obs) cudaFree(s->d_obs);
+    if (s->d_tot) cudaFree(s->d_tot);
+    arena_free(s->A);
+    delete s;
+}
+
+// Largest-remainder split of n over weights T^3 V (ties to the lower index).
+static int split_counts(int64_t n, const cuba_region* R, int nreg, std::vector<int64_t>& counts)
+{
+    std::vector<double> w(nreg), frac(nreg);
+    double wsum = 0.0;
+    for (int r = 0; r < nreg; ++r) {
+        double v = 1.0;
+        for (int a = 0; a < 3; ++a) v *= (R[r].hi[a] - R[r].lo[a]);
+        if (!(v > 0.0) || !(R[r].T > 0.0)) return fail(CUBA_ERR_INVALID, "region %d: empty box or T <= 0", r);
+        w[r] = R[r].T * R[r].T * R[r].T * v;
+        wsum += w[r];
+    }
+    counts.assign(nreg, 0);
+    int64_t assigned = 0;
+    for (int r = 0; r < nreg; ++r) {
+        const double q = (double)n * w[r] / wsum;
+        counts[r] = (int64_t)std::floor(q);
+        frac[r] = q - (double)counts[r];
+        assigned += counts[r];
+    }
+    while (assigned < n) {
+        int best = 0;
+        for (int r = 1; r < nreg; ++r)
+            if (frac[r] > frac[best]) best = r;
+        counts[best] += 1;
+        frac[best] = -1.0;
+        ++assigned;
+    }
+    return CUBA_OK;
+}
+
+int cuba_init_thermal(cuba_sim* s, int64_t n, const cuba_region* regions, int n_regions, void* stream)
+{
+    if (!s || !regions || n_regions < 1 || n_regions > 1024) return fail(CUBA_ERR_INVALID, "bad arguments");
+    if (n < 0 || n > (int64_t)s->A.pcap) return fail(CUBA_ERR_CAPACITY, "n = %lld exceeds max_particles = %u",
+                                                    (long long)n, s->A.pcap);
+    for (int r = 0; r < n_regions; ++r)
+        for (int a = 0; a < 3; ++a)
+            if (!(regions[r].lo[a] >= 0.0) || !(regions[r].hi[a] <= s->params.L[a]) || !(regions[r].lo[a] < regions[r].hi[a]))
+                return fail(CUBA_ERR_INVALID, "region %d is not a box inside [0, L]", r);
+    std::vector<int64_t> counts;
+    int rc = split_counts(n, regions, n_regions, counts);
+    if (rc) return rc;
+    std::vector<double> hreg(7 * n_regions);
+    std::vector<uint64_t> first(n_regions);
+    uint64_t acc = 0;
+    for (int r = 0; r < n_regions; ++r) {
+        for (int a = 0; a < 3; ++a) {
+            hreg[7 * r + a] = regions[r].lo[a];
+            hreg[7 * r + 3 + a] = regions[r].hi[a];
+        }
+        hreg[7 * r + 6] = regions[r].T;
+        first[r] = acc;
+        acc += (uint64_t)counts[r];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double* d_reg = nullptr;
+    uint64_t* d_first = nullptr;
+    if ((rc = dalloc(&d_reg, hreg.size() * sizeof(double), "regions"))) return rc;
+    if ((rc = dalloc(&d_first, first.size() * sizeof(uint64_t), "regions"))) {
+        cudaFree(d_reg);
+        return rc;
+    }
+    cudaMemcpy(d_reg, hreg.data(), hreg.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_first, first.data(), first.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    cudaStreamSynchronize(st);
+    s->desc.np = (uint32_t)n;
+    s->desc.p_off = 0;
+    s->desc.cell_off = 0;
+    s->desc.step = 0;
+    s->A.np = (uint32_t)n;
+    rc = upload_desc(s, st);
+    if (!rc && launch_init_thermal(s->A, 0, s->desc, d_reg, n_regions, d_first, st))
+        rc = fail(CUBA_ERR_CUDA, "thermal sampling launch failed");
+    if (!rc) rc = settle_state(s, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(d_reg);
+    cudaFree(d_first);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "init_thermal");
+    return rc;
+}
+
+int cuba_init_riemann(cuba_sim* s, int64_t n, double T_left, double T_right, void* stream)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    cuba_region R[2];
+    const double* L = s->params.L;
+    for (int a = 0; a < 3; ++a) {
+        R[0].lo[a] = 0.0;
+        R[0].hi[a] = L[a];
+        R[1].lo[a] = 0.0;
+        R[1].hi[a] = L[a];
+    }
+    R[0].hi[0] = 0.5 * L[0];
+    R[1].lo[0] = 0.5 * L[0];
+    R[0].T = T_left;
+    R[1].T = T_right;
+    return cuba_init_thermal(s, n, R, 2, stream);
+}
+
+int cuba_set_state(cuba_sim* s, const void* soa, int64_t n, void* stream)
+{
+    if (!s || (!soa && n > 0)) return fail(CUBA_ERR_INVALID, "bad arguments");
+    if (n < 0 || n > (int64_t)s->A.pcap) return fail(CUBA_ERR_CAPACITY, "n = %lld exceeds max_particles", (long long)n);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = s->A.precision == CUBA_FP64 ? 8 : 4;
+    s->A.cur = 0;
+    for (int c = 0; c < 6; ++c)
+        CUDA_TRY(cudaMemcpyAsync((char*)s->A.st[0] + (size_t)c * s->A.pcap * es, (const char*)soa + (size_t)c * n * es,
+                                 (size_t)n * es, cudaMemcpyDefault, st),
+                 "copy state in");
+    s->desc.np = (uint32_t)n;
+    s->desc.p_off = 0;
+    s->desc.cell_off = 0;
+    // keep the step counter
+    uint32_t step = 0;
+    CUDA_TRY(cudaMemcpyAsync(&step, &s->A.d_sims[0].step, 4, cudaMemcpyDeviceToHost, st), "read step");
+    CUDA_TRY(cudaStreamSynchronize(st), "sync");
+    s->desc.step = step;
+    s->A.np = (uint32_t)n;
+    int rc = upload_desc(s, st);
+    if (!rc) rc = settle_state(s, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "set_state");
+    return rc;
+}
+
+int cuba_get_state(cuba_sim* s, void* out, void* stream)
+{
+    if (!s || (!out && s->A.np)) return fail(CUBA_ERR_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = s->A.precision == CUBA_FP64 ? 8 : 4;
+    const size_t n = s->A.np;
+    for (int c = 0; c < 6; ++c)
+        CUDA_TRY(cudaMemcpyAsync((char*)out + (size_t)c * n * es, (const char*)s->A.st[s->A.cur] + (size_t)c * s->A.pcap * es,
+                                 n * es, cudaMemcpyDefault, st),
+                 "copy state out");
+    CUDA_TRY(cudaStreamSynchronize(st), "sync");
+    return check_kernel_errors(s);
+}
+
+int cuba_sizes(const cuba_sim* s, int64_t* np, int64_t* nc)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    if (np) *np = s->A.np;
+    if (nc) *nc = s->A.ncells;
+    return CUBA_OK;
+}
+
+int cuba_get_step(const cuba_sim* s, uint32_t* step)
+{
+    if (!s || !step) return fail(CUBA_ERR_INVALID, "bad arguments");
+    CUDA_TRY(cudaMemcpy(step, &s->A.d_sims[0].step, 4, cudaMemcpyDeviceToHost), "read step");
+    return CUBA_OK;
+}
+
+int cuba_set_step(cuba_sim* s, uint32_t step)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    if (step == 0xFFFFFFFFu) return fail(CUBA_ERR_INVALID, "step 0xFFFFFFFF is reserved for sampling");
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    CUDA_TRY(cudaMemcpy(&s->A.d_sims[0].step, &step, 4, cudaMemcpyHostToDevice), "write step");
+    s->desc.step = step;
+    return CUBA_OK;
+}
+
+int cuba_step(cuba_sim* s, int n_steps, void* stream)
+{
+    if (!s || n_steps < 0) return fail(CUBA_ERR_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < n_steps; ++k) {
+        const int which = s->A.cur;
+        if (!s->graph[which]) {
+            int rc = capture_graph(s, which);
+            if (rc) return rc;
+        }
+        CUDA_TRY(cudaGraphLaunch(s->graph[which], st), "graph launch");
+        s->A.cur ^= 1;
+    }
+    return CUBA_OK;
+}
+
+int cuba_step_profiled(cuba_sim* s, int n_steps, double* phase_ms, void* stream)
+{
+    if (!s || n_steps < 0 || !phase_ms) return fail(CUBA_ERR_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[7];
+    for (int k = 0; k < 7; ++k) CUDA_TRY(cudaEventCreate(&ev[k]), "event");
+    for (int k = 0; k < 6; ++k) phase_ms[k] = 0.0;
+    Arena& A = s->A;
+    int rc = CUBA_OK;
+    for (int it = 0; it < n_steps && !rc; ++it) {
+        cudaEventRecord(ev[0], st);
+        if (launch_stream_key(A, st)) rc = fail(CUBA_ERR_CUDA, "stream/key launch failed");
+        cudaEventRecord(ev[1], st);
+        if (!rc && launch_sort_and_bin(A, st)) rc = fail(CUBA_ERR_CUDA, "sort launch failed");
+        cudaEventRecord(ev[2], st);
+        if (!rc && launch_cell_prep(A, st)) rc = fail(CUBA_ERR_CUDA, "cell preparation launch failed");
+        cudaEventRecord(ev[3], st);
+        if (!rc && launch_pair_tile(A, st)) rc = fail(CUBA_ERR_CUDA, "pair tile launch failed");
+        cudaEventRecord(ev[4], st);
+        if (!rc && launch_resolve(A, st)) rc = fail(CUBA_ERR_CUDA, "resolve launch failed");
+        cudaEventRecord(ev[5], st);
+        if (!rc && launch_advance(A, st)) rc = fail(CUBA_ERR_CUDA, "advance launch failed");
+        cudaEventRecord(ev[6], st);
+        cudaError_t e = cudaEventSynchronize(ev[6]);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "profiled step");
+        for (int k = 0; k < 6 && !rc; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            phase_ms[k] += ms;
+        }
+    }
+    for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
+    if (rc) return rc;
+    return check_kernel_errors(s);
+}
+
+int cuba_observables(cuba_sim* s, double* T00, double* T0x, int32_t* counts, void* stream)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nc = s->A.ncells;
+    double* dT00 = s->d_obs;
+    double* dT0x = s->d_obs + nc;
+    int32_t* dcnt = reinterpret_cast<int32_t*>(s->d_obs + 2 * nc);
+    if (launch_observables(s->A, 0, dT00, dT0x, dcnt, st)) return fail(CUBA_ERR_CUDA, "observables launch failed");
+    if (T00) CUDA_TRY(cudaMemcpyAsync(T00, dT00, nc * 8, cudaMemcpyDefault, st), "copy T00");
+    if (T0x) CUDA_TRY(cudaMemcpyAsync(T0x, dT0x, nc * 8, cudaMemcpyDefault, st), "copy T0x");
+    if (counts) CUDA_TRY(cudaMemcpyAsync(counts, dcnt, nc * 4, cudaMemcpyDefault, st), "copy counts");
+    CUDA_TRY(cudaStreamSynchronize(st), "sync");
+    return check_kernel_errors(s);
+}
+
+int cuba_totals(cuba_sim* s, double out[4], int64_t* n, void* stream)
+{
+    if (!s || !out) return fail(CUBA_ERR_INVALID, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (launch_totals(s->A, 0, s->d_tot, st)) return fail(CUBA_ERR_CUDA, "totals launch failed");
+    CUDA_TRY(cudaMemcpyAsync(out, s->d_tot, 4 * sizeof(double), cudaMemcpyDefault, st), "copy totals");
+    CUDA_TRY(cudaStreamSynchronize(st), "sync");
+    if (n) *n = s->A.np;
+    return check_kernel_errors(s);
+}
+
+int cuba_stats(cuba_sim* s, cuba_counters* out)
+{
+    if (!s || !out) return fail(CUBA_ERR_INVALID, "bad arguments");
+    unsigned long long h[kStatCount];
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    CUDA_TRY(cudaMemcpy(h, s->A.stats, sizeof(h), cudaMemcpyDeviceToHost), "read stats");
+    out->steps = (int64_t)h[kStatSteps];
+    out->pair_tests = (int64_t)h[kStatPairTests];
+    out->accepted = (int64_t)h[kStatAccepted];
+    out->executed = (int64_t)h[kStatExecuted];
+    out->reflections = (int64_t)h[kStatReflections];
+    out->fp64_boosts = (int64_t)h[kStatFp64Boosts];
+    out->overflow = (int64_t)h[kStatOverflow];
+    out->reserved = 0;
+    return check_kernel_errors(s);
+}
+
+int cuba_trace_enable(cuba_sim* s, int on)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    if (on && !s->A.trace_keys) {
+        int rc = dalloc(&s->A.trace_keys, (size_t)std::max<uint32_t>(s->A.pcap, 1) * 4, "trace");
+        if (rc) return rc;
+    }
+    s->A.trace = on ? 1 : 0;
+    drop_graphs(s);
+    return CUBA_OK;
+}
+
+int cuba_trace_get(cuba_sim* s, uint32_t* keys, uint32_t* perm, uint32_t* cell_start, uint32_t* pairs,
+                   uint8_t* executed, int64_t cap, int64_t* n_pairs)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    if (!s->A.trace) return fail(CUBA_ERR_INVALID, "tracing is off");
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    const Arena& A = s->A;
+    const size_t n = A.np, nc = A.ncells;
+    if (keys) CUDA_TRY(cudaMemcpy(keys, A.trace_keys, n * 4, cudaMemcpyDeviceToHost), "copy keys");
+    if (perm) CUDA_TRY(cudaMemcpy(perm, A.idx[A.sorted_buf], n * 4, cudaMemcpyDeviceToHost), "copy perm");
+    if (cell_start) CUDA_TRY(cudaMemcpy(cell_start, A.cell_start, (nc + 1) * 4, cudaMemcpyDeviceToHost), "copy cells");
+    std::vector<uint2> work(nc + 1);
+    std::vector<uint32_t> cnt(nc);
+    CUDA_TRY(cudaMemcpy(work.data(), A.cell_work, (nc + 1) * sizeof(uint2), cudaMemcpyDeviceToHost), "copy work");
+    CUDA_TRY(cudaMemcpy(cnt.data(), A.acc_count, nc * 4, cudaMemcpyDeviceToHost), "copy counts");
+    int64_t total = 0;
+    std::vector<unsigned long long> seg;
+    for (size_t c = 0; c < nc; ++c) {
+        uint32_t m = std::min(cnt[c], work[c + 1].y - work[c].y);
+        if (!m) continue;
+        seg.resize(m);
+        CUDA_TRY(cudaMemcpy(seg.data(), A.acc + work[c].y, m * 8, cudaMemcpyDeviceToHost), "copy pairs");
+        for (uint32_t k = 0; k < m; ++k) {
+            if (total < cap) {
+                if (pairs) {
+                    pairs[3 * total] = (uint32_t)c;
+                    pairs[3 * total + 1] = (uint32_t)(seg[k] >> 32) & 0x7FFFFFFFu;
+                    pairs[3 * total + 2] = (uint32_t)seg[k];
+                }
+                if (executed) executed[total] = (seg[k] >> 63) ? 1 : 0;
+            }
+            ++total;
+        }
+    }
+    if (n_pairs) *n_pairs = total;
+    return check_kernel_errors(s);
+}
+
+int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(CUBA_ERR_INVALID, "bad arguments");
+    if (launch_philox(ctr, n, key, out, (cudaStream_t)stream)) return fail(CUBA_ERR_CUDA, "philox launch failed");
+    return CUBA_OK;
+}
+
+}  // extern "C"

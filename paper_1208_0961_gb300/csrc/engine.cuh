@@ -1,0 +1,158 @@
+// Device-side data structures and kernel launchers of the test-particle step.
+//
+// Several independent simulations can share one arena: simulation s owns the
+// particles [p_off, p_off + np) and the global cells [cell_off, cell_off +
+// ncells).  Global cell keys are cell_off + local key, so one stable sort of
+// the whole arena by global key keeps every simulation inside its own range.
+// A single simulation is an arena with one entry.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "philox.cuh"
+
+namespace cuba {
+
+struct SimDesc {
+    double L[3];      // box edges, fm
+    double dx[3];     // cell edges L / n, fm
+    float Lf[3];      // FP32 copies (rounded once)
+    float dxf[3];
+    int32_t n[3];     // cells per axis
+    uint32_t ncells;  // n0 n1 n2
+    uint32_t cell_off;
+    uint32_t p_off;
+    uint32_t np;
+    uint32_t step;    // index of the next step (first Philox counter word)
+    double dt;
+    float dtf;
+    float Cf;         // FP32 copy of C
+    double C;         // sigma dt / (n_test V_cell): P22 = C v_rel
+    double norm;      // n_test V_cell: T^00 = sum E / norm
+    uint32_t key0, key1;
+    uint32_t thr8;    // top byte above thr8 rejects a pair outright; 256 = never
+    float gamma_fp64; // FP32 path: CM boosts with gamma above this use FP64
+};
+
+// Per-simulation counters (unsigned long long for atomics).
+enum StatIdx {
+    kStatSteps = 0,
+    kStatPairTests,
+    kStatAccepted,
+    kStatExecuted,
+    kStatReflections,
+    kStatFp64Boosts,
+    kStatOverflow,
+    kStatCount = 8
+};
+
+// Error bits set by kernels.
+constexpr uint32_t kErrAccOverflow = 1u;   // accepted list ran out of room
+constexpr uint32_t kErrCapacity = 2u;      // list capacity of a step exceeds the allocation
+
+// Radix sort geometry: 8-bit digits, 256 threads x 16 keys per tile.
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Scan geometry: 256 threads x 8 items per block.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Pair tile: one warp per item of 32 rows of one cell.
+constexpr int kPairRows = 32;
+constexpr int kPairThreads = 256;
+constexpr int kQueueCap = 64;         // queued Philox blocks per warp (flush above 32)
+
+// Resolve: per-cell accepted lists up to this size are sorted in shared memory.
+constexpr int kResolveThreads = 256;
+constexpr int kResolveSmemPairs = 4096;
+constexpr int kResolveBitmapWords = 4096;   // cells up to 131072 particles
+
+struct Uint2Add {
+    __host__ __device__ uint2 operator()(uint2 a, uint2 b) const { return make_uint2(a.x + b.x, a.y + b.y); }
+};
+
+// Locate the simulation that owns global particle g / global cell c.
+__device__ __forceinline__ int sim_of_particle(const SimDesc* sims, int nsims, uint32_t g)
+{
+    int lo = 0, hi = nsims - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sims[mid].p_off <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int sim_of_cell(const SimDesc* sims, int nsims, uint32_t c)
+{
+    int lo = 0, hi = nsims - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sims[mid].cell_off <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Device buffers of one arena.
+struct Arena {
+    int precision = 1;          // 0 FP32, 1 FP64
+    uint32_t pcap = 0, ccap = 0;
+    uint32_t np = 0, ncells = 0; // current totals
+    int nsims = 0, simcap = 0;
+    void* st[2] = {nullptr, nullptr};   // SoA state ping-pong, 6 * pcap elements
+    int cur = 0;
+    int sorted_buf = 0;                 // which key/idx buffer holds the last sort's result
+    uint32_t* key[2] = {nullptr, nullptr};
+    uint32_t* idx[2] = {nullptr, nullptr};
+    uint32_t* cell_start = nullptr;     // ccap + 1
+    uint2* cell_work = nullptr;         // ccap + 1: (pair items, list capacity) -> scanned
+    uint32_t* acc_count = nullptr;      // ccap
+    unsigned long long* acc = nullptr;  // accepted (i << 32 | j), per-cell segments
+    uint64_t acc_capacity = 0;
+    uint32_t* radix_hist = nullptr;     // 256 * tiles
+    uint32_t radix_hist_cap = 0;
+    void* scan_tmp = nullptr;           // scan partial sums
+    size_t scan_tmp_bytes = 0;
+    uint32_t* counters = nullptr;       // [0] pair work counter, [1] error bits, [2] active cells
+    uint32_t* active = nullptr;         // ccap: cells with at least one accepted pair
+    uint32_t* used_bits = nullptr;      // pcap / 32 + 1: greedy bitmap for cells too big for smem
+    unsigned long long* stats = nullptr;  // simcap * kStatCount
+    SimDesc* d_sims = nullptr;
+    // tracing
+    int trace = 0;
+    uint32_t* trace_keys = nullptr;     // pcap
+};
+
+// ---- launchers (kernels_sort.cu) ----
+int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double* d_regions, int nreg,
+                        const uint64_t* d_region_first, cudaStream_t st);
+int launch_keys_only(const Arena& A, cudaStream_t st);
+int launch_stream_key(const Arena& A, cudaStream_t st);
+int launch_sort_and_bin(Arena& A, cudaStream_t st);   // keys in key[0] -> sorted state, cell_start
+int launch_cell_prep(const Arena& A, cudaStream_t st);
+int launch_observables(const Arena& A, int sim, double* T00, double* T0x, int32_t* counts, cudaStream_t st);
+int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st);
+int launch_advance(const Arena& A, cudaStream_t st);
+int launch_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, cudaStream_t st);
+
+// ---- launchers (kernels_pairs.cu) ----
+int launch_pair_tile(const Arena& A, cudaStream_t st);
+int launch_resolve(const Arena& A, cudaStream_t st);
+int kernels_init();   // attributes and launch shapes; call before any capture
+
+// number of radix passes for a key range
+inline int radix_passes(uint32_t ncells)
+{
+    int bits = 0;
+    while (bits < 32 && (ncells - 1) >> bits) ++bits;
+    return (bits + kRadixBits - 1) / kRadixBits;
+}
+
+int sm_count();
+
+}  // namespace cuba

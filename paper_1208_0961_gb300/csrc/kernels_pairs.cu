@@ -1,0 +1,524 @@
+// Cell-parallel kernels of the collision step.
+//
+// k_pair_tile (A5): every pair i < j of every cell is tested against
+// P22 = C v_rel (Eq. 3).  The uniform u_ij = r_ij 2^-32 of a pair has its top
+// byte taken from the Philox block (step, cell, i, j / 16) — one block serves
+// sixteen pairs of a row — and its low 24 bits from the block
+// (step, cell, i, TAG_FINE | j).  Because P22 <= 2 C (1 + tiny) for every
+// pair, a top byte above thr8 = floor(2.0001 C 256) already proves
+// u_ij >= P22: such pairs are rejected from the first block alone, without
+// loading momenta; only the rare survivors (top byte <= thr8) evaluate the
+// second block and P22.  The decision is the same as testing every pair in
+// full.  Work unit: one warp takes 32 rows of one cell (lane = row) and walks
+// the row's column blocks; survivors are queued per warp in shared memory and
+// resolved together.  Accepted pairs go to the cell's segment of the list.
+//
+// k_resolve (A6, A7): per cell with accepted pairs — sort the list
+// lexicographically (bitonic network in shared memory), take the greedy
+// matching in that order (a particle collides at most once per step), then
+// apply the centre-of-mass kinematics to every executed pair in parallel.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "engine.cuh"
+#include "fp.cuh"
+
+namespace cuba {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kExecFlag = 1ull << 63;
+
+// u = r 2^-32 in the state's precision (FP32: r rounded to nearest float).
+template <typename T> __device__ __forceinline__ T unit_u(uint32_t r);
+template <> __device__ __forceinline__ double unit_u<double>(uint32_t r) { return __dmul_rn((double)r, 0x1p-32); }
+template <> __device__ __forceinline__ float unit_u<float>(uint32_t r) { return __fmul_rn(__uint2float_rn(r), 0x1p-32f); }
+
+// Unit direction p / E of a massless particle (zero vector if p = 0).
+template <typename T>
+__device__ __forceinline__ void unit_dir(const T* __restrict__ st, uint32_t pcap, uint32_t g, T u[3])
+{
+    const T px = st[3 * (size_t)pcap + g], py = st[4 * (size_t)pcap + g], pz = st[5 * (size_t)pcap + g];
+    const T E = sqrt_rn(add_rn(add_rn(mul_rn(px, px), mul_rn(py, py)), mul_rn(pz, pz)));
+    const bool ok = E > T(0);
+    u[0] = ok ? div_rn(px, E) : T(0);
+    u[1] = ok ? div_rn(py, E) : T(0);
+    u[2] = ok ? div_rn(pz, E) : T(0);
+}
+
+// P22 = C v_rel with v_rel = s / (2 E_i E_j) = |n_i - n_j|^2 / 2 (massless).
+template <typename T>
+__device__ __forceinline__ T pair_p22(T C, const T* __restrict__ st, uint32_t pcap, uint32_t gi, uint32_t gj)
+{
+    T ui[3], uj[3];
+    unit_dir<T>(st, pcap, gi, ui);
+    unit_dir<T>(st, pcap, gj, uj);
+    const T d0 = sub_rn(ui[0], uj[0]), d1 = sub_rn(ui[1], uj[1]), d2 = sub_rn(ui[2], uj[2]);
+    const T v = mul_rn(T(0.5), add_rn(add_rn(mul_rn(d0, d0), mul_rn(d1, d1)), mul_rn(d2, d2)));
+    return mul_rn(C, v);
+}
+
+// Nonzero iff some byte of the block is <= thr (thr < 128): a word has a byte
+// below m = thr + 1 iff (x - m * 0x01010101) & ~x & 0x80808080 != 0.
+__device__ __forceinline__ uint32_t any_byte_le(uint4 r, uint32_t thr)
+{
+    if (thr >= 128u) return 1u;
+    const uint32_t t = 0x01010101u * (thr + 1u);
+    const uint32_t h = ((r.x - t) & ~r.x) | ((r.y - t) & ~r.y) | ((r.z - t) & ~r.z) | ((r.w - t) & ~r.w);
+    return h & 0x80808080u;
+}
+
+struct CellCtx {
+    uint32_t c;       // global cell
+    uint32_t lc;      // cell index inside its simulation
+    uint32_t cbase;   // first particle of the cell
+    uint32_t n;       // particles in the cell
+    uint32_t list0;   // first slot of the cell's accepted-list segment
+    uint32_t room;    // slots in the segment
+    int s;            // simulation
+};
+
+template <typename T>
+__device__ __forceinline__ void resolve_candidates(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
+                                                   T C, const T* __restrict__ st, uint32_t pcap,
+                                                   const uint4* qw, const uint32_t* qi, const uint32_t* qg, uint32_t qn,
+                                                   uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
+                                                   uint64_t acc_cap, uint32_t* __restrict__ counters,
+                                                   uint32_t* __restrict__ active, unsigned long long* __restrict__ stats)
+{
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = lane; e < qn; e += 32) {
+        const uint4 r = qw[e];
+        const uint32_t i = qi[e], g = qg[e];
+        const uint32_t words[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int wi = 0; wi < 4; ++wi) {
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) {
+                const uint32_t b = (words[wi] >> (8 * bi)) & 0xFFu;
+                const uint32_t j = 16u * g + 4u * wi + bi;
+                if (b <= thr8 && j > i && j < cc.n) {
+                    const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
+                    const uint32_t rw = (b << 24) | (fine >> 8);
+                    const T u = unit_u<T>(rw);
+                    const T P = pair_p22<T>(C, st, pcap, cc.cbase + i, cc.cbase + j);
+                    if (u < P) {
+                        const uint32_t slot = atomicAdd(&acc_count[cc.c], 1u);
+                        if (slot == 0) active[atomicAdd(&counters[2], 1u)] = cc.c;
+                        if (slot < cc.room && (uint64_t)cc.list0 + slot < acc_cap) {
+                            acc[(size_t)cc.list0 + slot] = ((unsigned long long)i << 32) | j;
+                        } else {
+                            atomicOr(&counters[1], kErrAccOverflow);
+                            atomicAdd(&stats[cc.s * kStatCount + kStatOverflow], 1ull);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPairThreads) k_pair_tile(const SimDesc* __restrict__ sims, int nsims,
+                                                            const T* __restrict__ st, uint32_t pcap,
+                                                            const uint32_t* __restrict__ cell_start,
+                                                            const uint2* __restrict__ work, uint32_t ncells,
+                                                            uint32_t* __restrict__ acc_count,
+                                                            unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                            uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                            unsigned long long* __restrict__ stats)
+{
+    constexpr int kWarps = kPairThreads / 32;
+    __shared__ uint4 q_w[kWarps][kQueueCap];
+    __shared__ uint32_t q_i[kWarps][kQueueCap];
+    __shared__ uint32_t q_g[kWarps][kQueueCap];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t total = work[ncells].x;
+    if ((uint64_t)work[ncells].y > acc_cap) {
+        // the lists of this step do not fit the allocation: report, do nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&counters[1], kErrCapacity);
+        return;
+    }
+    uint32_t c = 0;  // search hint: items are handed out in increasing order
+
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&counters[0], 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= total) break;
+        // cell of the item: the last c with work[c].x <= item.  Gallop from
+        // the previous cell (work[c].x <= item holds there), then bisect.
+        {
+            uint32_t lo = c, stride = 1, hi = c + 1;
+            while (hi < ncells && work[hi].x <= item) {
+                lo = hi;
+                stride <<= 1;
+                hi = lo + stride;
+            }
+            uint32_t b = (hi < ncells ? hi : ncells) - 1;
+            while (lo < b) {
+                const uint32_t mid = (lo + b + 1) >> 1;
+                if (work[mid].x <= item) lo = mid; else b = mid - 1;
+            }
+            c = lo;
+        }
+        CellCtx cc;
+        cc.c = c;
+        cc.s = sim_of_cell(sims, nsims, c);
+        const SimDesc& S = sims[cc.s];
+        const uint2 w0 = work[c], w1 = work[c + 1];
+        cc.lc = c - S.cell_off;
+        cc.cbase = cell_start[c];
+        cc.n = cell_start[c + 1] - cc.cbase;
+        cc.list0 = w0.y;
+        cc.room = w1.y - w0.y;
+        const uint32_t rb = item - w0.x;
+        const uint32_t step = S.step, thr8 = S.thr8;
+        const T C = sim_C<T>(S);
+        const PhiloxKey K = philox_schedule(S.key0, S.key1);
+
+        const uint32_t i = rb * kPairRows + lane;
+        const bool row_ok = i + 1 < cc.n;
+        const uint32_t gfirst = (rb * kPairRows + 1) >> 4;
+        const uint32_t glast = (cc.n - 1) >> 4;
+        uint32_t qn = 0;
+        for (uint32_t g = gfirst; g <= glast; ++g) {
+            const uint4 r = philox4x32_10(make_uint4(step, cc.lc, i, g), K);
+            const uint32_t hit = row_ok ? any_byte_le(r, thr8) : 0u;
+            const unsigned ball = __ballot_sync(kFull, hit != 0u);
+            if (ball) {
+                if (qn + 32 > (uint32_t)kQueueCap) {
+                    __syncwarp();
+                    resolve_candidates<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], qn, acc_count, acc,
+                                          acc_cap, counters, active, stats);
+                    __syncwarp();
+                    qn = 0;
+                }
+                if (hit) {
+                    const uint32_t slot = qn + (uint32_t)__popc(ball & lt);
+                    q_w[w][slot] = r;
+                    q_i[w][slot] = i;
+                    q_g[w][slot] = g;
+                }
+                qn += (uint32_t)__popc(ball);
+            }
+        }
+        if (qn) {
+            __syncwarp();
+            resolve_candidates<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], qn, acc_count, acc, acc_cap,
+                                  counters, active, stats);
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A6-A7
+// ---------------------------------------------------------------------------
+
+// Sorting network for m keys in place, ascending; positions >= m behave as
+// +infinity and are never touched (flip/half-cleaner form of bitonic sort).
+__device__ void bitonic_sort(unsigned long long* L, uint32_t m)
+{
+    uint32_t p2 = 1;
+    while (p2 < m) p2 <<= 1;
+    for (uint32_t k = 2; k <= p2; k <<= 1) {
+        const uint32_t half = k >> 1;
+        for (uint32_t t = threadIdx.x; t < p2 / 2; t += blockDim.x) {
+            const uint32_t blk = t / half, off = t - blk * half;
+            const uint32_t a = blk * k + off, b = blk * k + k - 1 - off;
+            if (b < m) {
+                const unsigned long long x = L[a], y = L[b];
+                if (x > y) { L[a] = y; L[b] = x; }
+            }
+        }
+        __syncthreads();
+        for (uint32_t j = k >> 2; j >= 1; j >>= 1) {
+            for (uint32_t t = threadIdx.x; t < p2 / 2; t += blockDim.x) {
+                const uint32_t blk = t / j, off = t - blk * j;
+                const uint32_t a = blk * 2 * j + off, b = a + j;
+                if (b < m) {
+                    const unsigned long long x = L[a], y = L[b];
+                    if (x > y) { L[a] = y; L[b] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename R> __device__ __forceinline__ R word_unit(uint32_t w);
+template <> __device__ __forceinline__ double word_unit<double>(uint32_t w) { return (double)w * 0x1p-32; }
+template <> __device__ __forceinline__ float word_unit<float>(uint32_t w) { return __uint2float_rn(w) * 0x1p-32f; }
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+
+// Lorentz factor of the pair's centre-of-mass frame, gamma = E_t / sqrt(s).
+template <typename R>
+__device__ __forceinline__ R pair_gamma(const R mi[3], const R mj[3])
+{
+    const R Ei = sqrt((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]);
+    const R Ej = sqrt((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]);
+    if (!(Ei > R(0)) || !(Ej > R(0))) return R(0);
+    R d[3];
+    for (int a = 0; a < 3; ++a) d[a] = mi[a] / Ei - mj[a] / Ej;
+    const R s = ((R(2) * Ei) * Ej) * (R(0.5) * ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]));
+    return (s > R(0)) ? (Ei + Ej) / sqrt(s) : R(0);
+}
+
+// Executed pair (Sec. 2): boost to the CM frame, isotropic direction from the
+// Philox block (step, cell, i, TAG_ANGLE | j), boost back.
+// p' = p* + beta (gamma^2 / (gamma + 1) (beta . p*) + gamma E*), p2* = -p*.
+template <typename R>
+__device__ __forceinline__ bool collide_pair(const PhiloxKey& K, uint32_t step, uint32_t lc, uint32_t i, uint32_t j,
+                                             R mi[3], R mj[3])
+{
+    const R Ei = sqrt((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]);
+    const R Ej = sqrt((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]);
+    R ui[3], uj[3];
+    for (int a = 0; a < 3; ++a) {
+        ui[a] = (Ei > R(0)) ? mi[a] / Ei : R(0);
+        uj[a] = (Ej > R(0)) ? mj[a] / Ej : R(0);
+    }
+    const R d0 = ui[0] - uj[0], d1 = ui[1] - uj[1], d2 = ui[2] - uj[2];
+    const R s = ((R(2) * Ei) * Ej) * (R(0.5) * ((d0 * d0 + d1 * d1) + d2 * d2));
+    if (!(s > R(0))) return false;
+    const R rs = sqrt(s);
+    const R Es = R(0.5) * rs;
+    const R Et = Ei + Ej;
+    const R beta[3] = {(mi[0] + mj[0]) / Et, (mi[1] + mj[1]) / Et, (mi[2] + mj[2]) / Et};
+    const R gamma = Et / rs;
+    const uint4 w = philox4x32_10(make_uint4(step, lc, i, kTagAngle | j), K);
+    const R u1 = word_unit<R>(w.x), u2 = word_unit<R>(w.y);
+    const R ct = R(2) * u1 - R(1);
+    const R stt = sqrt((R(1) - ct) * (R(1) + ct));
+    R sp, cp;
+    sincos_t(R(2) * R(3.141592653589793) * u2, &sp, &cp);
+    const R ps[3] = {Es * (stt * cp), Es * (stt * sp), Es * ct};
+    const R bp = (beta[0] * ps[0] + beta[1] * ps[1]) + beta[2] * ps[2];
+    const R a = (gamma * gamma) / (gamma + R(1));
+    const R fi = a * bp + gamma * Es;
+    const R fj = -a * bp + gamma * Es;
+    for (int q = 0; q < 3; ++q) {
+        mi[q] = ps[q] + beta[q] * fi;
+        mj[q] = -ps[q] + beta[q] * fj;
+    }
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ int collide_state(const SimDesc& S, const PhiloxKey& K, uint32_t lc, uint32_t i, uint32_t j,
+                                             T* __restrict__ st, uint32_t pcap, uint32_t gi, uint32_t gj);
+
+template <>
+__device__ __forceinline__ int collide_state<double>(const SimDesc& S, const PhiloxKey& K, uint32_t lc, uint32_t i,
+                                                     uint32_t j, double* __restrict__ st, uint32_t pcap, uint32_t gi,
+                                                     uint32_t gj)
+{
+    double mi[3], mj[3];
+    for (int a = 0; a < 3; ++a) {
+        mi[a] = st[(size_t)(3 + a) * pcap + gi];
+        mj[a] = st[(size_t)(3 + a) * pcap + gj];
+    }
+    if (collide_pair<double>(K, S.step, lc, i, j, mi, mj)) {
+        for (int a = 0; a < 3; ++a) {
+            st[(size_t)(3 + a) * pcap + gi] = mi[a];
+            st[(size_t)(3 + a) * pcap + gj] = mj[a];
+        }
+    }
+    return 0;
+}
+
+// FP32 state: FP32 kinematics unless the CM Lorentz factor exceeds the
+// simulation's threshold, where the boost cancels badly and FP64 is used.
+template <>
+__device__ __forceinline__ int collide_state<float>(const SimDesc& S, const PhiloxKey& K, uint32_t lc, uint32_t i,
+                                                    uint32_t j, float* __restrict__ st, uint32_t pcap, uint32_t gi,
+                                                    uint32_t gj)
+{
+    float mi[3], mj[3];
+    for (int a = 0; a < 3; ++a) {
+        mi[a] = st[(size_t)(3 + a) * pcap + gi];
+        mj[a] = st[(size_t)(3 + a) * pcap + gj];
+    }
+    const float gam = pair_gamma<float>(mi, mj);
+    int used64 = 0;
+    bool ok;
+    if (gam > S.gamma_fp64 || !(gam > 0.0f)) {
+        double di[3], dj[3];
+        for (int a = 0; a < 3; ++a) { di[a] = mi[a]; dj[a] = mj[a]; }
+        ok = collide_pair<double>(K, S.step, lc, i, j, di, dj);
+        for (int a = 0; a < 3; ++a) { mi[a] = (float)di[a]; mj[a] = (float)dj[a]; }
+        used64 = 1;
+    } else {
+        ok = collide_pair<float>(K, S.step, lc, i, j, mi, mj);
+    }
+    if (ok) {
+        for (int a = 0; a < 3; ++a) {
+            st[(size_t)(3 + a) * pcap + gi] = mi[a];
+            st[(size_t)(3 + a) * pcap + gj] = mj[a];
+        }
+    }
+    return used64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kResolveThreads) k_resolve(const SimDesc* __restrict__ sims, int nsims, T* __restrict__ st,
+                                                             uint32_t pcap, const uint32_t* __restrict__ cell_start,
+                                                             const uint2* __restrict__ work,
+                                                             const uint32_t* __restrict__ acc_count,
+                                                             unsigned long long* __restrict__ acc,
+                                                             const uint32_t* __restrict__ counters,
+                                                             const uint32_t* __restrict__ active,
+                                                             uint64_t acc_cap, uint32_t* __restrict__ used_global,
+                                                             unsigned long long* __restrict__ stats)
+{
+    extern __shared__ unsigned long long smem[];
+    unsigned long long* list_s = smem;
+    uint32_t* bits_s = reinterpret_cast<uint32_t*>(smem + kResolveSmemPairs);
+    __shared__ uint32_t s_nexe, s_n64;
+    const uint32_t nact = counters[2];
+    for (uint32_t a = blockIdx.x; a < nact; a += gridDim.x) {
+        const uint32_t c = active[a];
+        const uint2 w0 = work[c], w1 = work[c + 1];
+        const uint32_t room = w1.y - w0.y;
+        const uint32_t cnt = acc_count[c];
+        uint32_t m = cnt < room ? cnt : room;
+        if ((uint64_t)w0.y + m > acc_cap) m = (w0.y < acc_cap) ? (uint32_t)(acc_cap - w0.y) : 0u;
+        const int s = sim_of_cell(sims, nsims, c);
+        const SimDesc& S = sims[s];
+        const uint32_t cbase = cell_start[c], n = cell_start[c + 1] - cbase;
+        const uint32_t lc = c - S.cell_off;
+        unsigned long long* gl = acc + w0.y;
+        const bool in_smem = m <= (uint32_t)kResolveSmemPairs;
+        const bool bits_in_smem = n <= 32u * kResolveBitmapWords;
+        unsigned long long* L = in_smem ? list_s : gl;
+        if (threadIdx.x == 0) { s_nexe = 0; s_n64 = 0; }
+        if (in_smem)
+            for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) L[k] = gl[k];
+        if (bits_in_smem)
+            for (uint32_t k = threadIdx.x; k < (n + 31) / 32; k += blockDim.x) bits_s[k] = 0u;
+        __syncthreads();
+        bitonic_sort(L, m);
+        // A6: greedy matching in lexicographic order
+        if (threadIdx.x == 0) {
+            uint32_t ne = 0;
+            for (uint32_t k = 0; k < m; ++k) {
+                const unsigned long long v = L[k];
+                const uint32_t i = (uint32_t)(v >> 32), j = (uint32_t)v;
+                if (bits_in_smem) {
+                    const uint32_t bi = (bits_s[i >> 5] >> (i & 31)) & 1u;
+                    const uint32_t bj = (bits_s[j >> 5] >> (j & 31)) & 1u;
+                    if (bi | bj) continue;
+                    bits_s[i >> 5] |= 1u << (i & 31);
+                    bits_s[j >> 5] |= 1u << (j & 31);
+                } else {
+                    const uint32_t gi = cbase + i, gj = cbase + j;
+                    const uint32_t bi = (atomicOr(&used_global[gi >> 5], 0u) >> (gi & 31)) & 1u;
+                    const uint32_t bj = (atomicOr(&used_global[gj >> 5], 0u) >> (gj & 31)) & 1u;
+                    if (bi | bj) continue;
+                    atomicOr(&used_global[gi >> 5], 1u << (gi & 31));
+                    atomicOr(&used_global[gj >> 5], 1u << (gj & 31));
+                }
+                L[k] = v | kExecFlag;
+                ++ne;
+            }
+            s_nexe = ne;
+        }
+        __syncthreads();
+        // A7: kinematics of the executed pairs (disjoint, so in parallel)
+        const PhiloxKey K = philox_schedule(S.key0, S.key1);
+        uint32_t n64 = 0;
+        for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+            const unsigned long long v = L[k];
+            if (!(v & kExecFlag)) continue;
+            const uint32_t i = (uint32_t)(v >> 32) & 0x7FFFFFFFu, j = (uint32_t)v;
+            n64 += (uint32_t)collide_state<T>(S, K, lc, i, j, st, pcap, cbase + i, cbase + j);
+            if (!bits_in_smem) {
+                atomicAnd(&used_global[(cbase + i) >> 5], ~(1u << ((cbase + i) & 31)));
+                atomicAnd(&used_global[(cbase + j) >> 5], ~(1u << ((cbase + j) & 31)));
+            }
+        }
+        if (n64) atomicAdd(&s_n64, n64);
+        if (in_smem)
+            for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) gl[k] = L[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicAdd(&stats[s * kStatCount + kStatAccepted], (unsigned long long)cnt);
+            atomicAdd(&stats[s * kStatCount + kStatExecuted], (unsigned long long)s_nexe);
+            if (s_n64) atomicAdd(&stats[s * kStatCount + kStatFp64Boosts], (unsigned long long)s_n64);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static int last_err() { return cudaPeekAtLastError() == cudaSuccess ? 0 : -1; }
+
+template <typename T>
+static unsigned pair_grid()
+{
+    static unsigned g = 0;
+    if (!g) {
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_tile<T>, kPairThreads, 0);
+        if (per < 1) per = 1;
+        g = (unsigned)(per * sm_count());
+    }
+    return g;
+}
+
+int launch_pair_tile(const Arena& A, cudaStream_t st)
+{
+    if (A.ncells == 0) return 0;
+    if (A.precision == 1)
+        k_pair_tile<double><<<pair_grid<double>(), kPairThreads, 0, st>>>(
+            A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count,
+            A.acc, A.acc_capacity, A.counters, A.active, A.stats);
+    else
+        k_pair_tile<float><<<pair_grid<float>(), kPairThreads, 0, st>>>(
+            A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count,
+            A.acc, A.acc_capacity, A.counters, A.active, A.stats);
+    return last_err();
+}
+
+static const size_t kResolveSmemBytes =
+    kResolveSmemPairs * sizeof(unsigned long long) + kResolveBitmapWords * sizeof(uint32_t);
+
+// Kernel attributes and launch shapes, set once before any stream capture.
+int kernels_init()
+{
+    static bool done = false;
+    if (done) return 0;
+    if (cudaFuncSetAttribute(k_resolve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResolveSmemBytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_resolve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResolveSmemBytes) !=
+            cudaSuccess)
+        return -1;
+    pair_grid<double>();
+    pair_grid<float>();
+    sm_count();
+    done = true;
+    return 0;
+}
+
+int launch_resolve(const Arena& A, cudaStream_t st)
+{
+    if (A.ncells == 0) return 0;
+    const size_t smem = kResolveSmemBytes;
+    const unsigned g = (unsigned)(sm_count() * 4);
+    if (A.precision == 1)
+        k_resolve<double><<<g, kResolveThreads, smem, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap,
+                                                           A.cell_start, A.cell_work, A.acc_count, A.acc, A.counters,
+                                                           A.active, A.acc_capacity, A.used_bits, A.stats);
+    else
+        k_resolve<float><<<g, kResolveThreads, smem, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap,
+                                                          A.cell_start, A.cell_work, A.acc_count, A.acc, A.counters,
+                                                          A.active, A.acc_capacity, A.used_bits, A.stats);
+    return last_err();
+}
+
+}  // namespace cuba

@@ -1,0 +1,678 @@
+// Particle-parallel kernels of the step: thermal sampling, free streaming with
+// wall reflection and cell keys (A1-A3), the stable counting sort by cell
+// (A4, an LSD radix sort on 8-bit digits), the per-cell work preparation of the
+// pair step, and the FP64 observables (A8).
+//
+// Bit-reproducibility: the streaming, the key and the sampling positions use
+// explicitly rounded IEEE operations (__dadd_rn, __fdiv_rn, ...) in the order
+// the method states, so that a CPU evaluation of the same expressions gives
+// identical bits.  The library is also compiled without multiply-add
+// contraction.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "engine.cuh"
+#include "fp.cuh"
+
+namespace cuba {
+
+// Cell key: i_a = clamp(floor(x_a / dx_a), 0, n_a - 1); key = ix + nx (iy + ny iz).
+template <typename T>
+__device__ __forceinline__ uint32_t cell_key(const SimDesc& S, const T pos[3])
+{
+    uint32_t id[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T c = floor_t(div_rn(pos[a], sim_dx<T>(S, a)));
+        uint32_t ic;
+        if (c < T(0)) ic = 0;
+        else if (c >= (T)S.n[a]) ic = (uint32_t)(S.n[a] - 1);
+        else ic = (uint32_t)c;
+        id[a] = ic;
+    }
+    return id[0] + (uint32_t)S.n[0] * (id[1] + (uint32_t)S.n[1] * id[2]);
+}
+
+// Free streaming x <- x + (p/E) dt (Eq. 2, c = 1, E = |p|) and elastic
+// reflection: beyond a wall the position is mirrored and that momentum
+// component flips.  Returns the number of reflections.
+template <typename T>
+__device__ __forceinline__ int stream_one(const SimDesc& S, T pos[3], T mom[3])
+{
+    const T E = sqrt_rn(add_rn(add_rn(mul_rn(mom[0], mom[0]), mul_rn(mom[1], mom[1])), mul_rn(mom[2], mom[2])));
+    const T dt = sim_dt<T>(S);
+    int nref = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T L = sim_L<T>(S, a);
+        const T v = (E > T(0)) ? div_rn(mom[a], E) : T(0);
+        T x = add_rn(pos[a], mul_rn(v, dt));
+        if (x < T(0)) {
+            x = -x;
+            mom[a] = -mom[a];
+            ++nref;
+        } else if (x > L) {
+            x = sub_rn(add_rn(L, L), x);
+            mom[a] = -mom[a];
+            ++nref;
+        }
+        pos[a] = x;
+    }
+    return nref;
+}
+
+// ---------------------------------------------------------------------------
+// A1-A3: stream, reflect, key (one thread per particle, SoA coalesced)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_key(const SimDesc* __restrict__ sims, int nsims, T* __restrict__ st,
+                                                    uint32_t pcap, uint32_t np, uint32_t* __restrict__ keys,
+                                                    unsigned long long* __restrict__ stats)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < np; g += stride) {
+        const int s = sim_of_particle(sims, nsims, g);
+        const SimDesc& S = sims[s];
+        T pos[3] = {st[g], st[pcap + g], st[2 * (size_t)pcap + g]};
+        T mom[3] = {st[3 * (size_t)pcap + g], st[4 * (size_t)pcap + g], st[5 * (size_t)pcap + g]};
+        const int nref = stream_one<T>(S, pos, mom);
+        st[g] = pos[0];
+        st[pcap + g] = pos[1];
+        st[2 * (size_t)pcap + g] = pos[2];
+        if (nref) {
+            st[3 * (size_t)pcap + g] = mom[0];
+            st[4 * (size_t)pcap + g] = mom[1];
+            st[5 * (size_t)pcap + g] = mom[2];
+        }
+        keys[g] = S.cell_off + cell_key<T>(S, pos);
+        // reflections: one atomic per warp and simulation
+        const unsigned peers = __match_any_sync(__activemask(), s);
+        const unsigned tot = __reduce_add_sync(peers, (unsigned)nref);
+        if ((threadIdx.x & 31) == (__ffs(peers) - 1) && tot) atomicAdd(&stats[s * kStatCount + kStatReflections], (unsigned long long)tot);
+    }
+}
+
+// Keys of a state without moving it (after sampling or loading a state).
+template <typename T>
+__global__ void __launch_bounds__(256) k_keys_only(const SimDesc* __restrict__ sims, int nsims, const T* __restrict__ st,
+                                                   uint32_t pcap, uint32_t np, uint32_t* __restrict__ keys)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < np; g += stride) {
+        const int s = sim_of_particle(sims, nsims, g);
+        const SimDesc& S = sims[s];
+        T pos[3] = {st[g], st[pcap + g], st[2 * (size_t)pcap + g]};
+        keys[g] = S.cell_off + cell_key<T>(S, pos);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Thermal sampling (generation order; sorted afterwards)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double open01(uint32_t r) { return ((double)r + 0.5) * 0x1p-32; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_thermal(SimDesc S, T* __restrict__ st, uint32_t pcap,
+                                                      const double* __restrict__ regions, int nreg,
+                                                      const uint64_t* __restrict__ first)
+{
+    const PhiloxKey K = philox_schedule(S.key0, S.key1);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < S.np; g += stride) {
+        int r = 0;
+        while (r + 1 < nreg && first[r + 1] <= g) ++r;
+        const double* R = regions + 7 * r;  // lo[3], hi[3], T
+        const uint4 a = philox4x32_10(make_uint4(kStepInit, g, 0u, 0u), K);
+        const uint4 b = philox4x32_10(make_uint4(kStepInit, g, 0u, 1u), K);
+        const uint32_t aw[3] = {a.x, a.y, a.z};
+        double pos[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+            pos[ax] = __dadd_rn(R[ax], __dmul_rn(open01(aw[ax]), __dsub_rn(R[3 + ax], R[ax])));
+        const double E = -R[6] * log(open01(a.w) * open01(b.x) * open01(b.y));
+        const double ct = 2.0 * open01(b.z) - 1.0;
+        const double stt = sqrt((1.0 - ct) * (1.0 + ct));
+        const double phi = 2.0 * 3.141592653589793 * open01(b.w);
+        double sp, cp;
+        sincos(phi, &sp, &cp);
+        const double mom[3] = {E * stt * cp, E * stt * sp, E * ct};
+        const uint32_t o = S.p_off + g;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            st[(size_t)ax * pcap + o] = (T)pos[ax];
+            st[(size_t)(3 + ax) * pcap + o] = (T)mom[ax];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan (reduce, scan partials, apply)
+// ---------------------------------------------------------------------------
+template <typename V, typename Op>
+__device__ __forceinline__ V warp_incl_scan(V v, Op op)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        V t;
+        if constexpr (sizeof(V) == 8) {
+            uint2 u = *reinterpret_cast<uint2*>(&v);
+            uint2 w;
+            w.x = __shfl_up_sync(0xffffffffu, u.x, o);
+            w.y = __shfl_up_sync(0xffffffffu, u.y, o);
+            t = *reinterpret_cast<V*>(&w);
+        } else {
+            t = __shfl_up_sync(0xffffffffu, v, o);
+        }
+        if (lane >= o) v = op(t, v);
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of kScanThreads values; returns the block total.
+template <typename V, typename Op>
+__device__ __forceinline__ V block_excl_scan(V v, V zero, Op op, V* excl)
+{
+    __shared__ V warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    V inc = warp_incl_scan(v, op);
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        V t = (lane < kScanThreads / 32) ? warp_tot[lane] : zero;
+        t = warp_incl_scan(t, op);
+        if (lane < kScanThreads / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    V base = (w > 0) ? warp_tot[w - 1] : zero;
+    V total = warp_tot[kScanThreads / 32 - 1];
+    // exclusive within warp
+    V ex;
+    if constexpr (sizeof(V) == 8) {
+        uint2 u = *reinterpret_cast<uint2*>(&inc);
+        uint2 q;
+        q.x = __shfl_up_sync(0xffffffffu, u.x, 1);
+        q.y = __shfl_up_sync(0xffffffffu, u.y, 1);
+        ex = *reinterpret_cast<V*>(&q);
+    } else {
+        ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    }
+    if (lane == 0) ex = zero;
+    *excl = op(base, ex);
+    __syncthreads();
+    return total;
+}
+
+template <typename V, typename Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const V* __restrict__ in, size_t n, V* __restrict__ partial, V zero, Op op)
+{
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+    V acc = zero;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) acc = op(acc, in[base + k]);
+    V ex;
+    V tot = block_excl_scan(acc, zero, op, &ex);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <typename V, typename Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(V* __restrict__ partial, size_t nb, V zero, Op op)
+{
+    V carry = zero;
+    for (size_t off = 0; off < nb; off += kScanTile) {
+        const size_t base = off + (size_t)threadIdx.x * kScanItems;
+        V vals[kScanItems];
+        V acc = zero;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            vals[k] = (base + k < nb) ? partial[base + k] : zero;
+            acc = op(acc, vals[k]);
+        }
+        V ex;
+        V tot = block_excl_scan(acc, zero, op, &ex);
+        V run = op(carry, ex);
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < nb) partial[base + k] = run;
+            run = op(run, vals[k]);
+        }
+        carry = op(carry, tot);
+        __syncthreads();
+    }
+}
+
+template <typename V, typename Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(V* __restrict__ data, size_t n, const V* __restrict__ partial, V zero, Op op)
+{
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+    V vals[kScanItems];
+    V acc = zero;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        vals[k] = (base + k < n) ? data[base + k] : zero;
+        acc = op(acc, vals[k]);
+    }
+    V ex;
+    block_excl_scan(acc, zero, op, &ex);
+    V run = op(partial[blockIdx.x], ex);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) data[base + k] = run;
+        run = op(run, vals[k]);
+    }
+}
+
+struct U32Add {
+    __host__ __device__ uint32_t operator()(uint32_t a, uint32_t b) const { return a + b; }
+};
+
+template <typename V, typename Op>
+static int exclusive_scan(V* data, size_t n, V zero, Op op, void* tmp, size_t tmp_bytes, cudaStream_t st)
+{
+    if (n == 0) return 0;
+    const size_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb * sizeof(V) > tmp_bytes) return -1;
+    V* partial = reinterpret_cast<V*>(tmp);
+    k_scan_reduce<V, Op><<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, partial, zero, op);
+    k_scan_partials<V, Op><<<1, kScanThreads, 0, st>>>(partial, nb, zero, op);
+    k_scan_apply<V, Op><<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, partial, zero, op);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// A4: stable LSD radix sort of the cell keys (8-bit digits)
+// ---------------------------------------------------------------------------
+// Tile t covers keys [t * 4096, (t + 1) * 4096); warp w of a tile owns the
+// contiguous 512 keys starting at w * 512, processed 32 at a time in order.
+// Stability follows from (tile, warp, round, lane) order = index order.
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
+                                                             uint32_t ntiles, uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kRadixBins];
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kSortTile;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t i = base + w * (32 * kSortItems) + r * 32 + lane;
+        const bool ok = i < n;
+        const uint32_t d = ok ? (keys[i] >> shift) & (kRadixBins - 1) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) hist[(size_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ key_in, const uint32_t* __restrict__ idx_in,
+                                                                uint32_t* __restrict__ key_out, uint32_t* __restrict__ idx_out,
+                                                                uint32_t n, int shift, uint32_t ntiles,
+                                                                const uint32_t* __restrict__ hist_scanned)
+{
+    __shared__ uint32_t wh[kSortThreads / 32][kRadixBins];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = lane; d < kRadixBins; d += 32) wh[w][d] = 0;
+    __syncwarp();
+    const uint32_t base = blockIdx.x * kSortTile + w * (32 * kSortItems);
+    uint32_t k[kSortItems], v[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        const bool ok = i < n;
+        k[r] = ok ? key_in[i] : 0xFFFFFFFFu;
+        v[r] = ok ? (idx_in ? idx_in[i] : i) : 0u;
+        const uint32_t d = ok ? (k[r] >> shift) & (kRadixBins - 1) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok && lane == __ffs(peers) - 1) wh[w][d] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: global tile offset, then warps in order
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+        uint32_t run = hist_scanned[(size_t)d * ntiles + blockIdx.x];
+#pragma unroll
+        for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+            const uint32_t c = wh[ww][d];
+            wh[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        const bool ok = i < n;
+        const uint32_t d = ok ? (k[r] >> shift) & (kRadixBins - 1) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t pos = 0;
+        if (ok) {
+            pos = wh[w][d] + (uint32_t)__popc(peers & lt);
+            key_out[pos] = k[r];
+            idx_out[pos] = v[r];
+        }
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) wh[w][d] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+}
+
+// Gather the payload into sorted order and derive cell_start from the sorted
+// keys: cell_start[c] = first sorted position with key >= c.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
+                                                const T* __restrict__ src, T* __restrict__ dst, uint32_t pcap,
+                                                uint32_t np, uint32_t* __restrict__ cell_start, uint32_t ncells)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
+        const uint32_t s = perm[k];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dst[(size_t)c * pcap + k] = src[(size_t)c * pcap + s];
+        const uint32_t kk = skey[k];
+        const int64_t prev = (k == 0) ? -1 : (int64_t)skey[k - 1];
+        for (int64_t c = prev + 1; c <= (int64_t)kk; ++c) cell_start[c] = k;
+        if (k == np - 1)
+            for (int64_t c = (int64_t)kk + 1; c <= (int64_t)ncells; ++c) cell_start[c] = np;
+    }
+}
+
+__global__ void k_fill_u32(uint32_t* p, uint32_t n, uint32_t v)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void k_iota(uint32_t* p, uint32_t n)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+// ---------------------------------------------------------------------------
+// Per-cell preparation of the pair step
+// ---------------------------------------------------------------------------
+// Row blocks of 32 rows (rows 0 .. n-2 have partners); accepted-list room is
+// mu + 8 sqrt(mu) + 16 with mu = 2.0001 C n (n - 1) / 2: the accepted count is
+// dominated by a binomial with success probability max P22 <= 2 C, so the
+// room is exceeded with probability far below 1e-15 per cell and step.
+__device__ __forceinline__ uint32_t list_room(double C, uint32_t n)
+{
+    const double mu = 2.0001 * C * (0.5 * (double)n * (double)(n - 1));
+    const double room = ceil(mu + 8.0 * sqrt(mu) + 16.0);
+    return room > 4.0e9 ? 0xFFFFFFFFu : (uint32_t)room;
+}
+
+__global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ sims, int nsims,
+                                                   const uint32_t* __restrict__ cell_start, uint2* __restrict__ work,
+                                                   uint32_t* __restrict__ acc_count, uint32_t ncells,
+                                                   uint32_t* __restrict__ counters, unsigned long long* __restrict__ stats)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0) {
+        counters[0] = 0;  // pair work counter
+        counters[2] = 0;  // active cells
+        work[ncells] = make_uint2(0, 0);
+    }
+    for (uint32_t c = t0; c < ncells; c += stride) {
+        const int s = sim_of_cell(sims, nsims, c);
+        const SimDesc& S = sims[s];
+        const uint32_t n = cell_start[c + 1] - cell_start[c];
+        uint32_t items = 0, room = 0;
+        if (n >= 2 && S.C > 0.0) {
+            items = (n - 1 + kPairRows - 1) / kPairRows;
+            room = list_room(S.C, n);
+            atomicAdd(&stats[s * kStatCount + kStatPairTests], (unsigned long long)n * (n - 1) / 2);
+        }
+        work[c] = make_uint2(items, room);
+        acc_count[c] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A8: observables (FP64 sums per cell, fixed order) and totals
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum_fixed(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    }
+    __syncthreads();
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_observables(SimDesc S, const T* __restrict__ st, uint32_t pcap,
+                                                     const uint32_t* __restrict__ cell_start, double* __restrict__ T00,
+                                                     double* __restrict__ T0x, int32_t* __restrict__ counts)
+{
+    __shared__ double red[8];
+    for (uint32_t c = blockIdx.x; c < S.ncells; c += gridDim.x) {
+        const uint32_t b = cell_start[S.cell_off + c], e = cell_start[S.cell_off + c + 1];
+        double se = 0.0, sx = 0.0;
+        for (uint32_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+            const double qx = st[3 * (size_t)pcap + k], qy = st[4 * (size_t)pcap + k], qz = st[5 * (size_t)pcap + k];
+            se += sqrt((qx * qx + qy * qy) + qz * qz);
+            sx += qx;
+        }
+        const double te = block_sum_fixed(se, red);
+        const double tx = block_sum_fixed(sx, red);
+        if (threadIdx.x == 0) {
+            T00[c] = te / S.norm;
+            T0x[c] = tx / S.norm;
+            counts[c] = (int32_t)(e - b);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_totals_partial(SimDesc S, const T* __restrict__ st, uint32_t pcap,
+                                                        double* __restrict__ part)
+{
+    __shared__ double red[8];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < S.np; k += stride) {
+        const uint32_t g = S.p_off + k;
+        const double qx = st[3 * (size_t)pcap + g], qy = st[4 * (size_t)pcap + g], qz = st[5 * (size_t)pcap + g];
+        a[0] += sqrt((qx * qx + qy * qy) + qz * qz);
+        a[1] += qx;
+        a[2] += qy;
+        a[3] += qz;
+    }
+    for (int q = 0; q < 4; ++q) {
+        const double t = block_sum_fixed(a[q], red);
+        if (threadIdx.x == 0) part[blockIdx.x * 4 + q] = t;
+    }
+}
+
+__global__ void k_totals_final(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[b * 4 + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
+__global__ void k_advance(SimDesc* sims, int nsims, unsigned long long* stats)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsims) {
+        sims[s].step += 1;
+        stats[s * kStatCount + kStatSteps] += 1;
+    }
+}
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* __restrict__ out)
+{
+    const PhiloxKey K = philox_schedule(k0, k1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+        const uint4 r = philox4x32_10(c, K);
+        out[4 * i] = r.x;
+        out[4 * i + 1] = r.y;
+        out[4 * i + 2] = r.z;
+        out[4 * i + 3] = r.w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+static unsigned grid_for(uint64_t n, int threads, int per_sm)
+{
+    uint64_t need = (n + threads - 1) / threads;
+    uint64_t cap = (uint64_t)sm_count() * per_sm;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+static int last_err() { return cudaPeekAtLastError() == cudaSuccess ? 0 : -1; }
+
+int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double* d_regions, int nreg,
+                        const uint64_t* d_first, cudaStream_t st)
+{
+    (void)sim;
+    if (S.np == 0) return 0;
+    const unsigned g = grid_for(S.np, 256, 8);
+    if (A.precision == 1)
+        k_init_thermal<double><<<g, 256, 0, st>>>(S, (double*)A.st[A.cur], A.pcap, d_regions, nreg, d_first);
+    else
+        k_init_thermal<float><<<g, 256, 0, st>>>(S, (float*)A.st[A.cur], A.pcap, d_regions, nreg, d_first);
+    return last_err();
+}
+
+int launch_keys_only(const Arena& A, cudaStream_t st)
+{
+    if (A.np == 0) return 0;
+    const unsigned g = grid_for(A.np, 256, 8);
+    if (A.precision == 1)
+        k_keys_only<double><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, A.np, A.key[0]);
+    else
+        k_keys_only<float><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, A.np, A.key[0]);
+    return last_err();
+}
+
+int launch_stream_key(const Arena& A, cudaStream_t st)
+{
+    if (A.np == 0) return 0;
+    const unsigned g = grid_for(A.np, 256, 8);
+    if (A.precision == 1)
+        k_stream_key<double><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, A.np, A.key[0], A.stats);
+    else
+        k_stream_key<float><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap, A.np, A.key[0], A.stats);
+    return last_err();
+}
+
+// Keys of the current state are in key[0].  Sorts the state into the other
+// buffer (A.cur flips), leaves the permutation in idx[final] and the sorted
+// keys in key[final], and writes cell_start.
+int launch_sort_and_bin(Arena& A, cudaStream_t st)
+{
+    const uint32_t n = A.np;
+    if (A.trace && n) cudaMemcpyAsync(A.trace_keys, A.key[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+    if (n == 0) {
+        k_fill_u32<<<grid_for(A.ncells + 1, 256, 4), 256, 0, st>>>(A.cell_start, A.ncells + 1, 0u);
+        return last_err();
+    }
+    const int passes = radix_passes(A.ncells);
+    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    int src = 0;
+    if (passes == 0) {
+        // one cell: the order is unchanged
+        k_iota<<<grid_for(n, 256, 4), 256, 0, st>>>(A.idx[0], n);
+    }
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(A.key[src], n, shift, ntiles, A.radix_hist);
+        if (exclusive_scan<uint32_t, U32Add>(A.radix_hist, (size_t)kRadixBins * ntiles, 0u, U32Add(), A.scan_tmp,
+                                             A.scan_tmp_bytes, st))
+            return -1;
+        k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(A.key[src], p == 0 ? nullptr : A.idx[src], A.key[src ^ 1],
+                                                         A.idx[src ^ 1], n, shift, ntiles, A.radix_hist);
+        src ^= 1;
+    }
+    const unsigned g = grid_for(n, 256, 8);
+    if (A.precision == 1)
+        k_gather<double><<<g, 256, 0, st>>>(A.idx[src], A.key[src], (const double*)A.st[A.cur], (double*)A.st[A.cur ^ 1],
+                                            A.pcap, n, A.cell_start, A.ncells);
+    else
+        k_gather<float><<<g, 256, 0, st>>>(A.idx[src], A.key[src], (const float*)A.st[A.cur], (float*)A.st[A.cur ^ 1],
+                                           A.pcap, n, A.cell_start, A.ncells);
+    A.cur ^= 1;
+    A.sorted_buf = src;
+    return last_err();
+}
+
+int launch_cell_prep(const Arena& A, cudaStream_t st)
+{
+    const unsigned g = grid_for(A.ncells, 256, 8);
+    k_cell_prep<<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.cell_start, A.cell_work, A.acc_count, A.ncells, A.counters, A.stats);
+    if (last_err()) return -1;
+    return exclusive_scan<uint2, Uint2Add>(A.cell_work, (size_t)A.ncells + 1, make_uint2(0, 0), Uint2Add(), A.scan_tmp,
+                                           A.scan_tmp_bytes, st);
+}
+
+int launch_observables(const Arena& A, int sim, double* T00, double* T0x, int32_t* counts, cudaStream_t st)
+{
+    SimDesc S;
+    if (cudaMemcpy(&S, A.d_sims + sim, sizeof(SimDesc), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    const unsigned g = grid_for((uint64_t)S.ncells * 256, 256, 16);
+    if (A.precision == 1)
+        k_observables<double><<<g, 256, 0, st>>>(S, (const double*)A.st[A.cur], A.pcap, A.cell_start, T00, T0x, counts);
+    else
+        k_observables<float><<<g, 256, 0, st>>>(S, (const float*)A.st[A.cur], A.pcap, A.cell_start, T00, T0x, counts);
+    return last_err();
+}
+
+int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st)
+{
+    SimDesc S;
+    if (cudaMemcpy(&S, A.d_sims + sim, sizeof(SimDesc), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    const int nb = 256;
+    double* part = reinterpret_cast<double*>(A.scan_tmp);
+    if (A.scan_tmp_bytes < nb * 4 * sizeof(double)) return -1;
+    if (A.precision == 1)
+        k_totals_partial<double><<<nb, 256, 0, st>>>(S, (const double*)A.st[A.cur], A.pcap, part);
+    else
+        k_totals_partial<float><<<nb, 256, 0, st>>>(S, (const float*)A.st[A.cur], A.pcap, part);
+    k_totals_final<<<1, 32, 0, st>>>(part, nb, d_out4);
+    return last_err();
+}
+
+int launch_advance(const Arena& A, cudaStream_t st)
+{
+    k_advance<<<(A.nsims + 127) / 128, 128, 0, st>>>(A.d_sims, A.nsims, A.stats);
+    return last_err();
+}
+
+int launch_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    const unsigned g = grid_for((uint64_t)n, 256, 8);
+    k_philox<<<g, 256, 0, st>>>(ctr, n, (uint32_t)key, (uint32_t)(key >> 32), out);
+    return last_err();
+}
+
+}  // namespace cuba

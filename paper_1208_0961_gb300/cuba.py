@@ -1,0 +1,325 @@
+"""Python binding of the C ABI in ``include/cuba.h`` (argument marshalling only).
+
+Every entry point keeps its C name.  Device buffers are torch tensors (their
+``data_ptr()`` is passed through); streams are torch CUDA streams.  All work
+runs in ``libcuba.so``; if the library cannot be loaded the import of this
+module's functions raises — there is no other implementation behind them.
+
+Units: fm, fm/c, GeV; cross sections in fm^2 (1 mb = 0.1 fm^2).
+"""
+import ctypes as C
+import os
+
+from . import _build
+
+CUBA_OK = 0
+CUBA_ERR_INVALID = -1
+CUBA_ERR_OOM = -2
+CUBA_ERR_CUDA = -3
+CUBA_ERR_OVERFLOW = -4
+CUBA_ERR_P22 = -5
+CUBA_ERR_CAPACITY = -6
+CUBA_FP32 = 0
+CUBA_FP64 = 1
+
+FM2_PER_MB = 0.1
+
+
+class cuba_params(C.Structure):
+    _fields_ = [
+        ("L", C.c_double * 3),
+        ("n_cells", C.c_int32 * 3),
+        ("dt", C.c_double),
+        ("sigma_fm2", C.c_double),
+        ("n_test", C.c_double),
+        ("precision", C.c_int32),
+        ("seed", C.c_uint64),
+        ("gamma_fp64", C.c_double),
+    ]
+
+
+class cuba_region(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("T", C.c_double)]
+
+
+class cuba_counters(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in
+                ("steps", "pair_tests", "accepted", "executed", "reflections", "fp64_boosts", "overflow",
+                 "reserved")]
+
+
+class CubaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("cuba error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libcuba.so (building it first if asked and missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not os.path.exists(path):
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libcuba.so is not built (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    i64p = C.POINTER(C.c_int64)
+    u32p = C.POINTER(C.c_uint32)
+    sig = {
+        "cuba_create": (C.c_int, [C.POINTER(cuba_params), C.c_int64, C.POINTER(vp)]),
+        "cuba_destroy": (None, [vp]),
+        "cuba_init_thermal": (C.c_int, [vp, C.c_int64, C.POINTER(cuba_region), C.c_int, vp]),
+        "cuba_init_riemann": (C.c_int, [vp, C.c_int64, C.c_double, C.c_double, vp]),
+        "cuba_set_state": (C.c_int, [vp, vp, C.c_int64, vp]),
+        "cuba_get_state": (C.c_int, [vp, vp, vp]),
+        "cuba_sizes": (C.c_int, [vp, i64p, i64p]),
+        "cuba_get_step": (C.c_int, [vp, u32p]),
+        "cuba_set_step": (C.c_int, [vp, C.c_uint32]),
+        "cuba_step": (C.c_int, [vp, C.c_int, vp]),
+        "cuba_observables": (C.c_int, [vp, vp, vp, vp, vp]),
+        "cuba_totals": (C.c_int, [vp, C.POINTER(C.c_double), i64p, vp]),
+        "cuba_stats": (C.c_int, [vp, C.POINTER(cuba_counters)]),
+        "cuba_last_error": (C.c_char_p, []),
+        "cuba_trace_enable": (C.c_int, [vp, C.c_int]),
+        "cuba_trace_get": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int64, i64p]),
+        "cuba_philox": (C.c_int, [vp, C.c_int64, C.c_uint64, vp, vp]),
+        "cuba_step_profiled": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != CUBA_OK:
+        msg = load().cuba_last_error()
+        raise CubaError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (or None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return C.c_void_p(x.ctypes.data)
+    return C.c_void_p(int(x))
+
+
+def make_params(L=(10.0, 1.0, 1.0), n_cells=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_test=1.0,
+                precision=CUBA_FP64, seed=0, gamma_fp64=0.0):
+    p = cuba_params()
+    for a in range(3):
+        p.L[a] = float(L[a])
+        p.n_cells[a] = int(n_cells[a])
+    p.dt = float(dt)
+    p.sigma_fm2 = float(sigma_fm2)
+    p.n_test = float(n_test)
+    p.precision = int(precision)
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.gamma_fp64 = float(gamma_fp64)
+    return p
+
+
+def make_regions(regions):
+    regions = list(regions)
+    arr = (cuba_region * len(regions))()
+    for k, (lo, hi, T) in enumerate(regions):
+        for a in range(3):
+            arr[k].lo[a] = float(lo[a])
+            arr[k].hi[a] = float(hi[a])
+        arr[k].T = float(T)
+    return arr
+
+
+# ---- thin wrappers with the C names ------------------------------------------
+
+def cuba_create(params, max_particles):
+    h = C.c_void_p()
+    _check(load().cuba_create(C.byref(params), int(max_particles), C.byref(h)))
+    return h
+
+
+def cuba_destroy(sim):
+    load().cuba_destroy(sim)
+
+
+def cuba_init_thermal(sim, n, regions, stream=None):
+    R = make_regions(regions)
+    _check(load().cuba_init_thermal(sim, int(n), R, len(R), _stream_ptr(stream)))
+
+
+def cuba_init_riemann(sim, n, T_left, T_right, stream=None):
+    _check(load().cuba_init_riemann(sim, int(n), float(T_left), float(T_right), _stream_ptr(stream)))
+
+
+def cuba_set_state(sim, soa, n, stream=None):
+    _check(load().cuba_set_state(sim, _ptr(soa), int(n), _stream_ptr(stream)))
+
+
+def cuba_get_state(sim, out, stream=None):
+    _check(load().cuba_get_state(sim, _ptr(out), _stream_ptr(stream)))
+
+
+def cuba_sizes(sim):
+    n = C.c_int64()
+    c = C.c_int64()
+    _check(load().cuba_sizes(sim, C.byref(n), C.byref(c)))
+    return n.value, c.value
+
+
+def cuba_get_step(sim):
+    s = C.c_uint32()
+    _check(load().cuba_get_step(sim, C.byref(s)))
+    return s.value
+
+
+def cuba_set_step(sim, step):
+    _check(load().cuba_set_step(sim, int(step)))
+
+
+def cuba_step(sim, n_steps, stream=None):
+    _check(load().cuba_step(sim, int(n_steps), _stream_ptr(stream)))
+
+
+def cuba_step_profiled(sim, n_steps, stream=None):
+    """Per-phase device milliseconds summed over n_steps (see include/cuba.h)."""
+    out = (C.c_double * 6)()
+    _check(load().cuba_step_profiled(sim, int(n_steps), out, _stream_ptr(stream)))
+    return list(out)
+
+
+def cuba_observables(sim, T00=None, T0x=None, counts=None, stream=None):
+    _check(load().cuba_observables(sim, _ptr(T00), _ptr(T0x), _ptr(counts), _stream_ptr(stream)))
+
+
+def cuba_totals(sim, stream=None):
+    out = (C.c_double * 4)()
+    n = C.c_int64()
+    _check(load().cuba_totals(sim, out, C.byref(n), _stream_ptr(stream)))
+    return list(out), n.value
+
+
+def cuba_stats(sim):
+    c = cuba_counters()
+    _check(load().cuba_stats(sim, C.byref(c)))
+    return {name: getattr(c, name) for name, _ in cuba_counters._fields_}
+
+
+def cuba_trace_enable(sim, on=True):
+    _check(load().cuba_trace_enable(sim, 1 if on else 0))
+
+
+def cuba_trace_get(sim, keys=None, perm=None, cell_start=None, pairs=None, executed=None, cap=0):
+    n = C.c_int64()
+    _check(load().cuba_trace_get(sim, _ptr(keys), _ptr(perm), _ptr(cell_start), _ptr(pairs), _ptr(executed),
+                                 int(cap), C.byref(n)))
+    return n.value
+
+
+def cuba_philox(ctr, n, key, out, stream=None):
+    _check(load().cuba_philox(_ptr(ctr), int(n), int(key) & 0xFFFFFFFFFFFFFFFF, _ptr(out), _stream_ptr(stream)))
+
+
+def cuba_last_error():
+    return load().cuba_last_error().decode()
+
+
+# ---- a small object wrapper -------------------------------------------------
+
+class Sim:
+    """Owns one simulation handle; state exchange via numpy (host) arrays."""
+
+    def __init__(self, params, max_particles):
+        self.params = params
+        self.h = cuba_create(params, max_particles)
+        self.dtype = "float64" if params.precision == CUBA_FP64 else "float32"
+
+    def close(self):
+        if self.h:
+            cuba_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_cells(self):
+        return cuba_sizes(self.h)[1]
+
+    @property
+    def n(self):
+        return cuba_sizes(self.h)[0]
+
+    def init_thermal(self, n, regions, stream=None):
+        cuba_init_thermal(self.h, n, regions, stream)
+
+    def init_riemann(self, n, T_left, T_right, stream=None):
+        cuba_init_riemann(self.h, n, T_left, T_right, stream)
+
+    def set_state(self, st, stream=None):
+        import numpy as np
+        st = np.ascontiguousarray(st, dtype=self.dtype)
+        cuba_set_state(self.h, st, st.shape[1], stream)
+
+    def get_state(self, stream=None):
+        import numpy as np
+        out = np.zeros((6, self.n), dtype=self.dtype)
+        cuba_get_state(self.h, out, stream)
+        return out
+
+    def step(self, n_steps=1, stream=None):
+        cuba_step(self.h, n_steps, stream)
+
+    def observables(self, stream=None):
+        import numpy as np
+        nc = self.n_cells
+        T00 = np.zeros(nc)
+        T0x = np.zeros(nc)
+        cnt = np.zeros(nc, dtype=np.int32)
+        cuba_observables(self.h, T00, T0x, cnt, stream)
+        return T00, T0x, cnt
+
+    def totals(self, stream=None):
+        return cuba_totals(self.h, stream)
+
+    def stats(self):
+        return cuba_stats(self.h)
+
+    def trace(self):
+        import numpy as np
+        n, nc = cuba_sizes(self.h)
+        keys = np.zeros(n, dtype=np.uint32)
+        perm = np.zeros(n, dtype=np.uint32)
+        cs = np.zeros(nc + 1, dtype=np.uint32)
+        total = cuba_trace_get(self.h, keys, perm, cs, None, None, 0)
+        pairs = np.zeros((max(total, 1), 3), dtype=np.uint32)
+        exe = np.zeros(max(total, 1), dtype=np.uint8)
+        cuba_trace_get(self.h, None, None, None, pairs, exe, total)
+        return keys, perm, cs, pairs[:total], exe[:total].astype(bool)

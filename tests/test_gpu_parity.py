@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+Bars (per the method's reading of the single-step comparison):
+  * cell keys, sort permutation, cell_start, particle counts: bit-exact;
+  * positions: bit-exact (streaming and reflection are separately rounded
+    IEEE operations on both sides);
+  * accepted pair set and executed (greedy) set: identical in FP64 and in FP32
+    against the oracle's single-precision mirror;
+  * momenta after collisions: |dp|_inf <= 1e-12 (E_i + E_j) in FP64 (only the
+    libm/CUDA sin, cos, log differ), <= 1e-5 (E_i + E_j) in FP32;
+  * observables: relative 1e-12 (FP64 sums in a different order).
+Inputs come from the seeded numpy sampler in paper_1208_0961_gb300.workloads,
+never from the GPU.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1208_0961_gb300 import cuba
+from paper_1208_0961_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0):
+    p = cuba.make_params(L=L, n_cells=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test,
+                         precision=cuba.CUBA_FP32 if fp32 else cuba.CUBA_FP64, seed=seed, gamma_fp64=gamma_fp64)
+    op = O.make_params(L=L, n=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test, fp32=fp32, seed=seed)
+    return p, op
+
+
+def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_index=3):
+    p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed)
+    dtype = np.float32 if fp32 else np.float64
+    st0 = st0.astype(dtype)
+    n = st0.shape[1]
+    sim = cuba.Sim(p, max(n, 1))
+    try:
+        sim.set_state(st0)
+        cuba.cuba_trace_enable(sim.h, True)
+        cuba.cuba_set_step(sim.h, step_index)
+        g_in = sim.get_state()
+        sim.step(1)
+        g_out = sim.get_state()
+        keys, perm, cs, pairs, exe = sim.trace()
+        stats = sim.stats()
+        assert cuba.cuba_get_step(sim.h) == step_index + 1
+    finally:
+        sim.close()
+    # oracle: same input, same stable sort, one step
+    o_in, _, _, _ = O.sort(op, st0.astype(np.float64))
+    assert np.array_equal(g_in.astype(np.float64), o_in), "set_state sort differs"
+    o_out, res = O.step(op, step_index, o_in)
+    assert np.array_equal(keys, res.keys.astype(np.uint32)), "keys differ"
+    assert np.array_equal(perm.astype(np.int64), res.perm), "permutation differs"
+    assert np.array_equal(cs.astype(np.int64), res.cell_start), "cell_start differs"
+    assert np.array_equal(g_out[:3].astype(np.float64), o_out[:3]), "positions differ"
+    acc_o = [tuple(x) for x in res.accepted.tolist()]
+    acc_g = [tuple(x) for x in pairs.tolist()]
+    assert acc_g == acc_o, "accepted pairs differ (%d vs %d)" % (len(acc_g), len(acc_o))
+    exe_o = set(tuple(x) for x in res.executed.tolist())
+    exe_g = set(tuple(x) for x in pairs[exe].tolist())
+    assert exe_g == exe_o, "executed pairs differ"
+    # momenta
+    E = np.sqrt((o_out[3:] ** 2).sum(axis=0))
+    tol = np.zeros(n)
+    for c, i, j in res.executed.tolist():
+        b = res.cell_start[c]
+        s = E[b + i] + E[b + j]
+        tol[b + i] = s
+        tol[b + j] = s
+    rel = 1e-5 if fp32 else 1e-12
+    d = np.abs(g_out[3:].astype(np.float64) - o_out[3:]).max(axis=0)
+    moved = tol > 0
+    assert np.all(d[~moved] == 0), "momenta of non-colliding particles differ"
+    if moved.any():
+        assert np.all(d[moved] <= rel * tol[moved]), "max rel dp %.3g" % (d[moved] / tol[moved]).max()
+    assert stats["accepted"] == len(acc_o)
+    assert stats["executed"] == len(exe_o)
+    assert stats["reflections"] == res.n_reflections
+    assert stats["pair_tests"] == res.n_pairs_tested
+    return len(acc_o), len(exe_o)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_single_step_riemann_small(fp32):
+    cfg = W.riemann_1d(20000, 100, 0.05, 10.0)
+    st0 = W.thermal_state(20000, cfg["regions"], seed=1)
+    na, ne = _one_step_compare(cfg["L"], cfg["n_cells"], cfg["dt"], cfg["sigma_fm2"], cfg["n_test"], fp32, 0, st0)
+    assert na > 1000 and ne > 500
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_single_step_3d_ragged(fp32):
+    L = (1.2, 0.9, 0.6)
+    regs = [((0.0, 0.0, 0.0), L, 0.4)]
+    st0 = W.thermal_state(12345, regs, seed=2)
+    na, ne = _one_step_compare(L, (6, 5, 4), 0.1, 0.02, 3.0, fp32, 77, st0, step_index=11)
+    assert na > 100
+
+
+def test_large_accepted_list_uses_global_sort_path():
+    # one cell, ~10^4 accepted pairs: beyond the shared-memory list size
+    L = (0.5, 0.5, 0.5)
+    regs = [((0.0, 0.0, 0.0), L, 0.4)]
+    st0 = W.thermal_state(2500, regs, seed=3)
+    na, ne = _one_step_compare(L, (1, 1, 1), 0.1, 0.0042, 1.0, False, 5, st0)
+    assert na > 4096
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 33, 4097])
+def test_tiny_and_ragged_sizes(n):
+    L = (1.0, 1.0, 1.0)
+    regs = [((0.0, 0.0, 0.0), L, 0.4)]
+    st0 = W.thermal_state(n, regs, seed=4) if n else np.zeros((6, 0))
+    _one_step_compare(L, (2, 2, 1), 0.2, 0.5, 1.0, False, 9, st0)
+
+
+def test_sigma_zero_is_free_streaming():
+    cfg = W.riemann_1d(5000, 50, 0.05, 0.0)
+    st0 = W.thermal_state(5000, cfg["regions"], seed=5)
+    na, ne = _one_step_compare(cfg["L"], cfg["n_cells"], cfg["dt"], 0.0, cfg["n_test"], False, 0, st0)
+    assert na == 0 and ne == 0
+
+
+def test_init_thermal_matches_oracle_sampling():
+    cfg = W.riemann_1d(30000, 100, 0.05, 10.0)
+    p, op = _pair(cfg["L"], cfg["n_cells"], cfg["dt"], cfg["sigma_fm2"], cfg["n_test"], False, 1234)
+    sim = cuba.Sim(p, 30000)
+    try:
+        sim.init_riemann(30000, 0.4, 0.32)
+        g = sim.get_state()
+        assert cuba.cuba_get_step(sim.h) == 0
+    finally:
+        sim.close()
+    o = O.init_thermal(op, 30000, O.riemann_regions(cfg["L"], 0.4, 0.32))
+    o, _, _, _ = O.sort(op, o)
+    # positions are exact arithmetic; momenta go through log/sin/cos
+    assert np.array_equal(g[:3], o[:3])
+    E = np.sqrt((o[3:] ** 2).sum(axis=0))
+    assert np.max(np.abs(g[3:] - o[3:]).max(axis=0) / E) < 1e-13
+
+
+def test_observables_and_totals_match_oracle():
+    cfg = W.riemann_1d(40000, 100, 0.05, 10.0)
+    p, op = _pair(cfg["L"], cfg["n_cells"], cfg["dt"], cfg["sigma_fm2"], cfg["n_test"], False, 3)
+    st0 = W.thermal_state(40000, cfg["regions"], seed=6)
+    sim = cuba.Sim(p, 40000)
+    try:
+        sim.set_state(st0)
+        sim.step(2)
+        g = sim.get_state()
+        T00, T0x, cnt = sim.observables()
+        tot, n = sim.totals()
+    finally:
+        sim.close()
+    _, _, _, cs = O.sort(op, g.astype(np.float64))
+    oT00, oT0x, ocnt = O.observables(op, g, cs)
+    assert np.array_equal(cnt, ocnt) and cnt.sum() == 40000 and n == 40000
+    assert np.allclose(T00, oT00, rtol=1e-12, atol=0)
+    assert np.allclose(T0x, oT0x, rtol=1e-12, atol=1e-12 * np.abs(oT00).max())
+    ot = O.totals(g)
+    assert abs(tot[0] - ot[0]) <= 1e-12 * ot[0]
+    assert np.max(np.abs(np.array(tot[1:]) - ot[1:])) <= 1e-12 * ot[0]
+
+
+def test_multi_step_energy_conservation_fp64_and_fp32():
+    cfg = W.riemann_1d(20000, 100, 0.05, 10.0)
+    for fp32 in (False, True):
+        p, _ = _pair(cfg["L"], cfg["n_cells"], cfg["dt"], cfg["sigma_fm2"], cfg["n_test"], fp32, 0)
+        sim = cuba.Sim(p, 20000)
+        try:
+            sim.init_riemann(20000, 0.4, 0.32)
+            E0 = sim.totals()[0][0]
+            for _ in range(10):
+                sim.step(10)
+                E1, n = sim.totals()
+                assert n == 20000
+                drift = abs(E1[0] - E0) / E0
+                assert drift < (1e-6 * 100 if fp32 else 1e-12)
+            st = sim.stats()
+            assert st["steps"] == 100 and st["overflow"] == 0 and st["executed"] > 0
+        finally:
+            sim.close()
