@@ -223,7 +223,7 @@ int settle_state(cuba_sim* s, cudaStream_t st)
     Arena& A = s->A;
     if (launch_keys_only(A, st)) return fail(CUBA_ERR_CUDA, "key launch failed");
     if (launch_sort_and_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
-    if (launch_cell_prep(A, st)) return fail(CUBA_ERR_CUDA, "cell preparation failed");
+    if (launch_cell_prep(A, st, 0)) return fail(CUBA_ERR_CUDA, "cell preparation failed");
     uint2 tot;
     CUDA_TRY(cudaMemcpyAsync(&tot, A.cell_work + A.ncells, sizeof(uint2), cudaMemcpyDeviceToHost, st), "read list size");
     CUDA_TRY(cudaStreamSynchronize(st), "sync");

@@ -66,7 +66,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 // Pair tile: one warp per item of 32 rows of one cell.
 constexpr int kPairRows = 32;
 constexpr int kPairThreads = 256;
-constexpr int kQueueCap = 64;         // queued Philox blocks per warp (flush above 32)
+constexpr int kQueueCap = 96;         // queued Philox blocks per warp (resolved 32 at a time)
 
 // Resolve: per-cell accepted lists up to this size are sorted in shared memory.
 constexpr int kResolveThreads = 256;
@@ -134,7 +134,7 @@ int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double*
 int launch_keys_only(const Arena& A, cudaStream_t st);
 int launch_stream_key(const Arena& A, cudaStream_t st);
 int launch_sort_and_bin(Arena& A, cudaStream_t st);   // keys in key[0] -> sorted state, cell_start
-int launch_cell_prep(const Arena& A, cudaStream_t st);
+int launch_cell_prep(const Arena& A, cudaStream_t st, int count_pairs = 1);
 int launch_observables(const Arena& A, int sim, double* T00, double* T0x, int32_t* counts, cudaStream_t st);
 int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st);
 int launch_advance(const Arena& A, cudaStream_t st);

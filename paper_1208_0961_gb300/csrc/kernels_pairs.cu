@@ -59,13 +59,52 @@ __device__ __forceinline__ T pair_p22(T C, const T* __restrict__ st, uint32_t pc
 }
 
 // Nonzero iff some byte of the block is <= thr (thr < 128): a word has a byte
-// below m = thr + 1 iff (x - m * 0x01010101) & ~x & 0x80808080 != 0.
+// below m = thr + 1 iff (x - m * 0x01010101) & ~x & 0x80808080 != 0 (a
+// borrow can only add flags above a true one, so the "any" answer is exact).
 __device__ __forceinline__ uint32_t any_byte_le(uint4 r, uint32_t thr)
 {
     if (thr >= 128u) return 1u;
     const uint32_t t = 0x01010101u * (thr + 1u);
     const uint32_t h = ((r.x - t) & ~r.x) | ((r.y - t) & ~r.y) | ((r.z - t) & ~r.z) | ((r.w - t) & ~r.w);
     return h & 0x80808080u;
+}
+
+// Exact per-byte test of one word: bit b of the result (b = 0..3) is set iff
+// byte b <= thr.  With bit 7 of every byte forced on, subtracting m cannot
+// borrow across bytes; a byte is below m iff the difference drops bit 7 and
+// the byte itself had bit 7 clear.  The four flags are then gathered by one
+// multiply (their shifted copies land on distinct bit positions).
+__device__ __forceinline__ uint32_t word_le_mask(uint32_t x, uint32_t thr)
+{
+    const uint32_t t = 0x01010101u * (thr + 1u);
+    const uint32_t lt = ~((x | 0x80808080u) - t) & ~x & 0x80808080u;
+    return (((lt >> 7) * 0x00204081u) >> 21) & 0xFu;
+}
+
+// 16-bit mask of the bytes <= thr of a block (bit 4 w + b = byte b of word w).
+__device__ __forceinline__ uint32_t block_le_mask(uint4 r, uint32_t thr)
+{
+    if (thr >= 128u) return 0xFFFFu;
+    return word_le_mask(r.x, thr) | (word_le_mask(r.y, thr) << 4) | (word_le_mask(r.z, thr) << 8) |
+           (word_le_mask(r.w, thr) << 12);
+}
+
+// Columns j = 16 g + b of row i that are real pairs (i < j < n), as a mask.
+__device__ __forceinline__ uint32_t valid_cols(uint32_t g, uint32_t i, uint32_t n)
+{
+    const int base = (int)(16u * g);
+    int lo = (int)i + 1 - base;
+    int hi = (int)n - base;
+    lo = lo < 0 ? 0 : (lo > 16 ? 16 : lo);
+    hi = hi < 0 ? 0 : (hi > 16 ? 16 : hi);
+    if (hi <= lo) return 0u;
+    return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+}
+
+__device__ __forceinline__ uint32_t block_byte(uint4 r, uint32_t bit)
+{
+    const uint32_t w = (bit >> 2) == 0 ? r.x : (bit >> 2) == 1 ? r.y : (bit >> 2) == 2 ? r.z : r.w;
+    return (w >> (8u * (bit & 3u))) & 0xFFu;
 }
 
 struct CellCtx {
@@ -78,40 +117,40 @@ struct CellCtx {
     int s;            // simulation
 };
 
+// Resolve queued blocks [e0, e1) of the warp, one block per lane: the exact
+// bytes <= thr8 at real pairs j (i < j < n) are the candidates; for each, the
+// low 24 bits of u_ij come from the second Philox block, P22 from the momenta,
+// and accepted pairs are appended to the cell's list.
 template <typename T>
-__device__ __forceinline__ void resolve_candidates(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
-                                                   T C, const T* __restrict__ st, uint32_t pcap,
-                                                   const uint4* qw, const uint32_t* qi, const uint32_t* qg, uint32_t qn,
-                                                   uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
-                                                   uint64_t acc_cap, uint32_t* __restrict__ counters,
-                                                   uint32_t* __restrict__ active, unsigned long long* __restrict__ stats)
+__device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
+                                               T C, const T* __restrict__ st, uint32_t pcap, const uint4* qw,
+                                               const uint32_t* qi, const uint32_t* qg, uint32_t e0, uint32_t e1,
+                                               uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
+                                               uint64_t acc_cap, uint32_t* __restrict__ counters,
+                                               uint32_t* __restrict__ active, unsigned long long* __restrict__ stats)
 {
-    const int lane = threadIdx.x & 31;
-    for (uint32_t e = lane; e < qn; e += 32) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t e = e0 + lane; e < e1; e += 32) {
         const uint4 r = qw[e];
         const uint32_t i = qi[e], g = qg[e];
-        const uint32_t words[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int wi = 0; wi < 4; ++wi) {
-#pragma unroll
-            for (int bi = 0; bi < 4; ++bi) {
-                const uint32_t b = (words[wi] >> (8 * bi)) & 0xFFu;
-                const uint32_t j = 16u * g + 4u * wi + bi;
-                if (b <= thr8 && j > i && j < cc.n) {
-                    const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
-                    const uint32_t rw = (b << 24) | (fine >> 8);
-                    const T u = unit_u<T>(rw);
-                    const T P = pair_p22<T>(C, st, pcap, cc.cbase + i, cc.cbase + j);
-                    if (u < P) {
-                        const uint32_t slot = atomicAdd(&acc_count[cc.c], 1u);
-                        if (slot == 0) active[atomicAdd(&counters[2], 1u)] = cc.c;
-                        if (slot < cc.room && (uint64_t)cc.list0 + slot < acc_cap) {
-                            acc[(size_t)cc.list0 + slot] = ((unsigned long long)i << 32) | j;
-                        } else {
-                            atomicOr(&counters[1], kErrAccOverflow);
-                            atomicAdd(&stats[cc.s * kStatCount + kStatOverflow], 1ull);
-                        }
-                    }
+        uint32_t m = block_le_mask(r, thr8) & valid_cols(g, i, cc.n);
+        while (m) {
+            const uint32_t bit = (uint32_t)__ffs(m) - 1u;
+            m &= m - 1u;
+            const uint32_t j = 16u * g + bit;
+            const uint32_t b = block_byte(r, bit);
+            const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
+            const uint32_t rw = (b << 24) | (fine >> 8);
+            const T u = unit_u<T>(rw);
+            const T P = pair_p22<T>(C, st, pcap, cc.cbase + i, cc.cbase + j);
+            if (u < P) {
+                const uint32_t slot = atomicAdd(&acc_count[cc.c], 1u);
+                if (slot == 0) active[atomicAdd(&counters[2], 1u)] = cc.c;
+                if (slot < cc.room && (uint64_t)cc.list0 + slot < acc_cap) {
+                    acc[(size_t)cc.list0 + slot] = ((unsigned long long)i << 32) | j;
+                } else {
+                    atomicOr(&counters[1], kErrAccOverflow);
+                    atomicAdd(&stats[cc.s * kStatCount + kStatOverflow], 1ull);
                 }
             }
         }
@@ -129,10 +168,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_tile(const SimDesc* __res
                                                             unsigned long long* __restrict__ stats)
 {
     constexpr int kWarps = kPairThreads / 32;
+    static_assert(kQueueCap >= 96, "a warp pushes up to 64 blocks onto at most 32 queued ones");
     __shared__ uint4 q_w[kWarps][kQueueCap];
     __shared__ uint32_t q_i[kWarps][kQueueCap];
     __shared__ uint32_t q_g[kWarps][kQueueCap];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t total = work[ncells].x;
     if ((uint64_t)work[ncells].y > acc_cap) {
@@ -180,34 +221,49 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_tile(const SimDesc* __res
 
         const uint32_t i = rb * kPairRows + lane;
         const bool row_ok = i + 1 < cc.n;
+        PhiloxRow R;
+        R.init(step, cc.lc, i, K);
         const uint32_t gfirst = (rb * kPairRows + 1) >> 4;
         const uint32_t glast = (cc.n - 1) >> 4;
-        uint32_t qn = 0;
-        for (uint32_t g = gfirst; g <= glast; ++g) {
-            const uint4 r = philox4x32_10(make_uint4(step, cc.lc, i, g), K);
-            const uint32_t hit = row_ok ? any_byte_le(r, thr8) : 0u;
-            const unsigned ball = __ballot_sync(kFull, hit != 0u);
-            if (ball) {
-                if (qn + 32 > (uint32_t)kQueueCap) {
+        uint32_t qn = 0;  // warp-uniform number of queued blocks
+        for (uint32_t g = gfirst; g <= glast; g += 2) {
+            const bool two = g + 1 <= glast;
+            const uint4 r0 = R.block(g, K);
+            const uint4 r1 = two ? R.block(g + 1, K)
+                                 : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+            const bool h0 = row_ok && any_byte_le(r0, thr8);
+            const bool h1 = row_ok && any_byte_le(r1, thr8);
+            const unsigned b0 = __ballot_sync(kFull, h0);
+            const unsigned b1 = __ballot_sync(kFull, h1);
+            if (b0 | b1) {
+                // up to 64 blocks are pushed below: drain to at most 32 first
+                while (qn > (uint32_t)(kQueueCap - 64)) {
                     __syncwarp();
-                    resolve_candidates<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], qn, acc_count, acc,
-                                          acc_cap, counters, active, stats);
+                    resolve_blocks<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], qn - 32, qn, acc_count,
+                                      acc, acc_cap, counters, active, stats);
                     __syncwarp();
-                    qn = 0;
+                    qn -= 32;
                 }
-                if (hit) {
-                    const uint32_t slot = qn + (uint32_t)__popc(ball & lt);
-                    q_w[w][slot] = r;
+                if (h0) {
+                    const uint32_t slot = qn + (uint32_t)__popc(b0 & lt);
+                    q_w[w][slot] = r0;
                     q_i[w][slot] = i;
                     q_g[w][slot] = g;
                 }
-                qn += (uint32_t)__popc(ball);
+                qn += (uint32_t)__popc(b0);
+                if (h1) {
+                    const uint32_t slot = qn + (uint32_t)__popc(b1 & lt);
+                    q_w[w][slot] = r1;
+                    q_i[w][slot] = i;
+                    q_g[w][slot] = g + 1;
+                }
+                qn += (uint32_t)__popc(b1);
             }
         }
         if (qn) {
             __syncwarp();
-            resolve_candidates<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], qn, acc_count, acc, acc_cap,
-                                  counters, active, stats);
+            resolve_blocks<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], 0, qn, acc_count, acc, acc_cap,
+                              counters, active, stats);
             __syncwarp();
         }
     }

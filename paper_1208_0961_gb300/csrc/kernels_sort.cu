@@ -407,7 +407,8 @@ __device__ __forceinline__ uint32_t list_room(double C, uint32_t n)
 __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ sims, int nsims,
                                                    const uint32_t* __restrict__ cell_start, uint2* __restrict__ work,
                                                    uint32_t* __restrict__ acc_count, uint32_t ncells,
-                                                   uint32_t* __restrict__ counters, unsigned long long* __restrict__ stats)
+                                                   uint32_t* __restrict__ counters, unsigned long long* __restrict__ stats,
+                                                   int count_pairs)
 {
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
         if (n >= 2 && S.C > 0.0) {
             items = (n - 1 + kPairRows - 1) / kPairRows;
             room = list_room(S.C, n);
-            atomicAdd(&stats[s * kStatCount + kStatPairTests], (unsigned long long)n * (n - 1) / 2);
+            if (count_pairs) atomicAdd(&stats[s * kStatCount + kStatPairTests], (unsigned long long)n * (n - 1) / 2);
         }
         work[c] = make_uint2(items, room);
         acc_count[c] = 0;
@@ -625,10 +626,11 @@ int launch_sort_and_bin(Arena& A, cudaStream_t st)
     return last_err();
 }
 
-int launch_cell_prep(const Arena& A, cudaStream_t st)
+int launch_cell_prep(const Arena& A, cudaStream_t st, int count_pairs)
 {
     const unsigned g = grid_for(A.ncells, 256, 8);
-    k_cell_prep<<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.cell_start, A.cell_work, A.acc_count, A.ncells, A.counters, A.stats);
+    k_cell_prep<<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.cell_start, A.cell_work, A.acc_count, A.ncells, A.counters, A.stats,
+                                   count_pairs);
     if (last_err()) return -1;
     return exclusive_scan<uint2, Uint2Add>(A.cell_work, (size_t)A.ncells + 1, make_uint2(0, 0), Uint2Add(), A.scan_tmp,
                                            A.scan_tmp_bytes, st);
