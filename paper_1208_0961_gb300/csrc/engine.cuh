@@ -66,7 +66,11 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 // Pair tile: one warp per item of 32 rows of one cell.
 constexpr int kPairRows = 32;
 constexpr int kPairThreads = 256;
-constexpr int kQueueCap = 96;         // queued Philox blocks per warp (resolved 32 at a time)
+constexpr int kPairBlocksPerIter = 2; // Philox blocks each lane draws per loop iteration
+#ifndef CUBA_PAIR_MIN_BLOCKS
+#define CUBA_PAIR_MIN_BLOCKS 0        // > 0: resident blocks per SM the register budget targets
+#endif
+constexpr int kQueueCap = 32 + 32 * kPairBlocksPerIter;  // queued Philox blocks per warp
 
 // Resolve: per-cell accepted lists up to this size are sorted in shared memory.
 constexpr int kResolveThreads = 256;

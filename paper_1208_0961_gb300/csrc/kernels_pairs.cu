@@ -157,8 +157,14 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
     }
 }
 
+#if CUBA_PAIR_MIN_BLOCKS > 0
+#define CUBA_PAIR_BOUNDS __launch_bounds__(kPairThreads, CUBA_PAIR_MIN_BLOCKS)
+#else
+#define CUBA_PAIR_BOUNDS __launch_bounds__(kPairThreads)
+#endif
+
 template <typename T>
-__global__ void __launch_bounds__(kPairThreads) k_pair_tile(const SimDesc* __restrict__ sims, int nsims,
+__global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, int nsims,
                                                             const T* __restrict__ st, uint32_t pcap,
                                                             const uint32_t* __restrict__ cell_start,
                                                             const uint2* __restrict__ work, uint32_t ncells,
@@ -168,7 +174,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_tile(const SimDesc* __res
                                                             unsigned long long* __restrict__ stats)
 {
     constexpr int kWarps = kPairThreads / 32;
-    static_assert(kQueueCap >= 96, "a warp pushes up to 64 blocks onto at most 32 queued ones");
+    constexpr int NB = kPairBlocksPerIter;
+    static_assert(kQueueCap >= 32 + 32 * NB, "a warp pushes up to 32 NB blocks onto at most 32 queued ones");
     __shared__ uint4 q_w[kWarps][kQueueCap];
     __shared__ uint32_t q_i[kWarps][kQueueCap];
     __shared__ uint32_t q_g[kWarps][kQueueCap];
@@ -226,38 +233,38 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_tile(const SimDesc* __res
         const uint32_t gfirst = (rb * kPairRows + 1) >> 4;
         const uint32_t glast = (cc.n - 1) >> 4;
         uint32_t qn = 0;  // warp-uniform number of queued blocks
-        for (uint32_t g = gfirst; g <= glast; g += 2) {
-            const bool two = g + 1 <= glast;
-            const uint4 r0 = R.block(g, K);
-            const uint4 r1 = two ? R.block(g + 1, K)
-                                 : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-            const bool h0 = row_ok && any_byte_le(r0, thr8);
-            const bool h1 = row_ok && any_byte_le(r1, thr8);
-            const unsigned b0 = __ballot_sync(kFull, h0);
-            const unsigned b1 = __ballot_sync(kFull, h1);
-            if (b0 | b1) {
-                // up to 64 blocks are pushed below: drain to at most 32 first
-                while (qn > (uint32_t)(kQueueCap - 64)) {
+        for (uint32_t g = gfirst; g <= glast; g += NB) {
+            uint4 r[NB];
+            bool h[NB];
+            unsigned bal[NB];
+            unsigned any = 0;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                r[q] = (g + q <= glast) ? R.block(g + q, K)
+                                        : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+                h[q] = row_ok && any_byte_le(r[q], thr8);
+                bal[q] = __ballot_sync(kFull, h[q]);
+                any |= bal[q];
+            }
+            if (any) {
+                // up to 32 NB blocks are pushed below: drain to at most 32 first
+                while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
                     __syncwarp();
                     resolve_blocks<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], qn - 32, qn, acc_count,
                                       acc, acc_cap, counters, active, stats);
                     __syncwarp();
                     qn -= 32;
                 }
-                if (h0) {
-                    const uint32_t slot = qn + (uint32_t)__popc(b0 & lt);
-                    q_w[w][slot] = r0;
-                    q_i[w][slot] = i;
-                    q_g[w][slot] = g;
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    if (h[q]) {
+                        const uint32_t slot = qn + (uint32_t)__popc(bal[q] & lt);
+                        q_w[w][slot] = r[q];
+                        q_i[w][slot] = i;
+                        q_g[w][slot] = g + q;
+                    }
+                    qn += (uint32_t)__popc(bal[q]);
                 }
-                qn += (uint32_t)__popc(b0);
-                if (h1) {
-                    const uint32_t slot = qn + (uint32_t)__popc(b1 & lt);
-                    q_w[w][slot] = r1;
-                    q_i[w][slot] = i;
-                    q_g[w][slot] = g + 1;
-                }
-                qn += (uint32_t)__popc(b1);
             }
         }
         if (qn) {
