@@ -196,6 +196,36 @@ int cuba_step_profiled(cuba_sim* sim, int n_steps, double* phase_ms, void* strea
  */
 int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, void* stream);
 
+/*
+ * Cell keys and stable sort of particle positions without allocating memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory themselves -- code running inside a region
+ * that forbids allocation (a frame budget of a real-time loop, a memory pool
+ * that must not grow, a caller that has no CUDA allocator of its own) -- and
+ * still want the binning step (A3, A4) of the library.
+ *
+ * params: as for cuba_create (host struct; checked the same way).
+ * xyz: device, SoA positions x[n], y[n], z[n] of the params' precision.
+ * perm: device, n uint32 out: perm[k] = input index of the particle at sorted
+ * position k (stable within a cell).  cell_start: device, n_cells + 1 uint32
+ * out: first sorted position of each cell, cell_start[n_cells] = n.
+ * Async on `stream`.
+ *
+ * No cudaMalloc, cudaFree or allocating library call is made.  All scratch
+ * lives in one fixed device array inside the library, sized for
+ * CUBA_NOALLOC_MAX_PARTICLES particles (about 4 MiB); every GPU that loads the
+ * library holds it until the process exits.  n above the maximum fails with
+ * CUBA_ERR_CAPACITY before any GPU work.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress), which may load the
+ * library's device code; make that first call before any stream capture.
+ * Every call on a device shares the one array: calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and corrupt each other's
+ * results; serialise them.
+ */
+#define CUBA_NOALLOC_MAX_PARTICLES (1 << 18)
+int cuba_bin_noalloc(const cuba_params* params, const void* xyz, int64_t n, uint32_t* perm,
+                     uint32_t* cell_start, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

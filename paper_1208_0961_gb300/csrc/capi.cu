@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -644,3 +645,70 @@ int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, voi
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Binning without allocation
+// ---------------------------------------------------------------------------
+// Scratch of cuba_bin_noalloc: a file-scope device array of fixed size that
+// every GPU loading the library holds until exit.  Layout in 32-bit words:
+// keys (2 x max), permutation ping-pong (2 x max), radix histogram
+// (256 x tiles), scan partial sums.
+namespace {
+constexpr uint32_t kNoallocMax = CUBA_NOALLOC_MAX_PARTICLES;
+constexpr uint32_t kNoallocTiles = (kNoallocMax + kSortTile - 1) / kSortTile;
+constexpr size_t kNoallocPartialWords = 1024;
+constexpr size_t kNoallocWords = 4ull * kNoallocMax + (size_t)kRadixBins * kNoallocTiles + kNoallocPartialWords;
+}  // namespace
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocWords];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+uint32_t* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device; looked up once
+// per device (the host-side name of the array is not a device address).
+int noalloc_scratch(uint32_t** out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(CUBA_ERR_INVALID, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return CUBA_OK;
+}
+}  // namespace
+
+extern "C" int cuba_bin_noalloc(const cuba_params* params, const void* xyz, int64_t n, uint32_t* perm,
+                                uint32_t* cell_start, void* stream)
+{
+    SimDesc S;
+    int rc = make_desc(params, &S);
+    if (rc) return rc;
+    if (n < 0) return fail(CUBA_ERR_INVALID, "n must be >= 0");
+    if (n > (int64_t)kNoallocMax)
+        return fail(CUBA_ERR_CAPACITY, "cuba_bin_noalloc handles at most %u particles (got %lld)", kNoallocMax,
+                    (long long)n);
+    if (!cell_start || (n > 0 && (!xyz || !perm))) return fail(CUBA_ERR_INVALID, "NULL buffer");
+    uint32_t* scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    const uint32_t m = kNoallocMax;
+    uint32_t* key_a = scratch;
+    uint32_t* key_b = scratch + m;
+    uint32_t* idx_a = scratch + 2ull * m;
+    uint32_t* idx_b = scratch + 3ull * m;
+    uint32_t* hist = scratch + 4ull * m;
+    void* partials = scratch + 4ull * m + (size_t)kRadixBins * kNoallocTiles;
+    S.np = (uint32_t)n;
+    if (launch_bin_raw(S, params->precision, xyz, (uint32_t)n, key_a, key_b, idx_a, idx_b, hist, partials,
+                       kNoallocPartialWords * sizeof(uint32_t), perm, cell_start, (cudaStream_t)stream))
+        return fail(CUBA_ERR_CUDA, "binning launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return CUBA_OK;
+}

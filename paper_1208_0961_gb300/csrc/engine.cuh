@@ -143,6 +143,9 @@ int launch_observables(const Arena& A, int sim, double* T00, double* T0x, int32_
 int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st);
 int launch_advance(const Arena& A, cudaStream_t st);
 int launch_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, cudaStream_t st);
+int launch_bin_raw(const SimDesc& S, int precision, const void* xyz, uint32_t n, uint32_t* key_a, uint32_t* key_b,
+                   uint32_t* idx_a, uint32_t* idx_b, uint32_t* hist, void* partials, size_t partial_bytes,
+                   uint32_t* perm, uint32_t* cell_start, cudaStream_t st);
 
 // ---- launchers (kernels_pairs.cu) ----
 int launch_pair_tile(const Arena& A, cudaStream_t st);

@@ -526,6 +526,32 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, int64_t n, uint32_t k
     }
 }
 
+// Cell keys of caller-owned positions (SoA x, y, z of one simulation).
+template <typename T>
+__global__ void __launch_bounds__(256) k_keys_raw(SimDesc S, const T* __restrict__ xyz, uint32_t n,
+                                                  uint32_t* __restrict__ keys)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+        T pos[3] = {xyz[g], xyz[(size_t)n + g], xyz[2 * (size_t)n + g]};
+        keys[g] = cell_key<T>(S, pos);
+    }
+}
+
+// cell_start[c] = first sorted position with key >= c (keys sorted).
+__global__ void __launch_bounds__(256) k_cell_bounds(const uint32_t* __restrict__ skey, uint32_t np,
+                                                     uint32_t* __restrict__ cell_start, uint32_t ncells)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
+        const uint32_t kk = skey[k];
+        const int64_t prev = (k == 0) ? -1 : (int64_t)skey[k - 1];
+        for (int64_t c = prev + 1; c <= (int64_t)kk; ++c) cell_start[c] = k;
+        if (k == np - 1)
+            for (int64_t c = (int64_t)kk + 1; c <= (int64_t)ncells; ++c) cell_start[c] = np;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -666,6 +692,45 @@ int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st)
 int launch_advance(const Arena& A, cudaStream_t st)
 {
     k_advance<<<(A.nsims + 127) / 128, 128, 0, st>>>(A.d_sims, A.nsims, A.stats);
+    return last_err();
+}
+
+// Keys and stable counting sort of caller-owned positions with caller-given
+// scratch (no allocation): key_a/key_b/idx_a/idx_b hold n words each, hist
+// 256 * ceil(n / 4096) words, partials partial_bytes.  perm and cell_start
+// are outputs.
+int launch_bin_raw(const SimDesc& S, int precision, const void* xyz, uint32_t n, uint32_t* key_a, uint32_t* key_b,
+                   uint32_t* idx_a, uint32_t* idx_b, uint32_t* hist, void* partials, size_t partial_bytes,
+                   uint32_t* perm, uint32_t* cell_start, cudaStream_t st)
+{
+    if (n == 0) {
+        k_fill_u32<<<grid_for((uint64_t)S.ncells + 1, 256, 4), 256, 0, st>>>(cell_start, S.ncells + 1, 0u);
+        return last_err();
+    }
+    const unsigned g = grid_for(n, 256, 8);
+    if (precision == 1)
+        k_keys_raw<double><<<g, 256, 0, st>>>(S, (const double*)xyz, n, key_a);
+    else
+        k_keys_raw<float><<<g, 256, 0, st>>>(S, (const float*)xyz, n, key_a);
+    const int passes = radix_passes(S.ncells);
+    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    uint32_t* keys[2] = {key_a, key_b};
+    uint32_t* idx[2] = {idx_a, idx_b};
+    int src = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(keys[src], n, shift, ntiles, hist);
+        if (exclusive_scan<uint32_t, U32Add>(hist, (size_t)kRadixBins * ntiles, 0u, U32Add(), partials, partial_bytes, st))
+            return -1;
+        k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(keys[src], p == 0 ? nullptr : idx[src], keys[src ^ 1],
+                                                         idx[src ^ 1], n, shift, ntiles, hist);
+        src ^= 1;
+    }
+    if (passes == 0)
+        k_iota<<<grid_for(n, 256, 4), 256, 0, st>>>(perm, n);
+    else if (cudaMemcpyAsync(perm, idx[src], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return -1;
+    k_cell_bounds<<<g, 256, 0, st>>>(keys[src], n, cell_start, S.ncells);
     return last_err();
 }
 

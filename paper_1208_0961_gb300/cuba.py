@@ -94,6 +94,7 @@ def load(build_if_missing=True):
         "cuba_trace_get": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int64, i64p]),
         "cuba_philox": (C.c_int, [vp, C.c_int64, C.c_uint64, vp, vp]),
         "cuba_step_profiled": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), vp]),
+        "cuba_bin_noalloc": (C.c_int, [C.POINTER(cuba_params), vp, C.c_int64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -242,6 +243,16 @@ def cuba_trace_get(sim, keys=None, perm=None, cell_start=None, pairs=None, execu
 
 def cuba_philox(ctr, n, key, out, stream=None):
     _check(load().cuba_philox(_ptr(ctr), int(n), int(key) & 0xFFFFFFFFFFFFFFFF, _ptr(out), _stream_ptr(stream)))
+
+
+CUBA_NOALLOC_MAX_PARTICLES = 1 << 18
+
+
+def cuba_bin_noalloc(params, xyz, n, perm, cell_start, stream=None):
+    """Cell keys and stable sort of device positions into caller buffers,
+    with no allocation inside the library (see include/cuba.h)."""
+    _check(load().cuba_bin_noalloc(C.byref(params), _ptr(xyz), int(n), _ptr(perm), _ptr(cell_start),
+                                   _stream_ptr(stream)))
 
 
 def cuba_last_error():
