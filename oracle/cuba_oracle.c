@@ -103,7 +103,8 @@ static void philox(uint32_t a, uint32_t b, uint32_t c, uint32_t d, const uint32_
 }
 
 /* Counter tags of the random streams (fourth counter word).                 */
-#define TAG_FINE 0x40000000u   /* acceptance: low 24 bits of u_ij          */
+#define TAG_MID 0x20000000u    /* acceptance: bits 23..16 of u_ij           */
+#define TAG_FINE 0x40000000u   /* acceptance: low 16 bits of u_ij           */
 #define TAG_ANGLE 0x80000000u  /* kinematics: CM-frame direction           */
 #define STEP_INIT 0xFFFFFFFFu  /* first counter word reserved for sampling */
 
@@ -386,20 +387,23 @@ int orc_sort(const orc_params *p, int64_t n, double *st, uint32_t *keys_out, int
 
 /*
  * The 32-bit word r_ij behind u_ij = r_ij 2^-32 of pair (i, j), i < j, of a
- * cell.  Its top byte is byte (j mod 16) of the Philox block with counter
- * (step, cell, i, j / 16), taken little-endian across the four output words;
- * its low 24 bits are the top 24 bits of word 0 of the block with counter
- * (step, cell, i, TAG_FINE | j).  Both parts are uniform and independent, so
- * r_ij is a uniform 32-bit word.
+ * cell, assembled from three independent Philox streams (the paper only says
+ * "Monte-Carlo"; this layout is the library's reading):
+ *   bits 31..24: byte (j mod 16) of the block (step, cell, i, j / 16),
+ *   bits 23..16: byte (j mod 16) of the block (step, cell, i, TAG_MID | j / 16),
+ *   bits 15..0:  the top 16 bits of word 0 of the block (step, cell, i, TAG_FINE | j),
+ * bytes numbered little-endian across the four output words.  The three parts
+ * are independent uniforms, so r_ij is a uniform 32-bit word.
  */
 uint32_t orc_pair_word(const uint32_t key[2], uint32_t step, uint32_t cell, uint32_t i, uint32_t j)
 {
-    uint32_t a[4], b[4];
+    uint32_t a[4], m[4], b[4];
     philox(step, cell, i, j >> 4, key, a);
-    uint32_t w = a[(j >> 2) & 3u];
-    uint32_t top = (w >> (8u * (j & 3u))) & 0xFFu;
+    philox(step, cell, i, TAG_MID | (j >> 4), key, m);
+    uint32_t top = (a[(j >> 2) & 3u] >> (8u * (j & 3u))) & 0xFFu;
+    uint32_t mid = (m[(j >> 2) & 3u] >> (8u * (j & 3u))) & 0xFFu;
     philox(step, cell, i, TAG_FINE | j, key, b);
-    return (top << 24) | (b[0] >> 8);
+    return (top << 24) | (mid << 16) | (b[0] >> 16);
 }
 
 /* Unit direction p/E of a massless particle (zero vector if p = 0). */

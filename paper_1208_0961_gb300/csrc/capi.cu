@@ -80,6 +80,7 @@ int make_desc(const cuba_params* p, SimDesc* S)
     // A top byte above thr8 proves u >= (thr8 + 1) / 256 > 2.0001 C >= P22.
     const double pb = 2.0001 * S->C;
     S->thr8 = (pb >= 0.5) ? 256u : (uint32_t)std::floor(pb * 256.0);
+    S->thr16 = (pb >= 1.0) ? 65536u : (uint32_t)std::floor(pb * 65536.0);
     S->gamma_fp64 = (float)(p->gamma_fp64 > 0.0 ? p->gamma_fp64 : kDefaultGammaFp64);
     S->step = 0;
     return CUBA_OK;

@@ -32,6 +32,7 @@ struct SimDesc {
     double norm;      // n_test V_cell: T^00 = sum E / norm
     uint32_t key0, key1;
     uint32_t thr8;    // top byte above thr8 rejects a pair outright; 256 = never
+    uint32_t thr16;   // top 16 bits above thr16 reject a pair; 65536 = never
     float gamma_fp64; // FP32 path: CM boosts with gamma above this use FP64
 };
 

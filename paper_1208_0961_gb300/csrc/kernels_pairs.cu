@@ -1,17 +1,20 @@
 // Cell-parallel kernels of the collision step.
 //
 // k_pair_tile (A5): every pair i < j of every cell is tested against
-// P22 = C v_rel (Eq. 3).  The uniform u_ij = r_ij 2^-32 of a pair has its top
-// byte taken from the Philox block (step, cell, i, j / 16) — one block serves
-// sixteen pairs of a row — and its low 24 bits from the block
-// (step, cell, i, TAG_FINE | j).  Because P22 <= 2 C (1 + tiny) for every
-// pair, a top byte above thr8 = floor(2.0001 C 256) already proves
-// u_ij >= P22: such pairs are rejected from the first block alone, without
-// loading momenta; only the rare survivors (top byte <= thr8) evaluate the
-// second block and P22.  The decision is the same as testing every pair in
-// full.  Work unit: one warp takes 32 rows of one cell (lane = row) and walks
-// the row's column blocks; survivors are queued per warp in shared memory and
-// resolved together.  Accepted pairs go to the cell's segment of the list.
+// P22 = C v_rel (Eq. 3).  The uniform u_ij = r_ij 2^-32 of a pair is built
+// from three Philox streams: its top byte from the block (step, cell, i, j/16)
+// — one block serves sixteen pairs of a row — its next byte from the block
+// (step, cell, i, TAG_MID | j/16), its low 16 bits from the block
+// (step, cell, i, TAG_FINE | j).  Because P22 <= 2 C (1 + tiny) for every pair,
+// a top byte above thr8 = floor(2.0001 C 256) already proves u_ij >= P22, and
+// so does a 16-bit prefix above thr16 = floor(2.0001 C 65536): 255/256 of the
+// pairs are rejected from the first block alone, without momenta, and most of
+// the rest by the second; only the rare survivors draw the third block and
+// evaluate P22.  The decision is the same as testing every pair in full.
+// Work unit: one warp takes 32 rows of one cell (lane = row) and walks the
+// row's column blocks; blocks with a small byte are queued per warp in shared
+// memory and resolved together, one block per lane.  Accepted pairs go to the
+// cell's segment of the list.
 //
 // k_resolve (A6, A7): per cell with accepted pairs — sort the list
 // lexicographically (bitonic network in shared memory), take the greedy
@@ -117,30 +120,37 @@ struct CellCtx {
     int s;            // simulation
 };
 
-// Resolve queued blocks [e0, e1) of the warp, one block per lane: the exact
-// bytes <= thr8 at real pairs j (i < j < n) are the candidates; for each, the
-// low 24 bits of u_ij come from the second Philox block, P22 from the momenta,
-// and accepted pairs are appended to the cell's list.
+// Resolve queued blocks [e0, e1) of the warp, one block per lane.  The bytes
+// <= thr8 at real pairs j (i < j < n) are first refined by the pair's middle
+// byte, drawn from the block (step, cell, i, TAG_MID | g) shared by the 16
+// pairs of the group: a 16-bit prefix above thr16 also proves u_ij >= P22.
+// Only the rare survivors draw their low 16 bits (block (step, cell, i,
+// TAG_FINE | j)), load momenta and evaluate P22; accepted pairs are appended
+// to the cell's list.
 template <typename T>
 __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
-                                               T C, const T* __restrict__ st, uint32_t pcap, const uint4* qw,
-                                               const uint32_t* qi, const uint32_t* qg, uint32_t e0, uint32_t e1,
-                                               uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
-                                               uint64_t acc_cap, uint32_t* __restrict__ counters,
-                                               uint32_t* __restrict__ active, unsigned long long* __restrict__ stats)
+                                               uint32_t thr16, T C, const T* __restrict__ st, uint32_t pcap,
+                                               const uint4* qw, const uint32_t* qi, const uint32_t* qg, uint32_t e0,
+                                               uint32_t e1, uint32_t* __restrict__ acc_count,
+                                               unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                               uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                               unsigned long long* __restrict__ stats)
 {
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t e = e0 + lane; e < e1; e += 32) {
         const uint4 r = qw[e];
         const uint32_t i = qi[e], g = qg[e];
         uint32_t m = block_le_mask(r, thr8) & valid_cols(g, i, cc.n);
+        if (!m) continue;
+        const uint4 mb = philox4x32_10(make_uint4(step, cc.lc, i, kTagMid | g), K);
         while (m) {
             const uint32_t bit = (uint32_t)__ffs(m) - 1u;
             m &= m - 1u;
+            const uint32_t r16 = (block_byte(r, bit) << 8) | block_byte(mb, bit);
+            if (r16 > thr16) continue;
             const uint32_t j = 16u * g + bit;
-            const uint32_t b = block_byte(r, bit);
             const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
-            const uint32_t rw = (b << 24) | (fine >> 8);
+            const uint32_t rw = (r16 << 16) | (fine >> 16);
             const T u = unit_u<T>(rw);
             const T P = pair_p22<T>(C, st, pcap, cc.cbase + i, cc.cbase + j);
             if (u < P) {
@@ -222,7 +232,7 @@ __global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, i
         cc.list0 = w0.y;
         cc.room = w1.y - w0.y;
         const uint32_t rb = item - w0.x;
-        const uint32_t step = S.step, thr8 = S.thr8;
+        const uint32_t step = S.step, thr8 = S.thr8, thr16 = S.thr16;
         const T C = sim_C<T>(S);
         const PhiloxKey K = philox_schedule(S.key0, S.key1);
 
@@ -250,7 +260,7 @@ __global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, i
                 // up to 32 NB blocks are pushed below: drain to at most 32 first
                 while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
                     __syncwarp();
-                    resolve_blocks<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], qn - 32, qn, acc_count,
+                    resolve_blocks<T>(cc, K, step, thr8, thr16, C, st, pcap, q_w[w], q_i[w], q_g[w], qn - 32, qn, acc_count,
                                       acc, acc_cap, counters, active, stats);
                     __syncwarp();
                     qn -= 32;
@@ -269,7 +279,7 @@ __global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, i
         }
         if (qn) {
             __syncwarp();
-            resolve_blocks<T>(cc, K, step, thr8, C, st, pcap, q_w[w], q_i[w], q_g[w], 0, qn, acc_count, acc, acc_cap,
+            resolve_blocks<T>(cc, K, step, thr8, thr16, C, st, pcap, q_w[w], q_i[w], q_g[w], 0, qn, acc_count, acc, acc_cap,
                               counters, active, stats);
             __syncwarp();
         }

@@ -90,7 +90,8 @@ struct PhiloxRow {
 };
 
 // Counter layout of the random streams used by the step (fourth word tags).
-constexpr uint32_t kTagFine = 0x40000000u;   // low 24 bits of a pair's uniform
+constexpr uint32_t kTagMid = 0x20000000u;    // bits 23..16 of a pair's uniform
+constexpr uint32_t kTagFine = 0x40000000u;   // low 16 bits of a pair's uniform
 constexpr uint32_t kTagAngle = 0x80000000u;  // centre-of-mass direction
 constexpr uint32_t kStepInit = 0xFFFFFFFFu;  // first word reserved for sampling
 

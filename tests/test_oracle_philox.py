@@ -94,12 +94,27 @@ def test_pair_word_uniform_and_independent():
 
 
 def test_pair_word_structure():
-    """Top byte comes from block (step, cell, i, j/16); changing j/16 changes it."""
+    """Top byte from block (step, cell, i, j/16), next byte from the block
+    (step, cell, i, TAG_MID | j/16), low 16 bits from (step, cell, i, TAG_FINE | j)."""
     key = [1, 2]
     w = O.pair_word(key, 3, 4, 5, 37)
     blk = O.philox([3, 4, 5, 37 >> 4], key)
     top = (int(blk[(37 >> 2) & 3]) >> (8 * (37 & 3))) & 0xFF
-    assert (w >> 24) == top
-    # the low 24 bits come from a different stream: independent of j/16 block
+    mid_blk = O.philox([3, 4, 5, 0x20000000 | (37 >> 4)], key)
+    mid = (int(mid_blk[(37 >> 2) & 3]) >> (8 * (37 & 3))) & 0xFF
     fine = O.philox([3, 4, 5, 0x40000000 | 37], key)
-    assert (w & 0xFFFFFF) == (int(fine[0]) >> 8)
+    assert (w >> 24) == top
+    assert ((w >> 16) & 0xFF) == mid
+    assert (w & 0xFFFF) == (int(fine[0]) >> 16)
+
+
+def test_pair_word_parts_are_independent():
+    """Top byte, middle byte and low half of u_ij are uncorrelated."""
+    key = [9, 10]
+    w = np.array([O.pair_word(key, 1, 2, i, j) for i in range(30) for j in range(i + 1, 200)], dtype=np.uint64)
+    top = (w >> np.uint64(24)).astype(float)
+    mid = ((w >> np.uint64(16)) & np.uint64(0xFF)).astype(float)
+    low = (w & np.uint64(0xFFFF)).astype(float)
+    lim = 5.0 / np.sqrt(len(w))
+    for a, b in ((top, mid), (top, low), (mid, low)):
+        assert abs(np.corrcoef(a, b)[0, 1]) < lim
