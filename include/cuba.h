@@ -196,6 +196,68 @@ int cuba_step_profiled(cuba_sim* sim, int n_steps, double* phase_ms, void* strea
  */
 int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batches: many independent simulations advanced by one launch sequence.    */
+/* ------------------------------------------------------------------------ */
+/*
+ * A batch holds the state of many simulations (each with its own box, cells,
+ * dt, sigma, N_test, seed and step counter) in one device arena; every
+ * cuba_batch_step advances all resident simulations by the same number of
+ * steps with one captured graph per step (stream/key, one sort of the whole
+ * arena, one persistent pair-tile launch over all cells of all simulations,
+ * resolve).  Results of a simulation do not depend on the other residents:
+ * its random numbers are keyed by its own seed, step counter and local cell
+ * and particle indices, and every per-cell operation is order independent.
+ * This is the execution layer for ensembles and for serving (north star; the
+ * paper runs one simulation at a time).
+ */
+typedef struct cuba_batch cuba_batch;
+
+typedef struct cuba_batch_config {
+    int32_t precision;      /* CUBA_FP32 or CUBA_FP64 for all members */
+    int32_t max_sims;       /* resident simulations at most */
+    int64_t max_particles;  /* particles of all residents together */
+    int64_t max_cells;      /* cells of all residents together */
+} cuba_batch_config;
+
+/* Allocate an empty batch on the current device. */
+int cuba_batch_create(const cuba_batch_config* cfg, cuba_batch** out);
+void cuba_batch_destroy(cuba_batch* b);
+
+/*
+ * Admit a simulation: params as for cuba_create (precision must match the
+ * batch), n particles sampled like cuba_init_thermal.  Fails with
+ * CUBA_ERR_CAPACITY (nothing changes) if the batch lacks room.  *id receives
+ * a handle valid until cuba_batch_remove.  Synchronous.
+ */
+int cuba_batch_add(cuba_batch* b, const cuba_params* params, int64_t n, const cuba_region* regions,
+                   int n_regions, int32_t* id, void* stream);
+
+/* Same with a given state (SoA x, y, z, px, py, pz of n particles, host or
+   device memory, any order) instead of sampling.  Synchronous. */
+int cuba_batch_add_state(cuba_batch* b, const cuba_params* params, const void* soa, int64_t n, int32_t* id,
+                         void* stream);
+
+/* Retire a simulation and compact the arena.  Synchronous. */
+int cuba_batch_remove(cuba_batch* b, int32_t id);
+
+/* Advance every resident simulation by n_steps.  Async on `stream`. */
+int cuba_batch_step(cuba_batch* b, int n_steps, void* stream);
+
+/* Per-member queries, as the single-simulation calls (synchronous). */
+int cuba_batch_observables(cuba_batch* b, int32_t id, double* T00, double* T0x, int32_t* counts, void* stream);
+int cuba_batch_totals(cuba_batch* b, int32_t id, double out[4], int64_t* n_particles, void* stream);
+int cuba_batch_stats(cuba_batch* b, int32_t id, cuba_counters* out);
+int cuba_batch_get_state(cuba_batch* b, int32_t id, void* soa_out, void* stream);
+int cuba_batch_get_step(cuba_batch* b, int32_t id, uint32_t* step);
+
+/* Occupancy: resident simulations, particles and cells in use. */
+int cuba_batch_usage(const cuba_batch* b, int32_t* n_sims, int64_t* n_particles, int64_t* n_cells);
+
+/* Device bytes a batch of this configuration allocates at creation (the
+   accepted-pair list, sized from occupancy, comes on top). */
+int64_t cuba_batch_bytes(const cuba_batch_config* cfg);
+
 /*
  * Cell keys and stable sort of particle positions without allocating memory.
  * The paper has no counterpart: this entry point exists for callers that

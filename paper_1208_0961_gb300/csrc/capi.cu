@@ -13,10 +13,12 @@
 
 #include "../../include/cuba.h"
 #include "engine.cuh"
+#include "host.h"
 
 using namespace cuba;
 
-namespace {
+namespace cuba {
+namespace host {
 
 thread_local std::string g_last_error;
 
@@ -36,11 +38,6 @@ int cuda_fail(cudaError_t e, const char* what)
     return fail(CUBA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CUDA_TRY(call, what)                          \
-    do {                                              \
-        cudaError_t e_ = (call);                      \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
 
 constexpr double kDefaultGammaFp64 = 8.0;
 
@@ -83,19 +80,6 @@ int make_desc(const cuba_params* p, SimDesc* S)
     S->thr16 = (pb >= 1.0) ? 65536u : (uint32_t)std::floor(pb * 65536.0);
     S->gamma_fp64 = (float)(p->gamma_fp64 > 0.0 ? p->gamma_fp64 : kDefaultGammaFp64);
     S->step = 0;
-    return CUBA_OK;
-}
-
-template <typename P>
-int dalloc(P** ptr, size_t bytes, const char* what)
-{
-    *ptr = nullptr;
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc((void**)ptr, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CUBA_ERR_OOM, "cudaMalloc %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
-    }
     return CUBA_OK;
 }
 
@@ -156,33 +140,8 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
     return CUBA_OK;
 }
 
-}  // namespace
-
-struct cuba_sim {
-    cuba_params params;
-    SimDesc desc;      // host copy; the step counter lives on the device
-    Arena A;
-    cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    uint32_t graph_np = 0;            // what the graphs were captured for
-    const void* graph_acc = nullptr;
-    int graph_trace = 0;
-    double* d_obs = nullptr;  // scratch for observables: 2 n_cells doubles + n_cells ints
-    double* d_tot = nullptr;  // 4 doubles
-};
-
-namespace {
-
-void drop_graphs(cuba_sim* s)
-{
-    for (int k = 0; k < 2; ++k)
-        if (s->graph[k]) {
-            cudaGraphExecDestroy(s->graph[k]);
-            s->graph[k] = nullptr;
-        }
-}
-
-// Enqueue one step A1-A7 (both for direct launch and for capture).
+// Enqueue one step A1-A7 on every simulation of the arena (direct launch or
+// capture).
 int enqueue_step(Arena& A, cudaStream_t st)
 {
     if (launch_stream_key(A, st)) return fail(CUBA_ERR_CUDA, "stream/key launch failed");
@@ -194,43 +153,93 @@ int enqueue_step(Arena& A, cudaStream_t st)
     return CUBA_OK;
 }
 
-int capture_graph(cuba_sim* s, int which)
+// Largest-remainder split of n over weights T^3 V (ties to the lower index).
+int split_counts(int64_t n, const cuba_region* R, int nreg, std::vector<int64_t>& counts)
 {
-    Arena& A = s->A;
-    const int saved_cur = A.cur;
-    A.cur = which;
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    int rc = enqueue_step(A, s->capture_stream);
-    cudaError_t e = cudaStreamEndCapture(s->capture_stream, &g);
-    A.cur = saved_cur;
-    if (rc) {
-        if (g) cudaGraphDestroy(g);
-        return rc;
+    std::vector<double> w(nreg), frac(nreg);
+    double wsum = 0.0;
+    for (int r = 0; r < nreg; ++r) {
+        double v = 1.0;
+        for (int a = 0; a < 3; ++a) v *= (R[r].hi[a] - R[r].lo[a]);
+        if (!(v > 0.0) || !(R[r].T > 0.0)) return fail(CUBA_ERR_INVALID, "region %d: empty box or T <= 0", r);
+        w[r] = R[r].T * R[r].T * R[r].T * v;
+        wsum += w[r];
     }
-    if (e != cudaSuccess) return cuda_fail(e, "end capture");
-    e = cudaGraphInstantiate(&s->graph[which], g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
-    s->graph_np = A.np;
-    s->graph_acc = A.acc;
-    s->graph_trace = A.trace;
+    counts.assign(nreg, 0);
+    int64_t assigned = 0;
+    for (int r = 0; r < nreg; ++r) {
+        const double q = (double)n * w[r] / wsum;
+        counts[r] = (int64_t)std::floor(q);
+        frac[r] = q - (double)counts[r];
+        assigned += counts[r];
+    }
+    while (assigned < n) {
+        int best = 0;
+        for (int r = 1; r < nreg; ++r)
+            if (frac[r] > frac[best]) best = r;
+        counts[best] += 1;
+        frac[best] = -1.0;
+        ++assigned;
+    }
     return CUBA_OK;
 }
 
-// Sort the freshly loaded state (keys of the unsorted positions) and size the
-// accepted-pair list from the resulting occupancy.
-int settle_state(cuba_sim* s, cudaStream_t st)
+// Sample thermal regions into particles [S.p_off, S.p_off + n) of the arena.
+int sample_regions(Arena& A, int sim_index, const SimDesc& S, int64_t n, const cuba_region* regions, int n_regions,
+                   const double* L, cudaStream_t st)
 {
-    Arena& A = s->A;
+    if (!regions || n_regions < 1 || n_regions > 1024) return fail(CUBA_ERR_INVALID, "bad regions");
+    for (int r = 0; r < n_regions; ++r)
+        for (int a = 0; a < 3; ++a)
+            if (!(regions[r].lo[a] >= 0.0) || !(regions[r].hi[a] <= L[a]) || !(regions[r].lo[a] < regions[r].hi[a]))
+                return fail(CUBA_ERR_INVALID, "region %d is not a box inside [0, L]", r);
+    std::vector<int64_t> counts;
+    int rc = split_counts(n, regions, n_regions, counts);
+    if (rc) return rc;
+    std::vector<double> hreg(7 * n_regions);
+    std::vector<uint64_t> first(n_regions);
+    uint64_t acc = 0;
+    for (int r = 0; r < n_regions; ++r) {
+        for (int a = 0; a < 3; ++a) {
+            hreg[7 * r + a] = regions[r].lo[a];
+            hreg[7 * r + 3 + a] = regions[r].hi[a];
+        }
+        hreg[7 * r + 6] = regions[r].T;
+        first[r] = acc;
+        acc += (uint64_t)counts[r];
+    }
+    double* d_reg = nullptr;
+    uint64_t* d_first = nullptr;
+    if ((rc = dalloc(&d_reg, hreg.size() * sizeof(double), "regions"))) return rc;
+    if ((rc = dalloc(&d_first, first.size() * sizeof(uint64_t), "regions"))) {
+        cudaFree(d_reg);
+        return rc;
+    }
+    cudaMemcpy(d_reg, hreg.data(), hreg.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_first, first.data(), first.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    cudaStreamSynchronize(st);
+    if (launch_init_thermal(A, sim_index, S, d_reg, n_regions, d_first, st))
+        rc = fail(CUBA_ERR_CUDA, "thermal sampling launch failed");
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(d_reg);
+    cudaFree(d_first);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "thermal sampling");
+    return rc;
+}
+
+// Keys of the present positions, stable sort, and the size of the
+// accepted-pair lists for the present occupancy (room for four times the
+// present need plus 2^20 entries: occupancy changes as the system evolves).
+// Returns 1 in *realloc if the list buffer was replaced.
+int settle_arena(Arena& A, cudaStream_t st, int* realloc)
+{
+    if (realloc) *realloc = 0;
     if (launch_keys_only(A, st)) return fail(CUBA_ERR_CUDA, "key launch failed");
     if (launch_sort_and_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
     if (launch_cell_prep(A, st, 0)) return fail(CUBA_ERR_CUDA, "cell preparation failed");
     uint2 tot;
     CUDA_TRY(cudaMemcpyAsync(&tot, A.cell_work + A.ncells, sizeof(uint2), cudaMemcpyDeviceToHost, st), "read list size");
     CUDA_TRY(cudaStreamSynchronize(st), "sync");
-    // Room for four times the present need plus 2^20 entries: the occupancy
-    // of cells changes as the system evolves (a shock compresses it).
     const uint64_t want = 4ull * tot.y + (1ull << 20);
     if (want > A.acc_capacity) {
         if (A.acc) cudaFree(A.acc);
@@ -239,31 +248,96 @@ int settle_state(cuba_sim* s, cudaStream_t st)
         int rc = dalloc(&A.acc, want * sizeof(unsigned long long), "accepted list");
         if (rc) return rc;
         A.acc_capacity = want;
+        if (realloc) *realloc = 1;
     }
-    // captured graphs hold the particle count, the list buffer and the trace
-    // switch; keep them while those are unchanged
-    if (s->graph_np != A.np || s->graph_acc != A.acc || s->graph_trace != A.trace) drop_graphs(s);
     return CUBA_OK;
 }
 
-int upload_desc(cuba_sim* s, cudaStream_t st)
-{
-    CUDA_TRY(cudaMemcpyAsync(s->A.d_sims, &s->desc, sizeof(SimDesc), cudaMemcpyHostToDevice, st), "upload descriptor");
-    return CUBA_OK;
-}
-
-int check_kernel_errors(cuba_sim* s)
+int read_kernel_errors(Arena& A)
 {
     uint32_t err = 0;
     CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
-    CUDA_TRY(cudaMemcpy(&err, s->A.counters + 1, 4, cudaMemcpyDeviceToHost), "read error flags");
+    CUDA_TRY(cudaMemcpy(&err, A.counters + 1, 4, cudaMemcpyDeviceToHost), "read error flags");
     if (err) {
-        cudaMemset(s->A.counters + 1, 0, 4);
+        cudaMemset(A.counters + 1, 0, 4);
         if (err & kErrCapacity)
             return fail(CUBA_ERR_OVERFLOW, "accepted-pair lists of a step exceeded the allocated list; "
                                            "that step skipped its collisions");
         return fail(CUBA_ERR_OVERFLOW, "a cell's accepted-pair list overflowed; some accepted pairs were dropped");
     }
+    return CUBA_OK;
+}
+
+void StepGraphs::drop()
+{
+    for (int k = 0; k < 2; ++k)
+        if (g[k]) {
+            cudaGraphExecDestroy(g[k]);
+            g[k] = nullptr;
+        }
+}
+
+// Launch n steps, capturing one graph per ping-pong buffer on first use; the
+// graphs are dropped whenever the arena's layout changes.
+int StepGraphs::run(Arena& A, int n, cudaStream_t st)
+{
+    if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells) drop();
+    for (int k = 0; k < n; ++k) {
+        const int which = A.cur;
+        if (!g[which]) {
+            if (!capture) CUDA_TRY(cudaStreamCreateWithFlags(&capture, cudaStreamNonBlocking), "capture stream");
+            const int saved = A.cur;
+            A.cur = which;
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+            int rc = enqueue_step(A, capture);
+            cudaError_t e = cudaStreamEndCapture(capture, &graph);
+            A.cur = saved;
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            e = cudaGraphInstantiate(&g[which], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+            np = A.np;
+            acc = A.acc;
+            trace = A.trace;
+            nsims = A.nsims;
+            ncells = A.ncells;
+        }
+        CUDA_TRY(cudaGraphLaunch(g[which], st), "graph launch");
+        A.cur ^= 1;
+    }
+    return CUBA_OK;
+}
+
+StepGraphs::~StepGraphs()
+{
+    drop();
+    if (capture) cudaStreamDestroy(capture);
+}
+
+}  // namespace host
+}  // namespace cuba
+
+using namespace cuba::host;
+
+struct cuba_sim {
+    cuba_params params;
+    SimDesc desc;      // host copy; the step counter lives on the device
+    Arena A;
+    StepGraphs graphs;
+    double* d_obs = nullptr;  // scratch for observables: 2 n_cells doubles + n_cells ints
+    double* d_tot = nullptr;  // 4 doubles
+};
+
+namespace {
+
+int upload_desc(cuba_sim* s, cudaStream_t st)
+{
+    CUDA_TRY(cudaMemcpyAsync(s->A.d_sims, &s->desc, sizeof(SimDesc), cudaMemcpyHostToDevice, st), "upload descriptor");
     return CUBA_OK;
 }
 
@@ -294,11 +368,9 @@ int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out
     s->A.nsims = 1;
     s->A.ncells = S.ncells;
     s->A.np = 0;
-    if (cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        dalloc(&s->d_obs, (size_t)S.ncells * 20 + 64, "observables") ||
-        dalloc(&s->d_tot, 64, "totals")) {
+    if (dalloc(&s->d_obs, (size_t)S.ncells * 20 + 64, "observables") || dalloc(&s->d_tot, 64, "totals")) {
         cuba_destroy(s);
-        return fail(CUBA_ERR_CUDA, "stream or scratch allocation failed");
+        return fail(CUBA_ERR_OOM, "scratch allocation failed");
     }
     rc = upload_desc(s, 0);
     if (!rc) {
@@ -317,92 +389,28 @@ void cuba_destroy(cuba_sim* s)
 {
     if (!s) return;
     cudaDeviceSynchronize();
-    drop_graphs(s);
-    if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
+    s->graphs.drop();
     if (s->d_obs) cudaFree(s->d_obs);
     if (s->d_tot) cudaFree(s->d_tot);
     arena_free(s->A);
     delete s;
 }
 
-// Largest-remainder split of n over weights T^3 V (ties to the lower index).
-static int split_counts(int64_t n, const cuba_region* R, int nreg, std::vector<int64_t>& counts)
-{
-    std::vector<double> w(nreg), frac(nreg);
-    double wsum = 0.0;
-    for (int r = 0; r < nreg; ++r) {
-        double v = 1.0;
-        for (int a = 0; a < 3; ++a) v *= (R[r].hi[a] - R[r].lo[a]);
-        if (!(v > 0.0) || !(R[r].T > 0.0)) return fail(CUBA_ERR_INVALID, "region %d: empty box or T <= 0", r);
-        w[r] = R[r].T * R[r].T * R[r].T * v;
-        wsum += w[r];
-    }
-    counts.assign(nreg, 0);
-    int64_t assigned = 0;
-    for (int r = 0; r < nreg; ++r) {
-        const double q = (double)n * w[r] / wsum;
-        counts[r] = (int64_t)std::floor(q);
-        frac[r] = q - (double)counts[r];
-        assigned += counts[r];
-    }
-    while (assigned < n) {
-        int best = 0;
-        for (int r = 1; r < nreg; ++r)
-            if (frac[r] > frac[best]) best = r;
-        counts[best] += 1;
-        frac[best] = -1.0;
-        ++assigned;
-    }
-    return CUBA_OK;
-}
-
 int cuba_init_thermal(cuba_sim* s, int64_t n, const cuba_region* regions, int n_regions, void* stream)
 {
-    if (!s || !regions || n_regions < 1 || n_regions > 1024) return fail(CUBA_ERR_INVALID, "bad arguments");
-    if (n < 0 || n > (int64_t)s->A.pcap) return fail(CUBA_ERR_CAPACITY, "n = %lld exceeds max_particles = %u",
-                                                    (long long)n, s->A.pcap);
-    for (int r = 0; r < n_regions; ++r)
-        for (int a = 0; a < 3; ++a)
-            if (!(regions[r].lo[a] >= 0.0) || !(regions[r].hi[a] <= s->params.L[a]) || !(regions[r].lo[a] < regions[r].hi[a]))
-                return fail(CUBA_ERR_INVALID, "region %d is not a box inside [0, L]", r);
-    std::vector<int64_t> counts;
-    int rc = split_counts(n, regions, n_regions, counts);
-    if (rc) return rc;
-    std::vector<double> hreg(7 * n_regions);
-    std::vector<uint64_t> first(n_regions);
-    uint64_t acc = 0;
-    for (int r = 0; r < n_regions; ++r) {
-        for (int a = 0; a < 3; ++a) {
-            hreg[7 * r + a] = regions[r].lo[a];
-            hreg[7 * r + 3 + a] = regions[r].hi[a];
-        }
-        hreg[7 * r + 6] = regions[r].T;
-        first[r] = acc;
-        acc += (uint64_t)counts[r];
-    }
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    if (n < 0 || n > (int64_t)s->A.pcap)
+        return fail(CUBA_ERR_CAPACITY, "n = %lld exceeds max_particles = %u", (long long)n, s->A.pcap);
     cudaStream_t st = (cudaStream_t)stream;
-    double* d_reg = nullptr;
-    uint64_t* d_first = nullptr;
-    if ((rc = dalloc(&d_reg, hreg.size() * sizeof(double), "regions"))) return rc;
-    if ((rc = dalloc(&d_first, first.size() * sizeof(uint64_t), "regions"))) {
-        cudaFree(d_reg);
-        return rc;
-    }
-    cudaMemcpy(d_reg, hreg.data(), hreg.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(d_first, first.data(), first.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
-    cudaStreamSynchronize(st);
     s->desc.np = (uint32_t)n;
     s->desc.p_off = 0;
     s->desc.cell_off = 0;
     s->desc.step = 0;
     s->A.np = (uint32_t)n;
-    rc = upload_desc(s, st);
-    if (!rc && launch_init_thermal(s->A, 0, s->desc, d_reg, n_regions, d_first, st))
-        rc = fail(CUBA_ERR_CUDA, "thermal sampling launch failed");
-    if (!rc) rc = settle_state(s, st);
+    int rc = upload_desc(s, st);
+    if (!rc) rc = sample_regions(s->A, 0, s->desc, n, regions, n_regions, s->params.L, st);
+    if (!rc) rc = settle_arena(s->A, st, nullptr);
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(d_reg);
-    cudaFree(d_first);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "init_thermal");
     return rc;
 }
@@ -446,7 +454,7 @@ int cuba_set_state(cuba_sim* s, const void* soa, int64_t n, void* stream)
     s->desc.step = step;
     s->A.np = (uint32_t)n;
     int rc = upload_desc(s, st);
-    if (!rc) rc = settle_state(s, st);
+    if (!rc) rc = settle_arena(s->A, st, nullptr);
     cudaError_t e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "set_state");
     return rc;
@@ -463,7 +471,7 @@ int cuba_get_state(cuba_sim* s, void* out, void* stream)
                                  n * es, cudaMemcpyDefault, st),
                  "copy state out");
     CUDA_TRY(cudaStreamSynchronize(st), "sync");
-    return check_kernel_errors(s);
+    return read_kernel_errors(s->A);
 }
 
 int cuba_sizes(const cuba_sim* s, int64_t* np, int64_t* nc)
@@ -494,17 +502,7 @@ int cuba_set_step(cuba_sim* s, uint32_t step)
 int cuba_step(cuba_sim* s, int n_steps, void* stream)
 {
     if (!s || n_steps < 0) return fail(CUBA_ERR_INVALID, "bad arguments");
-    cudaStream_t st = (cudaStream_t)stream;
-    for (int k = 0; k < n_steps; ++k) {
-        const int which = s->A.cur;
-        if (!s->graph[which]) {
-            int rc = capture_graph(s, which);
-            if (rc) return rc;
-        }
-        CUDA_TRY(cudaGraphLaunch(s->graph[which], st), "graph launch");
-        s->A.cur ^= 1;
-    }
-    return CUBA_OK;
+    return s->graphs.run(s->A, n_steps, (cudaStream_t)stream);
 }
 
 int cuba_step_profiled(cuba_sim* s, int n_steps, double* phase_ms, void* stream)
@@ -540,7 +538,7 @@ int cuba_step_profiled(cuba_sim* s, int n_steps, double* phase_ms, void* stream)
     }
     for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
     if (rc) return rc;
-    return check_kernel_errors(s);
+    return read_kernel_errors(s->A);
 }
 
 int cuba_observables(cuba_sim* s, double* T00, double* T0x, int32_t* counts, void* stream)
@@ -556,7 +554,7 @@ int cuba_observables(cuba_sim* s, double* T00, double* T0x, int32_t* counts, voi
     if (T0x) CUDA_TRY(cudaMemcpyAsync(T0x, dT0x, nc * 8, cudaMemcpyDefault, st), "copy T0x");
     if (counts) CUDA_TRY(cudaMemcpyAsync(counts, dcnt, nc * 4, cudaMemcpyDefault, st), "copy counts");
     CUDA_TRY(cudaStreamSynchronize(st), "sync");
-    return check_kernel_errors(s);
+    return read_kernel_errors(s->A);
 }
 
 int cuba_totals(cuba_sim* s, double out[4], int64_t* n, void* stream)
@@ -567,7 +565,7 @@ int cuba_totals(cuba_sim* s, double out[4], int64_t* n, void* stream)
     CUDA_TRY(cudaMemcpyAsync(out, s->d_tot, 4 * sizeof(double), cudaMemcpyDefault, st), "copy totals");
     CUDA_TRY(cudaStreamSynchronize(st), "sync");
     if (n) *n = s->A.np;
-    return check_kernel_errors(s);
+    return read_kernel_errors(s->A);
 }
 
 int cuba_stats(cuba_sim* s, cuba_counters* out)
@@ -584,7 +582,7 @@ int cuba_stats(cuba_sim* s, cuba_counters* out)
     out->fp64_boosts = (int64_t)h[kStatFp64Boosts];
     out->overflow = (int64_t)h[kStatOverflow];
     out->reserved = 0;
-    return check_kernel_errors(s);
+    return read_kernel_errors(s->A);
 }
 
 int cuba_trace_enable(cuba_sim* s, int on)
@@ -596,7 +594,7 @@ int cuba_trace_enable(cuba_sim* s, int on)
         if (rc) return rc;
     }
     s->A.trace = on ? 1 : 0;
-    drop_graphs(s);
+    s->graphs.drop();
     return CUBA_OK;
 }
 
@@ -635,7 +633,7 @@ int cuba_trace_get(cuba_sim* s, uint32_t* keys, uint32_t* perm, uint32_t* cell_s
         }
     }
     if (n_pairs) *n_pairs = total;
-    return check_kernel_errors(s);
+    return read_kernel_errors(s->A);
 }
 
 int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, void* stream)

@@ -34,6 +34,7 @@ struct SimDesc {
     uint32_t thr8;    // top byte above thr8 rejects a pair outright; 256 = never
     uint32_t thr16;   // top 16 bits above thr16 reject a pair; 65536 = never
     float gamma_fp64; // FP32 path: CM boosts with gamma above this use FP64
+    uint32_t stat_slot; // row of the counters array (stable while the simulation lives)
 };
 
 // Per-simulation counters (unsigned long long for atomics).

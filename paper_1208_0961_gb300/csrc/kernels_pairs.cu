@@ -118,6 +118,7 @@ struct CellCtx {
     uint32_t list0;   // first slot of the cell's accepted-list segment
     uint32_t room;    // slots in the segment
     int s;            // simulation
+    uint32_t slot;    // its counters row
 };
 
 // Resolve queued blocks [e0, e1) of the warp, one block per lane.  The bytes
@@ -160,7 +161,7 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
                     acc[(size_t)cc.list0 + slot] = ((unsigned long long)i << 32) | j;
                 } else {
                     atomicOr(&counters[1], kErrAccOverflow);
-                    atomicAdd(&stats[cc.s * kStatCount + kStatOverflow], 1ull);
+                    atomicAdd(&stats[cc.slot * kStatCount + kStatOverflow], 1ull);
                 }
             }
         }
@@ -225,6 +226,7 @@ __global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, i
         cc.c = c;
         cc.s = sim_of_cell(sims, nsims, c);
         const SimDesc& S = sims[cc.s];
+        cc.slot = S.stat_slot;
         const uint2 w0 = work[c], w1 = work[c + 1];
         cc.lc = c - S.cell_off;
         cc.cbase = cell_start[c];
@@ -518,9 +520,10 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(const SimDesc* __re
             for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) gl[k] = L[k];
         __syncthreads();
         if (threadIdx.x == 0) {
-            atomicAdd(&stats[s * kStatCount + kStatAccepted], (unsigned long long)cnt);
-            atomicAdd(&stats[s * kStatCount + kStatExecuted], (unsigned long long)s_nexe);
-            if (s_n64) atomicAdd(&stats[s * kStatCount + kStatFp64Boosts], (unsigned long long)s_n64);
+            const uint32_t slot = S.stat_slot;
+            atomicAdd(&stats[slot * kStatCount + kStatAccepted], (unsigned long long)cnt);
+            atomicAdd(&stats[slot * kStatCount + kStatExecuted], (unsigned long long)s_nexe);
+            if (s_n64) atomicAdd(&stats[slot * kStatCount + kStatFp64Boosts], (unsigned long long)s_n64);
         }
         __syncthreads();
     }

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_stream_key(const SimDesc* __restrict__ 
         // reflections: one atomic per warp and simulation
         const unsigned peers = __match_any_sync(__activemask(), s);
         const unsigned tot = __reduce_add_sync(peers, (unsigned)nref);
-        if ((threadIdx.x & 31) == (__ffs(peers) - 1) && tot) atomicAdd(&stats[s * kStatCount + kStatReflections], (unsigned long long)tot);
+        if ((threadIdx.x & 31) == (__ffs(peers) - 1) && tot) atomicAdd(&stats[S.stat_slot * kStatCount + kStatReflections], (unsigned long long)tot);
     }
 }
 
@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
         if (n >= 2 && S.C > 0.0) {
             items = (n - 1 + kPairRows - 1) / kPairRows;
             room = list_room(S.C, n);
-            if (count_pairs) atomicAdd(&stats[s * kStatCount + kStatPairTests], (unsigned long long)n * (n - 1) / 2);
+            if (count_pairs)
+                atomicAdd(&stats[S.stat_slot * kStatCount + kStatPairTests], (unsigned long long)n * (n - 1) / 2);
         }
         work[c] = make_uint2(items, room);
         acc_count[c] = 0;
@@ -509,7 +510,7 @@ __global__ void k_advance(SimDesc* sims, int nsims, unsigned long long* stats)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < nsims) {
         sims[s].step += 1;
-        stats[s * kStatCount + kStatSteps] += 1;
+        stats[sims[s].stat_slot * kStatCount + kStatSteps] += 1;
     }
 }
 

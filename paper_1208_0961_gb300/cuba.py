@@ -48,6 +48,11 @@ class cuba_counters(C.Structure):
                  "reserved")]
 
 
+class cuba_batch_config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_sims", C.c_int32), ("max_particles", C.c_int64),
+                ("max_cells", C.c_int64)]
+
+
 class CubaError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("cuba error %d: %s" % (code, msg))
@@ -95,6 +100,20 @@ def load(build_if_missing=True):
         "cuba_philox": (C.c_int, [vp, C.c_int64, C.c_uint64, vp, vp]),
         "cuba_step_profiled": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), vp]),
         "cuba_bin_noalloc": (C.c_int, [C.POINTER(cuba_params), vp, C.c_int64, vp, vp, vp]),
+        "cuba_batch_create": (C.c_int, [C.POINTER(cuba_batch_config), C.POINTER(vp)]),
+        "cuba_batch_destroy": (None, [vp]),
+        "cuba_batch_add": (C.c_int, [vp, C.POINTER(cuba_params), C.c_int64, C.POINTER(cuba_region), C.c_int,
+                                     C.POINTER(C.c_int32), vp]),
+        "cuba_batch_add_state": (C.c_int, [vp, C.POINTER(cuba_params), vp, C.c_int64, C.POINTER(C.c_int32), vp]),
+        "cuba_batch_remove": (C.c_int, [vp, C.c_int32]),
+        "cuba_batch_step": (C.c_int, [vp, C.c_int, vp]),
+        "cuba_batch_observables": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp]),
+        "cuba_batch_totals": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), i64p, vp]),
+        "cuba_batch_stats": (C.c_int, [vp, C.c_int32, C.POINTER(cuba_counters)]),
+        "cuba_batch_get_state": (C.c_int, [vp, C.c_int32, vp, vp]),
+        "cuba_batch_get_step": (C.c_int, [vp, C.c_int32, u32p]),
+        "cuba_batch_usage": (C.c_int, [vp, C.POINTER(C.c_int32), i64p, i64p]),
+        "cuba_batch_bytes": (C.c_int64, [C.POINTER(cuba_batch_config)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -253,6 +272,159 @@ def cuba_bin_noalloc(params, xyz, n, perm, cell_start, stream=None):
     with no allocation inside the library (see include/cuba.h)."""
     _check(load().cuba_bin_noalloc(C.byref(params), _ptr(xyz), int(n), _ptr(perm), _ptr(cell_start),
                                    _stream_ptr(stream)))
+
+
+# ---- batches ---------------------------------------------------------------
+
+def make_batch_config(precision=CUBA_FP32, max_sims=16, max_particles=1 << 20, max_cells=1 << 16):
+    c = cuba_batch_config()
+    c.precision = int(precision)
+    c.max_sims = int(max_sims)
+    c.max_particles = int(max_particles)
+    c.max_cells = int(max_cells)
+    return c
+
+
+def cuba_batch_create(cfg):
+    h = C.c_void_p()
+    _check(load().cuba_batch_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def cuba_batch_destroy(b):
+    load().cuba_batch_destroy(b)
+
+
+def cuba_batch_add(b, params, n, regions, stream=None):
+    R = make_regions(regions)
+    i = C.c_int32()
+    _check(load().cuba_batch_add(b, C.byref(params), int(n), R, len(R), C.byref(i), _stream_ptr(stream)))
+    return i.value
+
+
+def cuba_batch_add_state(b, params, soa, n, stream=None):
+    i = C.c_int32()
+    _check(load().cuba_batch_add_state(b, C.byref(params), _ptr(soa), int(n), C.byref(i), _stream_ptr(stream)))
+    return i.value
+
+
+def cuba_batch_remove(b, sim_id):
+    _check(load().cuba_batch_remove(b, int(sim_id)))
+
+
+def cuba_batch_step(b, n_steps, stream=None):
+    _check(load().cuba_batch_step(b, int(n_steps), _stream_ptr(stream)))
+
+
+def cuba_batch_observables(b, sim_id, T00=None, T0x=None, counts=None, stream=None):
+    _check(load().cuba_batch_observables(b, int(sim_id), _ptr(T00), _ptr(T0x), _ptr(counts), _stream_ptr(stream)))
+
+
+def cuba_batch_totals(b, sim_id, stream=None):
+    out = (C.c_double * 4)()
+    n = C.c_int64()
+    _check(load().cuba_batch_totals(b, int(sim_id), out, C.byref(n), _stream_ptr(stream)))
+    return list(out), n.value
+
+
+def cuba_batch_stats(b, sim_id):
+    c = cuba_counters()
+    _check(load().cuba_batch_stats(b, int(sim_id), C.byref(c)))
+    return {name: getattr(c, name) for name, _ in cuba_counters._fields_}
+
+
+def cuba_batch_get_state(b, sim_id, out, stream=None):
+    _check(load().cuba_batch_get_state(b, int(sim_id), _ptr(out), _stream_ptr(stream)))
+
+
+def cuba_batch_get_step(b, sim_id):
+    s = C.c_uint32()
+    _check(load().cuba_batch_get_step(b, int(sim_id), C.byref(s)))
+    return s.value
+
+
+def cuba_batch_usage(b):
+    n = C.c_int32()
+    p = C.c_int64()
+    c = C.c_int64()
+    _check(load().cuba_batch_usage(b, C.byref(n), C.byref(p), C.byref(c)))
+    return n.value, p.value, c.value
+
+
+def cuba_batch_bytes(cfg):
+    return int(load().cuba_batch_bytes(C.byref(cfg)))
+
+
+class Batch:
+    """Owns one batch handle; members are addressed by the ids cuba returns."""
+
+    def __init__(self, cfg):
+        self.cfg = cfg
+        self.h = cuba_batch_create(cfg)
+        self.dtype = "float64" if cfg.precision == CUBA_FP64 else "float32"
+        self.members = {}
+
+    def close(self):
+        if self.h:
+            cuba_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, params, n, regions, stream=None):
+        i = cuba_batch_add(self.h, params, n, regions, stream)
+        self.members[i] = params
+        return i
+
+    def add_state(self, params, st, stream=None):
+        import numpy as np
+        st = np.ascontiguousarray(st, dtype=self.dtype)
+        i = cuba_batch_add_state(self.h, params, st, st.shape[1], stream)
+        self.members[i] = params
+        return i
+
+    def remove(self, sim_id):
+        cuba_batch_remove(self.h, sim_id)
+        self.members.pop(sim_id, None)
+
+    def step(self, n_steps=1, stream=None):
+        cuba_batch_step(self.h, n_steps, stream)
+
+    def n_cells(self, sim_id):
+        p = self.members[sim_id]
+        return p.n_cells[0] * p.n_cells[1] * p.n_cells[2]
+
+    def observables(self, sim_id, stream=None):
+        import numpy as np
+        nc = self.n_cells(sim_id)
+        T00 = np.zeros(nc)
+        T0x = np.zeros(nc)
+        cnt = np.zeros(nc, dtype=np.int32)
+        cuba_batch_observables(self.h, sim_id, T00, T0x, cnt, stream)
+        return T00, T0x, cnt
+
+    def totals(self, sim_id, stream=None):
+        return cuba_batch_totals(self.h, sim_id, stream)
+
+    def stats(self, sim_id):
+        return cuba_batch_stats(self.h, sim_id)
+
+    def get_state(self, sim_id, stream=None):
+        import numpy as np
+        n = self.totals(sim_id)[1]
+        out = np.zeros((6, n), dtype=self.dtype)
+        cuba_batch_get_state(self.h, sim_id, out, stream)
+        return out
+
+    def get_step(self, sim_id):
+        return cuba_batch_get_step(self.h, sim_id)
+
+    def usage(self):
+        return cuba_batch_usage(self.h)
 
 
 def cuba_last_error():

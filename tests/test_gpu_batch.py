@@ -1,0 +1,103 @@
+"""Batched execution (A9): many simulations in one arena and one launch
+sequence per step.  Each member's result must be bit-identical to the same
+simulation run alone (its random numbers are keyed by its own seed, step and
+local indices), also when other members are admitted and retired (with arena
+compaction) while it runs, and a member's step must match the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1208_0961_gb300 import cuba
+from paper_1208_0961_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _riemann(n, cells, sigma_mb, seed, prec, L=(10.0, 1.0, 1.0), dt=None):
+    cfg = W.riemann_1d(n, cells, dt or 0.5 * L[0] / cells, sigma_mb, L=L)
+    p = cuba.make_params(L=cfg["L"], n_cells=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
+                         n_test=cfg["n_test"], precision=prec, seed=seed)
+    return cfg, p
+
+
+def _alone(p, st, steps, prec):
+    sim = cuba.Sim(p, st.shape[1])
+    try:
+        sim.set_state(st)
+        sim.step(steps)
+        return sim.get_state(), sim.observables(), sim.stats()
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("prec", [cuba.CUBA_FP64, cuba.CUBA_FP32])
+def test_member_identical_alone_and_in_the_mix(prec):
+    dtype = np.float64 if prec == cuba.CUBA_FP64 else np.float32
+    cfgA, pA = _riemann(20000, 100, 10.0, seed=11, prec=prec)
+    cfgB, pB = _riemann(35000, 80, 30.0, seed=12, prec=prec, L=(8.0, 1.0, 1.0))
+    cfgC, pC = _riemann(9000, 300, 3.0, seed=13, prec=prec, L=(12.0, 2.0, 1.0))
+    stA = W.thermal_state(20000, cfgA["regions"], seed=1).astype(dtype)
+    stB = W.thermal_state(35000, cfgB["regions"], seed=2).astype(dtype)
+    stC = W.thermal_state(9000, cfgC["regions"], seed=3).astype(dtype)
+    refA, obsA, statA = _alone(pA, stA, 6, prec)
+    refC, obsC, statC = _alone(pC, stC, 3, prec)
+
+    b = cuba.Batch(cuba.make_batch_config(prec, max_sims=8, max_particles=100000, max_cells=1000))
+    try:
+        idB = b.add_state(pB, stB)
+        idA = b.add_state(pA, stA)
+        b.step(3)
+        b.remove(idB)          # A moves down: compaction
+        idC = b.add_state(pC, stC)
+        b.step(3)
+        assert b.get_step(idA) == 6 and b.get_step(idC) == 3
+        gA = b.get_state(idA)
+        gC = b.get_state(idC)
+        oA = b.observables(idA)
+        sA = b.stats(idA)
+        assert b.usage() == (2, 29000, 400)
+    finally:
+        b.close()
+    assert np.array_equal(gA, refA)
+    assert np.array_equal(gC, refC)
+    for x, y in zip(oA, obsA):
+        assert np.array_equal(x, y)
+    assert sA == statA and sA["executed"] > 0
+
+
+def test_batch_member_matches_oracle_one_step():
+    cfg, p = _riemann(20000, 100, 10.0, seed=5, prec=cuba.CUBA_FP64)
+    _, pO = _riemann(15000, 60, 20.0, seed=6, prec=cuba.CUBA_FP64, L=(6.0, 1.0, 1.0))
+    st = W.thermal_state(20000, cfg["regions"], seed=7)
+    stO = W.thermal_state(15000, W.riemann_regions((6.0, 1.0, 1.0), 0.4, 0.32), seed=8)
+    b = cuba.Batch(cuba.make_batch_config(cuba.CUBA_FP64, max_sims=4, max_particles=50000, max_cells=500))
+    try:
+        b.add_state(pO, stO)
+        i = b.add_state(p, st)
+        b.step(1)
+        g = b.get_state(i)
+        s = b.stats(i)
+    finally:
+        b.close()
+    op = O.make_params(L=cfg["L"], n=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
+                       n_test=cfg["n_test"], seed=5)
+    o, _, _, _ = O.sort(op, st)
+    o, res = O.step(op, 0, o)
+    assert np.array_equal(g[:3], o[:3])
+    E = np.sqrt((o[3:] ** 2).sum(axis=0))
+    assert np.max(np.abs(g[3:] - o[3:]).max(axis=0) / E) < 1e-9
+    assert s["accepted"] == res.n_acc and s["executed"] == res.n_exe
+
+
+def test_batch_capacity_is_enforced():
+    _, p = _riemann(20000, 100, 10.0, seed=5, prec=cuba.CUBA_FP32)
+    b = cuba.Batch(cuba.make_batch_config(cuba.CUBA_FP32, max_sims=2, max_particles=30000, max_cells=150))
+    try:
+        b.add(p, 20000, W.riemann_regions((10.0, 1.0, 1.0), 0.4, 0.32))
+        with pytest.raises(cuba.CubaError) as e:
+            b.add(p, 20000, W.riemann_regions((10.0, 1.0, 1.0), 0.4, 0.32))
+        assert e.value.code == cuba.CUBA_ERR_CAPACITY
+        assert b.usage() == (1, 20000, 100)
+        b.step(2)
+    finally:
+        b.close()
