@@ -36,6 +36,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuba", choices=["cuba", "reference"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+                    help="step: the headline single-workload line; batch: the batched ensemble; "
+                         "serve: the continuous-batching request stream")
+    ap.add_argument("--batch-sims", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-alone", type=int, default=1, help="also run the one-at-a-time loop")
     ap.add_argument("--n", type=int, default=16_000_000)
     ap.add_argument("--cells", type=int, default=2000)
     ap.add_argument("--dt", type=float, default=0.0025)
@@ -239,10 +247,129 @@ def run_reference(args):
     return 0
 
 
+def ensemble(n_sims, seed=0):
+    """Batched ensemble: independent 1D Riemann runs with particle counts
+    log-uniform in [5e4, 4e6], cell counts log-uniform in [100, 2000], sigma
+    log-uniform in [0.5, 50] mb, (T_L, T_R) from {400/320, 500/300, 350/250}
+    MeV; dt = min(dx/2, 0.1 lambda(T_L)); member k has seed 1000 + k."""
+    import numpy as np
+    from paper_1208_0961_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    pairs = [(0.4, 0.32), (0.5, 0.3), (0.35, 0.25)]
+    out = []
+    for k in range(n_sims):
+        n = int(round(math.exp(rng.uniform(math.log(5e4), math.log(4e6)))))
+        cells = int(round(math.exp(rng.uniform(math.log(100), math.log(2000)))))
+        sigma_mb = float(math.exp(rng.uniform(math.log(0.5), math.log(50.0))))
+        TL, TR = pairs[int(rng.integers(3))]
+        L = (10.0, 1.0, 1.0)
+        lam = 1.0 / (W.gluon_density(TL) * sigma_mb * W.FM2_PER_MB)
+        dt = min(0.5 * L[0] / cells, 0.1 * lam)
+        cfg = W.riemann_1d(n, cells, dt, sigma_mb, T_left=TL, T_right=TR, L=L)
+        cfg["seed"] = 1000 + k
+        out.append(cfg)
+    return out
+
+
+def run_batch_mode(args):
+    import torch
+    from paper_1208_0961_gb300 import cuba
+    torch.cuda.set_device(0)
+    cuba.load()
+    prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
+    members = ensemble(args.batch_sims, args.seed)
+    N = sum(m["n"] for m in members)
+    C = sum(m["n_cells"][0] for m in members)
+    cfg = cuba.make_batch_config(prec, max_sims=len(members), max_particles=N, max_cells=C)
+    b = cuba.Batch(cfg)
+    stream = torch.cuda.Stream()
+    params = []
+    for m in members:
+        p = cuba.make_params(L=m["L"], n_cells=m["n_cells"], dt=m["dt"], sigma_fm2=m["sigma_fm2"],
+                             n_test=m["n_test"], precision=prec, seed=m["seed"])
+        params.append(p)
+        b.add(p, m["n"], m["regions"], stream)
+    torch.cuda.synchronize()
+    b.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ids = list(b.members)
+    pair_tests = sum(b.stats(i)["pair_tests"] for i in ids) / (args.warmup + args.steps)
+    b.close()
+    # the plain loop: each member alone (single-simulation API), same steps
+    alone_ms = 0.0
+    for m, p in zip(members, params):
+        sim = cuba.Sim(p, m["n"])
+        sim.init_thermal(m["n"], m["regions"], stream)
+        cuba.cuba_step(sim.h, 1, stream)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        cuba.cuba_step(sim.h, args.steps, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        alone_ms += a0.elapsed_time(a1)
+        sim.close()
+    line = {"mode": "batch", "metric": "particle-updates/s (stream+bin+collide), batched ensemble",
+            "value": N * args.steps / (ms / 1000.0), "unit": "particle-updates/s", "steps": args.steps,
+            "ms_per_step": ms / args.steps, "members": len(members), "particles": N, "cells": C,
+            "pair_tests_per_step": pair_tests,
+            "alone": {"value": N * args.steps / (alone_ms / 1000.0), "ms_per_step": alone_ms / args.steps},
+            "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
+    line["speedup_vs_alone"] = line["value"] / line["alone"]["value"]
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_mode(args):
+    import torch
+    from paper_1208_0961_gb300 import cuba
+    from paper_1208_0961_gb300 import serve as S
+    torch.cuda.set_device(0)
+    cuba.load()
+    prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
+    reqs = S.poisson_stream(n_requests=args.serve_requests, rate_hz=args.serve_rate, seed=7)
+    stream = torch.cuda.Stream()
+    budget = int(args.serve_budget_gb * 1e9)
+    be = S.CudaBackend(budget, precision=prec, max_sims=256, stream=stream)
+    out = S.Server(be, quantum=32).run(reqs)
+    be.close()
+    line = {"mode": "serve", "metric": "served p50/p99 latency and particle-updates/s",
+            "requests": len(reqs), "rate_hz": args.serve_rate, "budget_gb": args.serve_budget_gb,
+            "served": out["served"], "rejected": out["rejected"], "p50_s": out["p50_s"], "p99_s": out["p99_s"],
+            "updates_per_s": out["updates_per_s"], "offered_updates_per_s": out["offered_updates_per_s"],
+            "makespan_s": out["makespan_s"], "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64",
+            "data": "synthetic"}
+    if args.serve_alone:
+        pb = 4 if prec == cuba.CUBA_FP32 else 8
+
+        def factory(r):
+            nc = r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+            return S.CudaBackend(2 * S.state_bytes(r.n, nc, pb) + (64 << 20), precision=prec, max_sims=1,
+                                 cells_per_particle=max(0.01, nc / max(1, r.n)), stream=stream)
+
+        alone = S.run_alone(factory, reqs)
+        line["alone"] = {"p50_s": alone["p50_s"], "p99_s": alone["p99_s"], "updates_per_s": alone["updates_per_s"],
+                         "makespan_s": alone["makespan_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch_mode(args)
+    if args.mode == "serve":
+        return run_serve_mode(args)
     import numpy as np
     import torch
     world, rank, local = dist_setup(args)

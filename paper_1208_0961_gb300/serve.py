@@ -1,0 +1,278 @@
+"""Continuous-batching server for whole test-particle simulations.
+
+Requests (a box, cells, dt, sigma, N_test, particle count, step count, seed and
+an initial state description) arrive over time.  The server keeps every
+admitted simulation's particle state resident in one device batch
+(`cuba_batch_*`), admits queued requests whenever particles, cells and member
+slots free up (the batch is sized from an HBM budget), advances all residents
+together in quanta of steps (one captured graph per step, all simulations in
+each launch), and retires a simulation when it has taken its steps: its
+observables (per-cell T^00, T^0x, counts) are read back and its latency
+(arrival to observables on the host) recorded.
+
+Each result is the same as the same request run alone: a simulation's random
+numbers depend only on its own seed, step counter and local indices.
+
+The scheduling logic is independent of the device: `Server` takes a backend
+object (the real one wraps `cuba.Batch`) and a clock, so that it can be
+tested on the CPU with a fake backend and a fake clock.
+"""
+import bisect
+import dataclasses
+import math
+import time
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float             # seconds after the start of the stream
+    kind: str                  # "riemann" or "thermal"
+    n: int                     # test particles
+    L: tuple
+    n_cells: tuple
+    dt: float
+    sigma_fm2: float
+    n_test: float
+    steps: int
+    regions: list              # [(lo, hi, T), ...]
+    seed: int
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    n: int
+    steps: int
+    observables: Optional[tuple] = None
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+def state_bytes(n, n_cells, precision_bytes=4):
+    """Device bytes a resident simulation occupies in a batch arena: two
+    state copies (6 components), keys and permutation ping-pong, per-cell
+    tables (start, work, counts, active)."""
+    return n * (2 * 6 * precision_bytes + 16 + 1) + n_cells * (4 + 8 + 4 + 4 + 20)
+
+
+# ---------------------------------------------------------------------------
+# Synthetic request streams (stand-ins for a real request log)
+# ---------------------------------------------------------------------------
+
+def _dt_for(dx_min, density, sigma_fm2):
+    """dt = min(dx/2, 0.1 lambda) with lambda = 1 / (n sigma) (0.1 mean free
+    path per step keeps the one-collision-per-step cap from distorting the
+    rate); dx/2 when sigma = 0."""
+    dt = 0.5 * dx_min
+    if sigma_fm2 > 0.0:
+        dt = min(dt, 0.1 / (density * sigma_fm2))
+    return dt
+
+
+def poisson_stream(n_requests=400, rate_hz=20.0, seed=7, n_min=1e4, n_max=8e6, steps_min=50, steps_max=500,
+                   sigma_mb_max=100.0, T_pairs=((0.4, 0.32), (0.5, 0.3), (0.35, 0.25))):
+    """Poisson arrivals; half 1D Riemann problems (cells along x, about 1000
+    particles per cell, between 100 and 2000 cells), half 3D thermal boxes
+    (n^3 cells of 0.1 fm with about 30 particles per cell, T = 0.4 GeV);
+    particle counts log-uniform, step counts and sigma uniform."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n_requests):
+        t += rng.exponential(1.0 / rate_hz)
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        steps = int(rng.integers(steps_min, steps_max + 1))
+        sigma_fm2 = float(rng.uniform(0.0, sigma_mb_max)) * W.FM2_PER_MB
+        if rng.random() < 0.5:
+            cells = int(min(2000, max(100, round(n / 1000))))
+            TL, TR = T_pairs[int(rng.integers(len(T_pairs)))]
+            L = (10.0, 1.0, 1.0)
+            regs = W.riemann_regions(L, TL, TR)
+            n_test = W.n_test_for(n, regs)
+            dt = _dt_for(L[0] / cells, W.gluon_density(TL), sigma_fm2)
+            out.append(Request(rid, t, "riemann", n, L, (cells, 1, 1), dt, sigma_fm2, n_test, steps, regs,
+                               1000 + rid))
+        else:
+            k = max(2, int(round((n / 30.0) ** (1.0 / 3.0))))
+            L = (0.1 * k, 0.1 * k, 0.1 * k)
+            regs = [((0.0, 0.0, 0.0), L, 0.4)]
+            n_test = W.n_test_for(n, regs)
+            dt = _dt_for(0.1, W.gluon_density(0.4), sigma_fm2)
+            out.append(Request(rid, t, "thermal", n, L, (k, k, k), dt, sigma_fm2, n_test, steps, regs, 1000 + rid))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Backends
+# ---------------------------------------------------------------------------
+
+class CudaBackend:
+    """The device: one cuba batch sized from an HBM budget."""
+
+    def __init__(self, budget_bytes, precision=None, max_sims=256, cells_per_particle=0.01, stream=None):
+        from . import cuba
+        self.cuba = cuba
+        precision = cuba.CUBA_FP32 if precision is None else precision
+        pb = 4 if precision == cuba.CUBA_FP32 else 8
+        per_particle = 2 * 6 * pb + 16 + 1
+        self.max_particles = int(min(0x7FFFFFF0, budget_bytes * 0.9 / (per_particle + 40 * cells_per_particle)))
+        self.max_cells = int(max(1 << 16, self.max_particles * cells_per_particle))
+        cfg = cuba.make_batch_config(precision, max_sims=max_sims, max_particles=self.max_particles,
+                                     max_cells=self.max_cells)
+        self.batch = cuba.Batch(cfg)
+        self.precision = precision
+        self.stream = stream
+        self.max_sims = max_sims
+
+    def fits(self, req, used_particles, used_cells, used_sims):
+        nc = req.n_cells[0] * req.n_cells[1] * req.n_cells[2]
+        return (used_particles + req.n <= self.max_particles and used_cells + nc <= self.max_cells
+                and used_sims < self.max_sims)
+
+    def admit(self, req):
+        p = self.cuba.make_params(L=req.L, n_cells=req.n_cells, dt=req.dt, sigma_fm2=req.sigma_fm2,
+                                  n_test=req.n_test, precision=self.precision, seed=req.seed)
+        return self.batch.add(p, req.n, req.regions, self.stream)
+
+    def step(self, k):
+        self.batch.step(k, self.stream)
+
+    def finish(self, handle):
+        obs = self.batch.observables(handle, self.stream)
+        self.batch.remove(handle)
+        return obs
+
+    def close(self):
+        self.batch.close()
+
+
+# ---------------------------------------------------------------------------
+# Scheduler
+# ---------------------------------------------------------------------------
+
+class Server:
+    """Continuous batching over a backend.
+
+    Each round: admit queued requests in arrival order while the backend has
+    room (a request that does not fit blocks the ones behind it, so large
+    requests are not starved), advance all residents by
+    k = min(quantum, smallest remaining step count) steps, and retire the
+    residents that are done.  Requests larger than the whole backend are
+    rejected.
+    """
+
+    def __init__(self, backend, quantum=64, clock: Callable[[], float] = time.perf_counter,
+                 sleep: Callable[[float], None] = time.sleep):
+        self.backend = backend
+        self.quantum = quantum
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests: List[Request], keep_observables=False):
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        t0 = self.clock()
+        now = lambda: self.clock() - t0  # noqa: E731
+        queue = []
+        resident = {}  # handle -> [request, remaining, admitted_at]
+        results, rejected = [], []
+        used_p = used_c = 0
+        nxt = 0
+        steps_run = 0
+        while nxt < len(reqs) or queue or resident:
+            t = now()
+            while nxt < len(reqs) and reqs[nxt].arrival <= t:
+                queue.append(reqs[nxt])
+                nxt += 1
+            # admission in arrival order
+            while queue:
+                r = queue[0]
+                nc = r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+                if not self.backend.fits(r, 0, 0, 0):
+                    rejected.append(queue.pop(0))
+                    continue
+                if not self.backend.fits(r, used_p, used_c, len(resident)):
+                    break
+                h = self.backend.admit(r)
+                resident[h] = [r, r.steps, now()]
+                used_p += r.n
+                used_c += nc
+                queue.pop(0)
+            if not resident:
+                if nxt < len(reqs):
+                    wait = reqs[nxt].arrival - now()
+                    if wait > 0:
+                        self.sleep(wait)
+                continue
+            k = min(self.quantum, min(v[1] for v in resident.values()))
+            self.backend.step(k)
+            steps_run += k
+            for h in list(resident):
+                v = resident[h]
+                v[1] -= k
+                if v[1] == 0:
+                    r = v[0]
+                    obs = self.backend.finish(h)
+                    t_done = now()
+                    results.append(Result(r.rid, r.arrival, v[2], t_done, r.n, r.steps,
+                                          obs if keep_observables else None))
+                    used_p -= r.n
+                    used_c -= r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+                    del resident[h]
+        makespan = now()
+        return summarize(results, rejected, makespan, reqs)
+
+
+def run_alone(backend_factory, requests: List[Request], clock=time.perf_counter, sleep=time.sleep,
+              keep_observables=False):
+    """The plain loop: one simulation at a time, in arrival order, each in a
+    backend of its own, stepped to completion before the next starts."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    t0 = clock()
+    now = lambda: clock() - t0  # noqa: E731
+    results = []
+    for r in reqs:
+        wait = r.arrival - now()
+        if wait > 0:
+            sleep(wait)
+        be = backend_factory(r)
+        t_adm = now()
+        h = be.admit(r)
+        left = r.steps
+        while left:
+            k = min(64, left)
+            be.step(k)
+            left -= k
+        obs = be.finish(h)
+        be.close()
+        results.append(Result(r.rid, r.arrival, t_adm, now(), r.n, r.steps, obs if keep_observables else None))
+    return summarize(results, [], now(), reqs)
+
+
+def summarize(results, rejected, makespan, requests):
+    lat = np.array(sorted(r.latency for r in results)) if results else np.zeros(0)
+    updates = float(sum(r.n * r.steps for r in results))
+    offered = float(sum(r.n * r.steps for r in requests))
+    span = max(makespan, 1e-12)
+    arrival_span = max((requests[-1].arrival - requests[0].arrival) if len(requests) > 1 else span, 1e-12)
+    return {
+        "served": len(results),
+        "rejected": len(rejected),
+        "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+        "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+        "mean_s": float(lat.mean()) if len(lat) else None,
+        "makespan_s": makespan,
+        "updates_per_s": updates / span,
+        "offered_updates_per_s": offered / arrival_span,
+        "results": results,
+    }

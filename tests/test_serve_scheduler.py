@@ -1,0 +1,104 @@
+"""Scheduling logic of the continuous-batching server, on the CPU with a fake
+device backend and a fake clock: admission in arrival order against the
+backend's capacity, no over-commit, rejection of requests larger than the
+whole device, latency accounting, and that batching shortens the makespan of a
+burst compared with the one-at-a-time loop."""
+import numpy as np
+
+from paper_1208_0961_gb300 import serve as S
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(0.0, dt)
+
+
+class FakeBackend:
+    """Capacity in particles/cells/members; a step of k costs k * (a + b * resident particles)
+    seconds of fake time (a fixed launch cost plus a per-particle cost)."""
+
+    def __init__(self, clock, max_particles=1000, max_cells=100, max_sims=4, a=1e-3, b=1e-6):
+        self.clock, self.max_particles, self.max_cells, self.max_sims = clock, max_particles, max_cells, max_sims
+        self.a, self.b = a, b
+        self.res = {}
+        self.next = 1
+        self.peak = (0, 0, 0)
+        self.log = []
+
+    def fits(self, r, p, c, s):
+        nc = r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+        return p + r.n <= self.max_particles and c + nc <= self.max_cells and s < self.max_sims
+
+    def admit(self, r):
+        h = self.next
+        self.next += 1
+        self.res[h] = r
+        p = sum(x.n for x in self.res.values())
+        c = sum(np.prod(x.n_cells) for x in self.res.values())
+        assert p <= self.max_particles and c <= self.max_cells and len(self.res) <= self.max_sims
+        self.peak = (max(self.peak[0], p), max(self.peak[1], c), max(self.peak[2], len(self.res)))
+        self.log.append(("admit", r.rid, self.clock()))
+        return h
+
+    def step(self, k):
+        p = sum(x.n for x in self.res.values())
+        self.clock.t += k * (self.a + self.b * p)
+
+    def finish(self, h):
+        r = self.res.pop(h)
+        self.log.append(("done", r.rid, self.clock()))
+        return (r.rid,)
+
+    def close(self):
+        pass
+
+
+def _req(rid, t, n, cells, steps):
+    return S.Request(rid, t, "riemann", n, (1.0, 1.0, 1.0), (cells, 1, 1), 0.01, 0.1, 1.0, steps,
+                     [((0, 0, 0), (1, 1, 1), 0.4)], rid)
+
+
+def test_all_served_in_capacity_and_fifo_admission():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    reqs = [_req(k, 0.001 * k, 200 + 50 * (k % 5), 10 + k % 7, 10 + 7 * (k % 4)) for k in range(30)]
+    reqs.append(_req(99, 0.005, 5000, 10, 5))  # larger than the whole device
+    out = S.Server(be, quantum=8, clock=clk, sleep=clk.sleep).run(reqs)
+    assert out["served"] == 30 and out["rejected"] == 1
+    admits = [rid for kind, rid, _ in be.log if kind == "admit"]
+    assert admits == sorted(admits)          # arrival order
+    assert be.peak[0] <= 1000 and be.peak[2] <= 4
+    for r in out["results"]:
+        assert r.finished >= r.admitted >= r.arrival
+        assert r.latency > 0
+
+
+def test_batching_beats_one_at_a_time_on_a_burst():
+    reqs = [_req(k, 0.0, 100, 10, 50) for k in range(8)]
+    clk = FakeClock()
+    batched = S.Server(FakeBackend(clk, max_sims=8), quantum=16, clock=clk, sleep=clk.sleep).run(reqs)
+    clk2 = FakeClock()
+    alone = S.run_alone(lambda r: FakeBackend(clk2, max_sims=1), reqs, clock=clk2, sleep=clk2.sleep)
+    assert batched["served"] == alone["served"] == 8
+    # eight launches' fixed cost shared: the burst finishes far earlier
+    assert batched["makespan_s"] < 0.5 * alone["makespan_s"]
+    assert batched["p99_s"] < alone["p99_s"]
+
+
+def test_poisson_stream_shape():
+    reqs = S.poisson_stream(n_requests=200, seed=7)
+    kinds = [r.kind for r in reqs]
+    assert 60 < kinds.count("riemann") < 140
+    ns = np.array([r.n for r in reqs])
+    assert ns.min() >= 1e4 and ns.max() <= 8e6
+    gaps = np.diff([r.arrival for r in reqs])
+    assert abs(gaps.mean() - 1 / 20.0) < 0.015
+    for r in reqs:
+        dx = min(r.L[a] / r.n_cells[a] for a in range(3))
+        assert r.dt < dx
