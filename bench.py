@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-alone", type=int, default=1, help="also run the one-at-a-time loop")
+    ap.add_argument("--serve-classes", type=int, default=3, choices=[1, 3])
     ap.add_argument("--n", type=int, default=16_000_000)
     ap.add_argument("--cells", type=int, default=2000)
     ap.add_argument("--dt", type=float, default=0.0025)
@@ -338,15 +339,25 @@ def run_serve_mode(args):
     reqs = S.poisson_stream(n_requests=args.serve_requests, rate_hz=args.serve_rate, seed=7)
     stream = torch.cuda.Stream()
     budget = int(args.serve_budget_gb * 1e9)
-    be = S.CudaBackend(budget, precision=prec, max_sims=256, stream=stream)
-    out = S.Server(be, quantum=32).run(reqs)
-    be.close()
+    if args.serve_classes == 1:
+        backends = [S.CudaBackend(budget, precision=prec, max_sims=256, stream=stream)]
+        srv = S.Server(backends, quantum=32)
+    else:
+        # cost classes (step under 0.1 ms, under 1 ms, larger), each its own
+        # batch and stream; the HBM budget split 10 / 30 / 60 %
+        fractions = (0.1, 0.3, 0.6)
+        backends = [S.CudaBackend(budget * f, precision=prec, max_sims=256, stream=torch.cuda.Stream())
+                    for f in fractions]
+        srv = S.Server(backends, quantum=256, classify=S.cost_class, round_s=0.02)
+    out = srv.run(reqs)
+    for be in backends:
+        be.close()
     line = {"mode": "serve", "metric": "served p50/p99 latency and particle-updates/s",
             "requests": len(reqs), "rate_hz": args.serve_rate, "budget_gb": args.serve_budget_gb,
             "served": out["served"], "rejected": out["rejected"], "p50_s": out["p50_s"], "p99_s": out["p99_s"],
             "updates_per_s": out["updates_per_s"], "offered_updates_per_s": out["offered_updates_per_s"],
-            "makespan_s": out["makespan_s"], "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64",
-            "data": "synthetic"}
+            "makespan_s": out["makespan_s"], "classes": args.serve_classes,
+            "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
     if args.serve_alone:
         pb = 4 if prec == cuba.CUBA_FP32 else 8
 

@@ -2,22 +2,25 @@
 
 Requests (a box, cells, dt, sigma, N_test, particle count, step count, seed and
 an initial state description) arrive over time.  The server keeps every
-admitted simulation's particle state resident in one device batch
-(`cuba_batch_*`), admits queued requests whenever particles, cells and member
-slots free up (the batch is sized from an HBM budget), advances all residents
-together in quanta of steps (one captured graph per step, all simulations in
-each launch), and retires a simulation when it has taken its steps: its
-observables (per-cell T^00, T^0x, counts) are read back and its latency
-(arrival to observables on the host) recorded.
+admitted simulation's particle state resident on the device, in one batch
+(`cuba_batch_*`) per cost class, admits queued requests whenever particles,
+cells and member slots of their class free up (the batches are sized from an
+HBM budget), advances the residents of each class together in quanta of
+steps (one captured graph per step, all simulations of the class in each
+launch; the classes run on their own streams and overlap on the device), and
+retires a simulation when it has taken its steps: its observables (per-cell
+T^00, T^0x, counts) are read back and its latency (arrival to observables on
+the host) recorded.  Cost classes keep a small request from advancing at the
+pace of the largest resident: each class's quantum is sized from an estimate
+of its step time.
 
 Each result is the same as the same request run alone: a simulation's random
 numbers depend only on its own seed, step counter and local indices.
 
-The scheduling logic is independent of the device: `Server` takes a backend
-object (the real one wraps `cuba.Batch`) and a clock, so that it can be
+The scheduling logic is independent of the device: `Server` takes backend
+objects (the real one wraps `cuba.Batch`) and a clock, so that it can be
 tested on the CPU with a fake backend and a fake clock.
 """
-import bisect
 import dataclasses
 import math
 import time
@@ -148,6 +151,17 @@ class CudaBackend:
     def step(self, k):
         self.batch.step(k, self.stream)
 
+    def step_time(self, requests):
+        """Estimated device seconds of one batch step with these residents."""
+        return STEP_FIXED_S + sum(step_cost(r) for r in requests)
+
+    def sync(self):
+        if self.stream is not None:
+            self.stream.synchronize()
+        else:
+            import torch
+            torch.cuda.synchronize()
+
     def finish(self, handle):
         obs = self.batch.observables(handle, self.stream)
         self.batch.remove(handle)
@@ -158,79 +172,135 @@ class CudaBackend:
 
 
 # ---------------------------------------------------------------------------
+# Cost model and classes
+# ---------------------------------------------------------------------------
+
+# Device time of one step of a simulation, from the measured rates of the
+# kernels: a fixed launch cost, HBM-bound streaming and binning per particle,
+# and the all-pairs test per pair.
+STEP_FIXED_S = 4e-5
+STEP_PER_PARTICLE_S = 4e-11
+STEP_PER_PAIR_S = 2.5e-13
+
+
+def pairs_per_step(r):
+    cells = r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+    return 0.0 if r.sigma_fm2 <= 0.0 else 0.5 * r.n * r.n / cells
+
+
+def step_cost(r):
+    """Estimated device seconds one step of request r adds to a batch step."""
+    return STEP_PER_PARTICLE_S * r.n + STEP_PER_PAIR_S * pairs_per_step(r)
+
+
+def cost_class(r, bounds=(1e-4, 1e-3)):
+    """0: steps under 0.1 ms, 1: under 1 ms, 2: larger."""
+    c = step_cost(r)
+    for k, b in enumerate(bounds):
+        if c < b:
+            return k
+    return len(bounds)
+
+
+# ---------------------------------------------------------------------------
 # Scheduler
 # ---------------------------------------------------------------------------
 
 class Server:
-    """Continuous batching over a backend.
+    """Continuous batching over one or more backends (cost classes).
 
-    Each round: admit queued requests in arrival order while the backend has
-    room (a request that does not fit blocks the ones behind it, so large
-    requests are not starved), advance all residents by
-    k = min(quantum, smallest remaining step count) steps, and retire the
-    residents that are done.  Requests larger than the whole backend are
-    rejected.
+    Requests go to the class of their estimated step cost (promoted to a
+    larger class if they do not fit an empty one; rejected if they fit none).
+    Each round: in every class, admit queued requests in arrival order while
+    the class's backend has room (a request that does not fit blocks the ones
+    behind it in its class, so large requests are not starved); then give
+    every class with residents a quantum of steps sized so that the class's
+    steps take about `round_s` of device time (at most the smallest remaining
+    step count of its residents), launch all classes (their streams overlap on
+    the device) and wait; retire residents that are done.  One class is plain
+    continuous batching with a common quantum.
     """
 
     def __init__(self, backend, quantum=64, clock: Callable[[], float] = time.perf_counter,
-                 sleep: Callable[[float], None] = time.sleep):
-        self.backend = backend
+                 sleep: Callable[[float], None] = time.sleep, classify=None, round_s=0.01):
+        self.backends = list(backend) if isinstance(backend, (list, tuple)) else [backend]
+        self.classify = classify or (lambda r: 0)
         self.quantum = quantum
+        self.round_s = round_s
         self.clock = clock
         self.sleep = sleep
 
+    def _quantum(self, backend, residents):
+        if len(self.backends) == 1:
+            return self.quantum
+        reqs = [v[0] for v in residents.values()]
+        if hasattr(backend, "step_time"):
+            cost = backend.step_time(reqs)
+        else:
+            cost = STEP_FIXED_S + sum(step_cost(r) for r in reqs)
+        return int(max(1, min(self.quantum, round(self.round_s / cost))))
+
     def run(self, requests: List[Request], keep_observables=False):
         reqs = sorted(requests, key=lambda r: r.arrival)
+        nb = len(self.backends)
         t0 = self.clock()
         now = lambda: self.clock() - t0  # noqa: E731
-        queue = []
-        resident = {}  # handle -> [request, remaining, admitted_at]
+        queues = [[] for _ in range(nb)]
+        resident = [dict() for _ in range(nb)]  # handle -> [request, remaining, admitted_at]
+        used = [[0, 0] for _ in range(nb)]
         results, rejected = [], []
-        used_p = used_c = 0
         nxt = 0
-        steps_run = 0
-        while nxt < len(reqs) or queue or resident:
+        while nxt < len(reqs) or any(queues) or any(resident):
             t = now()
             while nxt < len(reqs) and reqs[nxt].arrival <= t:
-                queue.append(reqs[nxt])
+                r = reqs[nxt]
                 nxt += 1
-            # admission in arrival order
-            while queue:
-                r = queue[0]
-                nc = r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
-                if not self.backend.fits(r, 0, 0, 0):
-                    rejected.append(queue.pop(0))
-                    continue
-                if not self.backend.fits(r, used_p, used_c, len(resident)):
-                    break
-                h = self.backend.admit(r)
-                resident[h] = [r, r.steps, now()]
-                used_p += r.n
-                used_c += nc
-                queue.pop(0)
-            if not resident:
+                k = min(max(0, int(self.classify(r))), nb - 1)
+                while k < nb and not self.backends[k].fits(r, 0, 0, 0):
+                    k += 1
+                if k == nb:
+                    rejected.append(r)
+                else:
+                    queues[k].append(r)
+            for k in range(nb):
+                be, q, res, u = self.backends[k], queues[k], resident[k], used[k]
+                while q:
+                    r = q[0]
+                    if not be.fits(r, u[0], u[1], len(res)):
+                        break
+                    h = be.admit(r)
+                    res[h] = [r, r.steps, now()]
+                    u[0] += r.n
+                    u[1] += r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+                    q.pop(0)
+            if not any(resident):
                 if nxt < len(reqs):
                     wait = reqs[nxt].arrival - now()
                     if wait > 0:
                         self.sleep(wait)
                 continue
-            k = min(self.quantum, min(v[1] for v in resident.values()))
-            self.backend.step(k)
-            steps_run += k
-            for h in list(resident):
-                v = resident[h]
-                v[1] -= k
-                if v[1] == 0:
-                    r = v[0]
-                    obs = self.backend.finish(h)
-                    t_done = now()
-                    results.append(Result(r.rid, r.arrival, v[2], t_done, r.n, r.steps,
-                                          obs if keep_observables else None))
-                    used_p -= r.n
-                    used_c -= r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
-                    del resident[h]
-        makespan = now()
-        return summarize(results, rejected, makespan, reqs)
+            ks = [0] * nb
+            for k in range(nb):
+                if resident[k]:
+                    ks[k] = min(self._quantum(self.backends[k], resident[k]), min(v[1] for v in resident[k].values()))
+                    self.backends[k].step(ks[k])
+            for k in range(nb):
+                if ks[k] and hasattr(self.backends[k], "sync"):
+                    self.backends[k].sync()
+            for k in range(nb):
+                res = resident[k]
+                for h in list(res):
+                    v = res[h]
+                    v[1] -= ks[k]
+                    if v[1] == 0:
+                        r = v[0]
+                        obs = self.backends[k].finish(h)
+                        results.append(Result(r.rid, r.arrival, v[2], now(), r.n, r.steps,
+                                              obs if keep_observables else None))
+                        used[k][0] -= r.n
+                        used[k][1] -= r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+                        del res[h]
+        return summarize(results, rejected, now(), reqs)
 
 
 def run_alone(backend_factory, requests: List[Request], clock=time.perf_counter, sleep=time.sleep,

@@ -50,6 +50,9 @@ class FakeBackend:
         p = sum(x.n for x in self.res.values())
         self.clock.t += k * (self.a + self.b * p)
 
+    def step_time(self, reqs):
+        return self.a + self.b * sum(r.n for r in reqs)
+
     def finish(self, h):
         r = self.res.pop(h)
         self.log.append(("done", r.rid, self.clock()))
@@ -102,3 +105,35 @@ def test_poisson_stream_shape():
     for r in reqs:
         dx = min(r.L[a] / r.n_cells[a] for a in range(3))
         assert r.dt < dx
+
+
+def test_cost_classes_keep_small_requests_fast():
+    big = S.Request(0, 0.0, "riemann", 900, (1.0, 1.0, 1.0), (2, 1, 1), 0.01, 0.1, 1.0, 200,
+                    [((0, 0, 0), (1, 1, 1), 0.4)], 0)
+    small = [_req(k, 0.001 + 0.001 * k, 20, 10, 200) for k in range(1, 6)]
+    reqs = [big] + small
+
+    def run(nclasses):
+        clk = FakeClock()
+        if nclasses == 1:
+            srv = S.Server(FakeBackend(clk, max_particles=2000, max_cells=200, max_sims=8, a=1e-5, b=1e-5),
+                           quantum=200, clock=clk, sleep=clk.sleep)
+        else:
+            bes = [FakeBackend(clk, max_particles=2000, max_cells=200, max_sims=8, a=1e-5, b=1e-5) for _ in range(2)]
+            srv = S.Server(bes, quantum=200, clock=clk, sleep=clk.sleep, classify=lambda r: 1 if r.n > 100 else 0,
+                           round_s=0.02)
+        out = srv.run(reqs)
+        return {r.rid: r.latency for r in out["results"]}
+
+    one, two = run(1), run(2)
+    assert len(one) == len(two) == 6
+    small_one = max(one[k] for k in range(1, 6))
+    small_two = max(two[k] for k in range(1, 6))
+    assert small_two < 0.5 * small_one
+
+
+def test_cost_model_orders_requests():
+    a = S.Request(0, 0.0, "riemann", 8_000_000, (10, 1, 1), (2000, 1, 1), 0.002, 1.0, 1e5, 100, [], 0)
+    b = S.Request(1, 0.0, "thermal", 20_000, (1, 1, 1), (9, 9, 9), 0.01, 1.0, 1e3, 100, [], 1)
+    assert S.step_cost(a) > 1e-3 > 1e-4 > S.step_cost(b)
+    assert S.cost_class(a) == 2 and S.cost_class(b) == 0
