@@ -175,6 +175,28 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def pair_tile_traffic():
+    """DRAM bytes of one full-size pair-tile launch from the committed ncu
+    summary, if the kernel's sources are unchanged since the capture."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "k_pair_tile_riemann1d_fp32.md")
+    srcs = ["kernels_pairs.cu", "engine.cuh", "philox.cuh", "fp.cuh"]
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256()
+        for f in srcs:
+            with open(os.path.join(ROOT, "paper_1208_0961_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        m = re.search(r"source-sha256[^:]*:\s*([0-9a-f]{64})", text)
+        t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+        if m and t and m.group(1) == h.hexdigest():
+            return int(t.group(1))
+    except OSError:
+        pass
+    return None
+
+
 def cpu_sample(args, cfg, steps):
     """Time the oracle on a strip of cells with the workload's occupancy.
 
@@ -425,14 +447,21 @@ def main():
     pair_ms = phase[3] / max(1, args.profile_steps)
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    # pair tile: integer-issue bound (Philox block per 16 pairs + byte test)
-    ops_per_pair = 3.0
+    # pair tile: integer-issue bound.  Algorithmic work per 16-pair Philox
+    # block: 16 wide multiplies + 18 xors (rounds after the row-invariant
+    # part) + 9 ops of the byte test = 43 lane-ops, i.e. 43/16 per pair test.
+    ops_per_pair = 43.0 / 16.0
+    pair_s = pair_ms / 1000.0
     peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12
-    achieved_tops = pairs_per_step * ops_per_pair / (pair_ms / 1000.0) / 1e12
+    achieved_tops = pairs_per_step * ops_per_pair / pair_s / 1e12
+    pipe_peak = n_sm * 32 * sm_mhz * 1e6  # one 32x32->64 multiply per pair at 32 lanes/clk/SM
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32 lane-ops)",
-                "frac": achieved_tops / peak_tops, "traffic": None,
-                "kernel": "k_pair_tile", "pair_tests_per_s": pairs_per_step / (pair_ms / 1000.0),
-                "ops_per_pair": ops_per_pair, "peak_basis": "%d SMs x 128 lanes x %.0f MHz (sampled median)" % (n_sm, sm_mhz)}
+                "frac": achieved_tops / peak_tops, "traffic": pair_tile_traffic(),
+                "kernel": "k_pair_tile", "pair_tests_per_s": pairs_per_step / pair_s,
+                "ops_per_pair": ops_per_pair,
+                "peak_basis": "%d SMs x 128 lanes x %.0f MHz (sampled median)" % (n_sm, sm_mhz),
+                "multiply_pipe_peak_pair_tests_per_s": pipe_peak,
+                "multiply_pipe_frac": pairs_per_step / pair_s / pipe_peak}
     # stream/bin phases against HBM: 56 algorithmic bytes per update (FP32)
     bpu = 56.0 if prec == cuba.CUBA_FP32 else 104.0
     sb_ms = (phase[0] + phase[1]) / max(1, args.profile_steps)
