@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-alone", type=int, default=1, help="also run the one-at-a-time loop")
     ap.add_argument("--serve-classes", type=int, default=3, choices=[1, 3])
+    ap.add_argument("--workload", default="riemann1d", choices=["riemann1d", "hotspot3d"],
+                    help="riemann1d: the headline 1D Riemann problem; hotspot3d: 3D thermal box with a hot spot")
     ap.add_argument("--n", type=int, default=16_000_000)
     ap.add_argument("--cells", type=int, default=2000)
     ap.add_argument("--dt", type=float, default=0.0025)
@@ -54,6 +56,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1, help="pick the collision launch shape before timing")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     return ap.parse_args()
@@ -61,6 +64,10 @@ def parse():
 
 def workload(args):
     from paper_1208_0961_gb300 import workloads as W
+    if args.workload == "hotspot3d":
+        cfg = W.hotspot_3d(args.n, args.cells, args.dt, args.sigma_mb)
+        cfg["name"] = "hotspot-3d-%dM-%d^3cells-%gmb" % (round(args.n / 1e6), args.cells, args.sigma_mb)
+        return cfg
     cfg = W.riemann_1d(args.n, args.cells, args.dt, args.sigma_mb)
     cfg["name"] = "riemann-1d-%dM-%dcells-%gmb" % (round(args.n / 1e6), args.cells, args.sigma_mb)
     return cfg
@@ -415,10 +422,19 @@ def main():
                          n_test=cfg["n_test"], precision=prec, seed=args.seed + rank)
     sim = cuba.Sim(p, args.n)
     stream = torch.cuda.Stream()
-    sim.init_riemann(args.n, cfg["T_left"], cfg["T_right"], stream)
+    if args.workload == "hotspot3d":
+        sim.init_hotspot(args.n, cfg["T0"], cfg["dT"], cfg["width"], stream)
+        args.no_cpu_baseline = True
+    else:
+        sim.init_riemann(args.n, cfg["T_left"], cfg["T_right"], stream)
     torch.cuda.synchronize()
     cuba.cuba_step(sim.h, args.warmup, stream)
     torch.cuda.synchronize()
+    tuned = None
+    if args.autotune:
+        tuned, tune_ms = cuba.cuba_autotune(sim.h, 2, stream)
+    else:
+        tune_ms = None
 
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -476,7 +492,7 @@ def main():
         host = torch.empty((6, args.n), dtype=torch.float32 if prec == cuba.CUBA_FP32 else torch.float64,
                            pin_memory=True)
         cuba.cuba_get_state(sim.h, host.data_ptr(), stream)
-        nc = args.cells
+        nc = cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2]
         T00 = torch.empty(nc, dtype=torch.float64, pin_memory=True)
         T0x = torch.empty(nc, dtype=torch.float64, pin_memory=True)
         cnt = torch.empty(nc, dtype=torch.int32, pin_memory=True)
@@ -507,9 +523,10 @@ def main():
             "config": {"workload": cfg["name"], "n_particles": args.n, "n_cells": args.cells, "dt": args.dt,
                        "sigma_mb": args.sigma_mb, "precision": args.precision, "n_test": cfg["n_test"],
                        "l2": "state %.0f MB > L2, no flush" % (args.n * 24 / 1e6 * (2 if prec else 1)),
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "small_max": cuba.cuba_get_small_max(sim.h), "autotune_ms": tune_ms},
             "clocks": clk,
-            "gpu_launches": launches_per_step(args.cells) * args.steps,
+            "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2]) * args.steps,
             "roofline": roofline,
             "hbm_phases": hbm,
             "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in zip(phase_names, phase)},

@@ -124,6 +124,19 @@ int cuba_init_thermal(cuba_sim* sim, int64_t n, const cuba_region* regions, int 
 int cuba_init_riemann(cuba_sim* sim, int64_t n, double T_left, double T_right, void* stream);
 
 /*
+ * Hot-spot initial state (the 3D thermal box with a hot spot): local
+ * temperature T(r) = T0 + dT exp(-|r - c|^2 / (2 width^2)) about the box
+ * centre c, density proportional to T(r)^3 (positions by rejection against
+ * (T(r)/(T0 + dT))^3, at most 64 tries per particle, then the last try is
+ * kept), E ~ E^2 exp(-E/T(r)) with isotropic directions.  Particle g uses the
+ * Philox blocks (0xFFFFFFFF, g, 0, 2 + k) for its tries and (…, 0), (…, 1)
+ * for its momentum.  Sorted by cell afterwards, step counter reset to 0.
+ * Synchronous.
+ */
+int cuba_init_hotspot(cuba_sim* sim, int64_t n, double T0, double dT, double width, void* stream);
+
+/*
+ * Load a state of n particles (SoA x, y, z, px, py, pz/*
  * Load a state of n particles (SoA x, y, z, px, py, pz of the simulation's
  * element type, host or device memory, any order); the library sorts it by
  * cell, stably.  Positions must lie in [0, L].  Synchronous.
@@ -162,6 +175,27 @@ int cuba_totals(cuba_sim* sim, double out[4], int64_t* n_particles, void* stream
 
 /* Counters since creation (host struct).  Synchronous; reports kernel errors. */
 int cuba_stats(cuba_sim* sim, cuba_counters* out);
+
+/*
+ * Launch shape of the collision step (no counterpart in the paper, which uses
+ * one thread per particle).  Cells with 2 <= n <= small_max particles take
+ * the warp-per-cell path (one warp tests all pairs of a cell, one warp
+ * resolves it); larger cells are split into 32-row items that persistent
+ * warps take from a queue.  small_max in [0, 1024]; 0 sends every cell to the
+ * item path.  Default 32.  Results do not depend on it.
+ */
+int cuba_set_small_max(cuba_sim* sim, int32_t small_max);
+int cuba_get_small_max(const cuba_sim* sim, int32_t* small_max);
+
+/*
+ * Autotuner: time n_steps steps for each candidate small_max
+ * {0, 16, 32, 64, 128, 256, 512, 1024}, each from the same saved copy of the
+ * present state (the simulation does not advance), and keep the fastest.
+ * *chosen (optional) receives it, ms_per_candidate (optional, host, 8
+ * doubles) the device time per step of each candidate.  Synchronous;
+ * allocates a temporary copy of the state.
+ */
+int cuba_autotune(cuba_sim* sim, int n_steps, int32_t* chosen, double* ms_per_candidate, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* cuba_last_error(void);
@@ -250,6 +284,11 @@ int cuba_batch_totals(cuba_batch* b, int32_t id, double out[4], int64_t* n_parti
 int cuba_batch_stats(cuba_batch* b, int32_t id, cuba_counters* out);
 int cuba_batch_get_state(cuba_batch* b, int32_t id, void* soa_out, void* stream);
 int cuba_batch_get_step(cuba_batch* b, int32_t id, uint32_t* step);
+
+/* Autotuner and launch shape of a batch, as cuba_autotune / cuba_set_small_max
+   (all resident members are timed together; none advances). */
+int cuba_batch_autotune(cuba_batch* b, int n_steps, int32_t* chosen, double* ms_per_candidate, void* stream);
+int cuba_batch_set_small_max(cuba_batch* b, int32_t small_max);
 
 /* Occupancy: resident simulations, particles and cells in use. */
 int cuba_batch_usage(const cuba_batch* b, int32_t* n_sims, int64_t* n_particles, int64_t* n_cells);

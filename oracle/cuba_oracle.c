@@ -229,6 +229,58 @@ int orc_init_thermal(const orc_params *p, int64_t n, const orc_region *R, int nr
     return ORC_OK;
 }
 
+/*
+ * Hot-spot initial state (the 3D thermal-box workload; the paper's runs use
+ * two temperatures, this profile is the library's reading of a "Gaussian hot
+ * spot"): T(r) = T0 + dT exp(-|r - centre|^2 / (2 w^2)) about the box centre,
+ * density proportional to T(r)^3.  Particle g places itself by rejection:
+ * try k = 0, 1, ... draws the block (STEP_INIT, g_lo, g_hi, 2 + k) with words
+ * 0..2 a uniform position in the box and word 3 the acceptance variate,
+ * accepted iff u < (T(r)/(T0 + dT))^3; after 64 rejected tries the 64th
+ * position is kept.  Momentum as in orc_init_thermal at the local T(r):
+ * E = -T ln(u1 u2 u3) with u1 = word 3 of block (STEP_INIT, g_lo, g_hi, 0) and
+ * u2, u3 = words 0, 1 of block (..., 1); direction from words 2, 3 of (..., 1).
+ */
+int orc_init_hotspot(const orc_params *p, int64_t n, double T0, double dT, double width, double *st)
+{
+    if (check_params(p) != ORC_OK || !(T0 > 0.0) || !(dT >= 0.0) || !(width > 0.0)) return ORC_ERR_INVALID;
+    const double Tmax = T0 + dT;
+    const double c[3] = {0.5 * p->L[0], 0.5 * p->L[1], 0.5 * p->L[2]};
+    for (int64_t g = 0; g < n; ++g) {
+        uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
+        double pos[3] = {0.0, 0.0, 0.0};
+        double T = T0;
+        for (uint32_t k = 0; k < 64; ++k) {
+            uint32_t t[4];
+            philox(STEP_INIT, glo, ghi, 2u + k, p->key, t);
+            double r2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                pos[a] = open01(t[a]) * p->L[a];
+                double d = pos[a] - c[a];
+                r2 += d * d;
+            }
+            T = T0 + dT * exp(-r2 / (2.0 * width * width));
+            double ratio = T / Tmax;
+            if (open01(t[3]) < ratio * ratio * ratio) break;
+        }
+        uint32_t a[4], b[4];
+        philox(STEP_INIT, glo, ghi, 0u, p->key, a);
+        philox(STEP_INIT, glo, ghi, 1u, p->key, b);
+        double E = -T * log(open01(a[3]) * open01(b[0]) * open01(b[1]));
+        double ct = 2.0 * open01(b[2]) - 1.0;
+        double stt = sqrt((1.0 - ct) * (1.0 + ct));
+        double phi = 2.0 * M_PI * open01(b[3]);
+        double mom[3] = {E * stt * cos(phi), E * stt * sin(phi), E * ct};
+        for (int ax = 0; ax < 3; ++ax) {
+            double v = pos[ax], q = mom[ax];
+            if (p->fp32) { v = (double)(float)v; q = (double)(float)q; }
+            st[ax * n + g] = v;
+            st[(3 + ax) * n + g] = q;
+        }
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* A1-A3: free streaming (Eq. 2), wall reflection, cell key                  */
 /* ------------------------------------------------------------------------ */

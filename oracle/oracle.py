@@ -71,6 +71,8 @@ def lib():
         L.orc_region_counts.restype = C.c_int
         L.orc_init_thermal.argtypes = [C.POINTER(Params), C.c_int64, C.POINTER(Region), C.c_int, dp]
         L.orc_init_thermal.restype = C.c_int
+        L.orc_init_hotspot.argtypes = [C.POINTER(Params), C.c_int64, C.c_double, C.c_double, C.c_double, dp]
+        L.orc_init_hotspot.restype = C.c_int
         L.orc_keys.argtypes = [C.POINTER(Params), C.c_int64, dp, u32p]
         L.orc_keys.restype = C.c_int
         L.orc_sort.argtypes = [C.POINTER(Params), C.c_int64, dp, u32p, i64p, i64p]
@@ -170,6 +172,15 @@ def init_thermal(p, n, regions):
     rc = lib().orc_init_thermal(C.byref(p), int(n), R, len(R), _ptr(st, C.c_double))
     if rc != 0:
         raise ValueError("orc_init_thermal failed: %d" % rc)
+    return st
+
+
+def init_hotspot(p, n, T0, dT, width):
+    """Hot-spot state in generation order (unsorted), shape (6, n)."""
+    st = np.zeros((6, int(n)), dtype=np.float64)
+    rc = lib().orc_init_hotspot(C.byref(p), int(n), float(T0), float(dT), float(width), _ptr(st, C.c_double))
+    if rc != 0:
+        raise ValueError("orc_init_hotspot failed: %d" % rc)
     return st
 
 

@@ -281,7 +281,9 @@ void StepGraphs::drop()
 // graphs are dropped whenever the arena's layout changes.
 int StepGraphs::run(Arena& A, int n, cudaStream_t st)
 {
-    if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells) drop();
+    if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells ||
+        small_max != A.small_max)
+        drop();
     for (int k = 0; k < n; ++k) {
         const int which = A.cur;
         if (!g[which]) {
@@ -306,11 +308,88 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
             trace = A.trace;
             nsims = A.nsims;
             ncells = A.ncells;
+            small_max = A.small_max;
         }
         CUDA_TRY(cudaGraphLaunch(g[which], st), "graph launch");
         A.cur ^= 1;
     }
     return CUBA_OK;
+}
+
+int set_small_max(Arena& A, int32_t v)
+{
+    if (v < 0 || v > 1024) return fail(CUBA_ERR_INVALID, "small_max must lie in [0, 1024]");
+    A.small_max = (uint32_t)v;
+    return CUBA_OK;
+}
+
+// Candidate thresholds of the warp-per-cell path, timed by autotune_arena.
+static const int32_t kTuneCandidates[] = {0, 16, 32, 64, 128, 256, 512, 1024};
+static const int kTuneCount = (int)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0]));
+
+// Time n_steps steps of the arena for every candidate threshold, each from
+// the same saved state (positions, momenta, step counters, counters), then
+// restore that state and keep the fastest threshold.  The simulations do not
+// advance.  ms (optional) receives kTuneCount timings in candidate order.
+int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms)
+{
+    if (n_steps < 1) return fail(CUBA_ERR_INVALID, "n_steps must be >= 1");
+    if (A.np == 0 || A.nsims == 0) {
+        if (chosen) *chosen = (int32_t)A.small_max;
+        return CUBA_OK;
+    }
+    const size_t es = A.precision == CUBA_FP64 ? 8 : 4;
+    const size_t col = (size_t)A.np * es;
+    void* saved = nullptr;
+    int rc = dalloc(&saved, 6 * col, "autotune state");
+    if (rc) return rc;
+    std::vector<SimDesc> table(A.nsims);
+    std::vector<unsigned long long> stats((size_t)A.simcap * kStatCount);
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    const int cur0 = A.cur;
+    const uint32_t keep = A.small_max;
+    for (int c = 0; c < 6; ++c)
+        cudaMemcpy((char*)saved + c * col, (char*)A.st[cur0] + (size_t)c * A.pcap * es, col, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(table.data(), A.d_sims, table.size() * sizeof(SimDesc), cudaMemcpyDeviceToHost);
+    cudaMemcpy(stats.data(), A.stats, stats.size() * 8, cudaMemcpyDeviceToHost);
+    auto restore = [&]() {
+        A.cur = cur0;
+        for (int c = 0; c < 6; ++c)
+            cudaMemcpy((char*)A.st[cur0] + (size_t)c * A.pcap * es, (char*)saved + c * col, col, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(A.d_sims, table.data(), table.size() * sizeof(SimDesc), cudaMemcpyHostToDevice);
+        cudaMemcpy(A.stats, stats.data(), stats.size() * 8, cudaMemcpyHostToDevice);
+        cudaDeviceSynchronize();
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    int32_t best_v = (int32_t)keep;
+    for (int k = 0; k < kTuneCount && !rc; ++k) {
+        restore();
+        A.small_max = (uint32_t)kTuneCandidates[k];
+        rc = enqueue_step(A, st);  // warm-up step (also loads the kernels)
+        cudaEventRecord(e0, st);
+        for (int it = 0; it < n_steps && !rc; ++it) rc = enqueue_step(A, st);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "autotune");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (ms) ms[k] = t / n_steps;
+        if (!rc && t < best) {
+            best = t;
+            best_v = kTuneCandidates[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    restore();
+    cudaFree(saved);
+    A.small_max = rc ? keep : (uint32_t)best_v;
+    if (chosen) *chosen = (int32_t)A.small_max;
+    if (rc) return rc;
+    return read_kernel_errors(A);
 }
 
 StepGraphs::~StepGraphs()
@@ -433,6 +512,27 @@ int cuba_init_riemann(cuba_sim* s, int64_t n, double T_left, double T_right, voi
     return cuba_init_thermal(s, n, R, 2, stream);
 }
 
+int cuba_init_hotspot(cuba_sim* s, int64_t n, double T0, double dT, double width, void* stream)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    if (!(T0 > 0.0) || !(dT >= 0.0) || !(width > 0.0)) return fail(CUBA_ERR_INVALID, "need T0 > 0, dT >= 0, width > 0");
+    if (n < 0 || n > (int64_t)s->A.pcap)
+        return fail(CUBA_ERR_CAPACITY, "n = %lld exceeds max_particles = %u", (long long)n, s->A.pcap);
+    cudaStream_t st = (cudaStream_t)stream;
+    s->desc.np = (uint32_t)n;
+    s->desc.p_off = 0;
+    s->desc.cell_off = 0;
+    s->desc.step = 0;
+    s->A.np = (uint32_t)n;
+    int rc = upload_desc(s, st);
+    if (!rc && launch_init_hotspot(s->A, s->desc, T0, dT, width, st))
+        rc = fail(CUBA_ERR_CUDA, "hot-spot sampling launch failed");
+    if (!rc) rc = settle_arena(s->A, st, nullptr);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "init_hotspot");
+    return rc;
+}
+
 int cuba_set_state(cuba_sim* s, const void* soa, int64_t n, void* stream)
 {
     if (!s || (!soa && n > 0)) return fail(CUBA_ERR_INVALID, "bad arguments");
@@ -539,6 +639,26 @@ int cuba_step_profiled(cuba_sim* s, int n_steps, double* phase_ms, void* stream)
     for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
     if (rc) return rc;
     return read_kernel_errors(s->A);
+}
+
+int cuba_set_small_max(cuba_sim* s, int32_t small_max)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    return set_small_max(s->A, small_max);
+}
+
+int cuba_get_small_max(const cuba_sim* s, int32_t* small_max)
+{
+    if (!s || !small_max) return fail(CUBA_ERR_INVALID, "bad arguments");
+    *small_max = (int32_t)s->A.small_max;
+    return CUBA_OK;
+}
+
+int cuba_autotune(cuba_sim* s, int n_steps, int32_t* chosen, double* ms_per_candidate, void* stream)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    return autotune_arena(s->A, n_steps, (cudaStream_t)stream, chosen, ms_per_candidate);
 }
 
 int cuba_observables(cuba_sim* s, double* T00, double* T0x, int32_t* counts, void* stream)

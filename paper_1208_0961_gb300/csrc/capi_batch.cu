@@ -347,6 +347,19 @@ int cuba_batch_get_step(cuba_batch* b, int32_t id, uint32_t* step)
     return CUBA_OK;
 }
 
+int cuba_batch_autotune(cuba_batch* b, int n_steps, int32_t* chosen, double* ms_per_candidate, void* stream)
+{
+    if (!b) return fail(CUBA_ERR_INVALID, "batch is NULL");
+    return autotune_arena(b->A, n_steps, (cudaStream_t)stream, chosen, ms_per_candidate);
+}
+
+int cuba_batch_set_small_max(cuba_batch* b, int32_t small_max)
+{
+    if (!b) return fail(CUBA_ERR_INVALID, "batch is NULL");
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    return set_small_max(b->A, small_max);
+}
+
 int cuba_batch_usage(const cuba_batch* b, int32_t* n_sims, int64_t* n_particles, int64_t* n_cells)
 {
     if (!b) return fail(CUBA_ERR_INVALID, "batch is NULL");

@@ -132,11 +132,15 @@ struct Arena {
     // tracing
     int trace = 0;
     uint32_t* trace_keys = nullptr;     // pcap
+    // cells with 2 <= n <= small_max take the warp-per-cell pair and resolve
+    // kernels (0: every cell takes the row-block path); at most 1024
+    uint32_t small_max = 32;
 };
 
 // ---- launchers (kernels_sort.cu) ----
 int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double* d_regions, int nreg,
                         const uint64_t* d_region_first, cudaStream_t st);
+int launch_init_hotspot(const Arena& A, const SimDesc& S, double T0, double dT, double width, cudaStream_t st);
 int launch_keys_only(const Arena& A, cudaStream_t st);
 int launch_stream_key(const Arena& A, cudaStream_t st);
 int launch_sort_and_bin(Arena& A, cudaStream_t st);   // keys in key[0] -> sorted state, cell_start

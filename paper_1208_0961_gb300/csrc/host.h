@@ -49,13 +49,15 @@ int sample_regions(Arena& A, int sim_index, const SimDesc& S, int64_t n, const c
                    const double* L, cudaStream_t st);
 int settle_arena(Arena& A, cudaStream_t st, int* realloc);
 int read_kernel_errors(Arena& A);
+int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms);
+int set_small_max(Arena& A, int32_t v);
 
 // Captured step graphs (one per ping-pong buffer) and what they were
 // captured for.
 struct StepGraphs {
     cudaGraphExec_t g[2] = {nullptr, nullptr};
     cudaStream_t capture = nullptr;
-    uint32_t np = 0, ncells = 0;
+    uint32_t np = 0, ncells = 0, small_max = 0;
     const void* acc = nullptr;
     int trace = 0, nsims = 0;
     void drop();

@@ -128,7 +128,7 @@ struct CellCtx {
 // Only the rare survivors draw their low 16 bits (block (step, cell, i,
 // TAG_FINE | j)), load momenta and evaluate P22; accepted pairs are appended
 // to the cell's list.
-template <typename T>
+template <typename T, bool kMark>
 __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
                                                uint32_t thr16, T C, const T* __restrict__ st, uint32_t pcap,
                                                const uint4* qw, const uint32_t* qi, const uint32_t* qg, uint32_t e0,
@@ -156,7 +156,7 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
             const T P = pair_p22<T>(C, st, pcap, cc.cbase + i, cc.cbase + j);
             if (u < P) {
                 const uint32_t slot = atomicAdd(&acc_count[cc.c], 1u);
-                if (slot == 0) active[atomicAdd(&counters[2], 1u)] = cc.c;
+                if (kMark && slot == 0) active[atomicAdd(&counters[2], 1u)] = cc.c;
                 if (slot < cc.room && (uint64_t)cc.list0 + slot < acc_cap) {
                     acc[(size_t)cc.list0 + slot] = ((unsigned long long)i << 32) | j;
                 } else {
@@ -168,6 +168,72 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
     }
 }
 
+// All pairs (i, j), i < j, of the rows [32 rb, 32 rb + 32) of one cell: one
+// lane per row walks the row's 16-pair Philox blocks two at a time; blocks
+// holding a byte <= thr8 are queued in the warp's shared-memory queue and
+// resolved 32 at a time.  kMark: the first accepted pair of the cell appends
+// it to the active-cell list (the small-cell path finds its cells by scanning).
+template <typename T, bool kMark>
+__device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32_t step, uint32_t thr8, uint32_t thr16,
+                                          T C, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap, uint4* qw,
+                                          uint32_t* qi, uint32_t* qg, uint32_t* __restrict__ acc_count,
+                                          unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                          uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                          unsigned long long* __restrict__ stats)
+{
+    constexpr int NB = kPairBlocksPerIter;
+    static_assert(kQueueCap >= 32 + 32 * NB, "a warp pushes up to 32 NB blocks onto at most 32 queued ones");
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t i = rb * kPairRows + lane;
+    const bool row_ok = i + 1 < cc.n;
+    PhiloxRow R;
+    R.init(step, cc.lc, i, K);
+    const uint32_t gfirst = (rb * kPairRows + 1) >> 4;
+    const uint32_t glast = (cc.n - 1) >> 4;
+    uint32_t qn = 0;  // warp-uniform number of queued blocks
+    for (uint32_t g = gfirst; g <= glast; g += NB) {
+        uint4 r[NB];
+        bool h[NB];
+        unsigned bal[NB];
+        unsigned any = 0;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            r[q] = (g + q <= glast) ? R.block(g + q, K)
+                                    : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+            h[q] = row_ok && any_byte_le(r[q], thr8);
+            bal[q] = __ballot_sync(kFull, h[q]);
+            any |= bal[q];
+        }
+        if (any) {
+            // up to 32 NB blocks are pushed below: drain to at most 32 first
+            while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
+                __syncwarp();
+                resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qi, qg, qn - 32, qn, acc_count,
+                                         acc, acc_cap, counters, active, stats);
+                __syncwarp();
+                qn -= 32;
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (h[q]) {
+                    const uint32_t slot = qn + (uint32_t)__popc(bal[q] & lt);
+                    qw[slot] = r[q];
+                    qi[slot] = i;
+                    qg[slot] = g + q;
+                }
+                qn += (uint32_t)__popc(bal[q]);
+            }
+        }
+    }
+    if (qn) {
+        __syncwarp();
+        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qi, qg, 0, qn, acc_count, acc, acc_cap,
+                                 counters, active, stats);
+        __syncwarp();
+    }
+}
+
 #if CUBA_PAIR_MIN_BLOCKS > 0
 #define CUBA_PAIR_BOUNDS __launch_bounds__(kPairThreads, CUBA_PAIR_MIN_BLOCKS)
 #else
@@ -175,24 +241,19 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
 #endif
 
 template <typename T>
-__global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, int nsims,
-                                                            const T* __restrict__ st, uint32_t pcap,
-                                                            const uint32_t* __restrict__ cell_start,
-                                                            const uint2* __restrict__ work, uint32_t ncells,
-                                                            uint32_t* __restrict__ acc_count,
-                                                            unsigned long long* __restrict__ acc, uint64_t acc_cap,
-                                                            uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
-                                                            unsigned long long* __restrict__ stats)
+__global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, int nsims, const T* __restrict__ st,
+                                            uint32_t pcap, const uint32_t* __restrict__ cell_start,
+                                            const uint2* __restrict__ work, uint32_t ncells,
+                                            uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
+                                            uint64_t acc_cap, uint32_t* __restrict__ counters,
+                                            uint32_t* __restrict__ active, unsigned long long* __restrict__ stats)
 {
     constexpr int kWarps = kPairThreads / 32;
-    constexpr int NB = kPairBlocksPerIter;
-    static_assert(kQueueCap >= 32 + 32 * NB, "a warp pushes up to 32 NB blocks onto at most 32 queued ones");
     __shared__ uint4 q_w[kWarps][kQueueCap];
     __shared__ uint32_t q_i[kWarps][kQueueCap];
     __shared__ uint32_t q_g[kWarps][kQueueCap];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const uint32_t total = work[ncells].x;
     if ((uint64_t)work[ncells].y > acc_cap) {
         // the lists of this step do not fit the allocation: report, do nothing
@@ -234,57 +295,54 @@ __global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, i
         cc.list0 = w0.y;
         cc.room = w1.y - w0.y;
         const uint32_t rb = item - w0.x;
-        const uint32_t step = S.step, thr8 = S.thr8, thr16 = S.thr16;
-        const T C = sim_C<T>(S);
         const PhiloxKey K = philox_schedule(S.key0, S.key1);
+        pair_rows<T, true>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_i[w], q_g[w],
+                           acc_count, acc, acc_cap, counters, active, stats);
+    }
+}
 
-        const uint32_t i = rb * kPairRows + lane;
-        const bool row_ok = i + 1 < cc.n;
-        PhiloxRow R;
-        R.init(step, cc.lc, i, K);
-        const uint32_t gfirst = (rb * kPairRows + 1) >> 4;
-        const uint32_t glast = (cc.n - 1) >> 4;
-        uint32_t qn = 0;  // warp-uniform number of queued blocks
-        for (uint32_t g = gfirst; g <= glast; g += NB) {
-            uint4 r[NB];
-            bool h[NB];
-            unsigned bal[NB];
-            unsigned any = 0;
-#pragma unroll
-            for (int q = 0; q < NB; ++q) {
-                r[q] = (g + q <= glast) ? R.block(g + q, K)
-                                        : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-                h[q] = row_ok && any_byte_le(r[q], thr8);
-                bal[q] = __ballot_sync(kFull, h[q]);
-                any |= bal[q];
-            }
-            if (any) {
-                // up to 32 NB blocks are pushed below: drain to at most 32 first
-                while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
-                    __syncwarp();
-                    resolve_blocks<T>(cc, K, step, thr8, thr16, C, st, pcap, q_w[w], q_i[w], q_g[w], qn - 32, qn, acc_count,
-                                      acc, acc_cap, counters, active, stats);
-                    __syncwarp();
-                    qn -= 32;
-                }
-#pragma unroll
-                for (int q = 0; q < NB; ++q) {
-                    if (h[q]) {
-                        const uint32_t slot = qn + (uint32_t)__popc(bal[q] & lt);
-                        q_w[w][slot] = r[q];
-                        q_i[w][slot] = i;
-                        q_g[w][slot] = g + q;
-                    }
-                    qn += (uint32_t)__popc(bal[q]);
-                }
-            }
-        }
-        if (qn) {
-            __syncwarp();
-            resolve_blocks<T>(cc, K, step, thr8, thr16, C, st, pcap, q_w[w], q_i[w], q_g[w], 0, qn, acc_count, acc, acc_cap,
-                              counters, active, stats);
-            __syncwarp();
-        }
+// Small cells (2 <= n <= small_max): one warp per cell, all its rows, found
+// by a grid-stride scan over the cells (no work queue, no per-cell atomic).
+template <typename T>
+__global__ void __launch_bounds__(kPairThreads) k_pair_small(const SimDesc* __restrict__ sims, int nsims,
+                                                             const T* __restrict__ st, uint32_t pcap,
+                                                             const uint32_t* __restrict__ cell_start,
+                                                             const uint2* __restrict__ work, uint32_t ncells,
+                                                             uint32_t small_max, uint32_t* __restrict__ acc_count,
+                                                             unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                             uint32_t* __restrict__ counters,
+                                                             uint32_t* __restrict__ active,
+                                                             unsigned long long* __restrict__ stats)
+{
+    constexpr int kWarps = kPairThreads / 32;
+    __shared__ uint4 q_w[kWarps][kQueueCap];
+    __shared__ uint32_t q_i[kWarps][kQueueCap];
+    __shared__ uint32_t q_g[kWarps][kQueueCap];
+    const int w = threadIdx.x >> 5;
+    if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
+    const uint32_t nwarps = gridDim.x * kWarps;
+    for (uint32_t c = blockIdx.x * kWarps + w; c < ncells; c += nwarps) {
+        const uint32_t cbase = cell_start[c];
+        const uint32_t n = cell_start[c + 1] - cbase;
+        if (n < 2 || n > small_max) continue;
+        const int s = sim_of_cell(sims, nsims, c);
+        const SimDesc& S = sims[s];
+        if (!(S.C > 0.0)) continue;
+        CellCtx cc;
+        cc.c = c;
+        cc.s = s;
+        cc.slot = S.stat_slot;
+        cc.lc = c - S.cell_off;
+        cc.cbase = cbase;
+        cc.n = n;
+        const uint2 w0 = work[c], w1 = work[c + 1];
+        cc.list0 = w0.y;
+        cc.room = w1.y - w0.y;
+        const PhiloxKey K = philox_schedule(S.key0, S.key1);
+        const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
+        for (uint32_t rb = 0; rb < nrb; ++rb)
+            pair_rows<T, false>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_i[w], q_g[w],
+                                acc_count, acc, acc_cap, counters, active, stats);
     }
 }
 
@@ -529,6 +587,102 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(const SimDesc* __re
     }
 }
 
+// A6-A7 for small cells (n <= small_max <= 1024) with at most 32 accepted
+// pairs: one warp per cell, found by a grid-stride scan.  The list is sorted
+// by rank counting across the lanes, the greedy matching taken by lane 0 on a
+// shared-memory bitmap of the cell, and the kinematics applied one pair per
+// lane.  Small cells with more accepted pairs are handed to the block path by
+// appending them to the active-cell list.  Counters are summed per warp and
+// flushed once per simulation change.
+template <typename T>
+__global__ void __launch_bounds__(256) k_resolve_small(const SimDesc* __restrict__ sims, int nsims, T* __restrict__ st,
+                                                       uint32_t pcap, const uint32_t* __restrict__ cell_start,
+                                                       const uint2* __restrict__ work, uint32_t ncells,
+                                                       uint32_t small_max, const uint32_t* __restrict__ acc_count,
+                                                       unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                       uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                       unsigned long long* __restrict__ stats)
+{
+    constexpr int kWarps = 8;
+    __shared__ unsigned long long sl[kWarps][32];
+    __shared__ uint32_t sbits[kWarps][32];
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * kWarps;
+    uint32_t cur_slot = 0xFFFFFFFFu;
+    unsigned long long a_acc = 0, a_exe = 0, a_64 = 0;
+    for (uint32_t c = blockIdx.x * kWarps + w; c < ncells; c += nwarps) {
+        const uint32_t cnt = acc_count[c];
+        if (cnt == 0) continue;
+        const uint32_t cbase = cell_start[c];
+        const uint32_t n = cell_start[c + 1] - cbase;
+        if (n < 2 || n > small_max) continue;
+        const uint2 w0 = work[c], w1 = work[c + 1];
+        const uint32_t room = w1.y - w0.y;
+        uint32_t m = cnt < room ? cnt : room;
+        if ((uint64_t)w0.y + m > acc_cap) m = (w0.y < acc_cap) ? (uint32_t)(acc_cap - w0.y) : 0u;
+        if (m > 32) {
+            if (lane == 0) active[atomicAdd(&counters[2], 1u)] = c;
+            continue;
+        }
+        const int s = sim_of_cell(sims, nsims, c);
+        const SimDesc& S = sims[s];
+        const uint32_t slot = S.stat_slot;
+        if (slot != cur_slot) {
+            if (lane == 0 && cur_slot != 0xFFFFFFFFu) {
+                atomicAdd(&stats[cur_slot * kStatCount + kStatAccepted], a_acc);
+                atomicAdd(&stats[cur_slot * kStatCount + kStatExecuted], a_exe);
+                if (a_64) atomicAdd(&stats[cur_slot * kStatCount + kStatFp64Boosts], a_64);
+            }
+            a_acc = a_exe = a_64 = 0;
+            cur_slot = slot;
+        }
+        unsigned long long* gl = acc + w0.y;
+        const unsigned long long v = lane < m ? gl[lane] : ~0ull;
+        uint32_t rank = 0;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) rank += (__shfl_sync(kFull, v, k) < v) ? 1u : 0u;
+        if (lane < m) sl[w][rank] = v;
+        for (uint32_t k = lane; k < (n + 31) / 32; k += 32) sbits[w][k] = 0u;
+        __syncwarp();
+        uint32_t ne = 0;
+        if (lane == 0) {
+            for (uint32_t k = 0; k < m; ++k) {
+                const unsigned long long e = sl[w][k];
+                const uint32_t i = (uint32_t)(e >> 32), j = (uint32_t)e;
+                const uint32_t bi = (sbits[w][i >> 5] >> (i & 31)) & 1u;
+                const uint32_t bj = (sbits[w][j >> 5] >> (j & 31)) & 1u;
+                if (bi | bj) continue;
+                sbits[w][i >> 5] |= 1u << (i & 31);
+                sbits[w][j >> 5] |= 1u << (j & 31);
+                sl[w][k] = e | kExecFlag;
+                ++ne;
+            }
+        }
+        __syncwarp();
+        uint32_t n64 = 0;
+        if (lane < m) {
+            const unsigned long long e = sl[w][lane];
+            if (e & kExecFlag) {
+                const uint32_t i = (uint32_t)(e >> 32) & 0x7FFFFFFFu, j = (uint32_t)e;
+                const PhiloxKey K = philox_schedule(S.key0, S.key1);
+                n64 = (uint32_t)collide_state<T>(S, K, c - S.cell_off, i, j, st, pcap, cbase + i, cbase + j);
+            }
+            gl[lane] = e;
+        }
+        n64 = __reduce_add_sync(kFull, n64);
+        a_acc += cnt;
+        a_exe += __shfl_sync(kFull, ne, 0);
+        a_64 += n64;
+        __syncwarp();
+    }
+    if (lane == 0 && cur_slot != 0xFFFFFFFFu) {
+        atomicAdd(&stats[cur_slot * kStatCount + kStatAccepted], a_acc);
+        atomicAdd(&stats[cur_slot * kStatCount + kStatExecuted], a_exe);
+        if (a_64) atomicAdd(&stats[cur_slot * kStatCount + kStatFp64Boosts], a_64);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -547,17 +701,39 @@ static unsigned pair_grid()
     return g;
 }
 
+template <typename T>
+static unsigned small_grid()
+{
+    static unsigned g = 0;
+    if (!g) {
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_small<T>, kPairThreads, 0);
+        if (per < 1) per = 1;
+        g = (unsigned)(per * sm_count());
+    }
+    return g;
+}
+
 int launch_pair_tile(const Arena& A, cudaStream_t st)
 {
     if (A.ncells == 0) return 0;
-    if (A.precision == 1)
+    if (A.precision == 1) {
+        if (A.small_max)
+            k_pair_small<double><<<small_grid<double>(), kPairThreads, 0, st>>>(
+                A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells,
+                A.small_max, A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats);
         k_pair_tile<double><<<pair_grid<double>(), kPairThreads, 0, st>>>(
             A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count,
             A.acc, A.acc_capacity, A.counters, A.active, A.stats);
-    else
+    } else {
+        if (A.small_max)
+            k_pair_small<float><<<small_grid<float>(), kPairThreads, 0, st>>>(
+                A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells,
+                A.small_max, A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats);
         k_pair_tile<float><<<pair_grid<float>(), kPairThreads, 0, st>>>(
             A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count,
             A.acc, A.acc_capacity, A.counters, A.active, A.stats);
+    }
     return last_err();
 }
 
@@ -576,6 +752,8 @@ int kernels_init()
         return -1;
     pair_grid<double>();
     pair_grid<float>();
+    small_grid<double>();
+    small_grid<float>();
     sm_count();
     done = true;
     return 0;
@@ -586,6 +764,17 @@ int launch_resolve(const Arena& A, cudaStream_t st)
     if (A.ncells == 0) return 0;
     const size_t smem = kResolveSmemBytes;
     const unsigned g = (unsigned)(sm_count() * 4);
+    if (A.small_max) {
+        const unsigned gs = (unsigned)(sm_count() * 8);
+        if (A.precision == 1)
+            k_resolve_small<double><<<gs, 256, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, A.cell_start,
+                                                         A.cell_work, A.ncells, A.small_max, A.acc_count, A.acc,
+                                                         A.acc_capacity, A.counters, A.active, A.stats);
+        else
+            k_resolve_small<float><<<gs, 256, 0, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap, A.cell_start,
+                                                        A.cell_work, A.ncells, A.small_max, A.acc_count, A.acc,
+                                                        A.acc_capacity, A.counters, A.active, A.stats);
+    }
     if (A.precision == 1)
         k_resolve<double><<<g, kResolveThreads, smem, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap,
                                                            A.cell_start, A.cell_work, A.acc_count, A.acc, A.counters,

@@ -146,6 +146,53 @@ __global__ void __launch_bounds__(256) k_init_thermal(SimDesc S, T* __restrict__
     }
 }
 
+// Hot-spot state: T(r) = T0 + dT exp(-|r - centre|^2 / (2 w^2)), density
+// proportional to T(r)^3 by rejection (try k draws the block
+// (STEP_INIT, g, 0, 2 + k): a uniform position and the acceptance variate;
+// after 64 rejected tries the last position is kept), momentum from the
+// thermal blocks (…, 0) and (…, 1) at the local T(r).
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_hotspot(SimDesc S, T* __restrict__ st, uint32_t pcap, double T0,
+                                                      double dT, double width)
+{
+    const PhiloxKey K = philox_schedule(S.key0, S.key1);
+    const double Tmax = T0 + dT;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < S.np; g += stride) {
+        double pos[3] = {0.0, 0.0, 0.0};
+        double Tl = T0;
+        for (uint32_t k = 0; k < 64; ++k) {
+            const uint4 t = philox4x32_10(make_uint4(kStepInit, g, 0u, 2u + k), K);
+            const uint32_t tw[3] = {t.x, t.y, t.z};
+            double r2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                pos[a] = __dmul_rn(open01(tw[a]), S.L[a]);
+                const double d = __dsub_rn(pos[a], __dmul_rn(0.5, S.L[a]));
+                r2 = __dadd_rn(r2, __dmul_rn(d, d));
+            }
+            Tl = T0 + dT * exp(-r2 / (2.0 * width * width));
+            const double ratio = Tl / Tmax;
+            if (open01(t.w) < ratio * ratio * ratio) break;
+        }
+        const uint4 a = philox4x32_10(make_uint4(kStepInit, g, 0u, 0u), K);
+        const uint4 b = philox4x32_10(make_uint4(kStepInit, g, 0u, 1u), K);
+        const double E = -Tl * log(open01(a.w) * open01(b.x) * open01(b.y));
+        const double ct = 2.0 * open01(b.z) - 1.0;
+        const double stt = sqrt((1.0 - ct) * (1.0 + ct));
+        const double phi = 2.0 * 3.141592653589793 * open01(b.w);
+        double sp, cp;
+        sincos(phi, &sp, &cp);
+        const double mom[3] = {E * stt * cp, E * stt * sp, E * ct};
+        const uint32_t o = S.p_off + g;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            st[(size_t)ax * pcap + o] = (T)pos[ax];
+            st[(size_t)(3 + ax) * pcap + o] = (T)mom[ax];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Device-wide exclusive scan (reduce, scan partials, apply)
 // ---------------------------------------------------------------------------
@@ -406,7 +453,7 @@ __device__ __forceinline__ uint32_t list_room(double C, uint32_t n)
 
 __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ sims, int nsims,
                                                    const uint32_t* __restrict__ cell_start, uint2* __restrict__ work,
-                                                   uint32_t* __restrict__ acc_count, uint32_t ncells,
+                                                   uint32_t* __restrict__ acc_count, uint32_t ncells, uint32_t small_max,
                                                    uint32_t* __restrict__ counters, unsigned long long* __restrict__ stats,
                                                    int count_pairs)
 {
@@ -417,20 +464,37 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
         counters[2] = 0;  // active cells
         work[ncells] = make_uint2(0, 0);
     }
+    // pair tests summed per thread and simulation, flushed on a change
+    uint32_t cur_slot = 0xFFFFFFFFu;
+    unsigned long long tests = 0;
     for (uint32_t c = t0; c < ncells; c += stride) {
         const int s = sim_of_cell(sims, nsims, c);
         const SimDesc& S = sims[s];
         const uint32_t n = cell_start[c + 1] - cell_start[c];
         uint32_t items = 0, room = 0;
         if (n >= 2 && S.C > 0.0) {
-            items = (n - 1 + kPairRows - 1) / kPairRows;
+            if (n > small_max) items = (n - 1 + kPairRows - 1) / kPairRows;
             room = list_room(S.C, n);
-            if (count_pairs)
-                atomicAdd(&stats[S.stat_slot * kStatCount + kStatPairTests], (unsigned long long)n * (n - 1) / 2);
+            if (count_pairs) {
+                if (S.stat_slot != cur_slot) {
+                    if (tests) atomicAdd(&stats[cur_slot * kStatCount + kStatPairTests], tests);
+                    tests = 0;
+                    cur_slot = S.stat_slot;
+                }
+                tests += (unsigned long long)n * (n - 1) / 2;
+            }
         }
         work[c] = make_uint2(items, room);
         acc_count[c] = 0;
     }
+    // one atomic per warp and simulation
+    const unsigned mask = __activemask();
+    const unsigned peers = __match_any_sync(mask, cur_slot);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long sum = 0;
+    for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, tests, __ffs(m) - 1);
+    if ((int)(threadIdx.x & 31) == leader && cur_slot != 0xFFFFFFFFu && sum)
+        atomicAdd(&stats[cur_slot * kStatCount + kStatPairTests], sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -591,6 +655,17 @@ int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double*
     return last_err();
 }
 
+int launch_init_hotspot(const Arena& A, const SimDesc& S, double T0, double dT, double width, cudaStream_t st)
+{
+    if (S.np == 0) return 0;
+    const unsigned g = grid_for(S.np, 256, 8);
+    if (A.precision == 1)
+        k_init_hotspot<double><<<g, 256, 0, st>>>(S, (double*)A.st[A.cur], A.pcap, T0, dT, width);
+    else
+        k_init_hotspot<float><<<g, 256, 0, st>>>(S, (float*)A.st[A.cur], A.pcap, T0, dT, width);
+    return last_err();
+}
+
 int launch_keys_only(const Arena& A, cudaStream_t st)
 {
     if (A.np == 0) return 0;
@@ -656,8 +731,8 @@ int launch_sort_and_bin(Arena& A, cudaStream_t st)
 int launch_cell_prep(const Arena& A, cudaStream_t st, int count_pairs)
 {
     const unsigned g = grid_for(A.ncells, 256, 8);
-    k_cell_prep<<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.cell_start, A.cell_work, A.acc_count, A.ncells, A.counters, A.stats,
-                                   count_pairs);
+    k_cell_prep<<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.cell_start, A.cell_work, A.acc_count, A.ncells, A.small_max,
+                                   A.counters, A.stats, count_pairs);
     if (last_err()) return -1;
     return exclusive_scan<uint2, Uint2Add>(A.cell_work, (size_t)A.ncells + 1, make_uint2(0, 0), Uint2Add(), A.scan_tmp,
                                            A.scan_tmp_bytes, st);

@@ -85,6 +85,7 @@ def load(build_if_missing=True):
         "cuba_destroy": (None, [vp]),
         "cuba_init_thermal": (C.c_int, [vp, C.c_int64, C.POINTER(cuba_region), C.c_int, vp]),
         "cuba_init_riemann": (C.c_int, [vp, C.c_int64, C.c_double, C.c_double, vp]),
+        "cuba_init_hotspot": (C.c_int, [vp, C.c_int64, C.c_double, C.c_double, C.c_double, vp]),
         "cuba_set_state": (C.c_int, [vp, vp, C.c_int64, vp]),
         "cuba_get_state": (C.c_int, [vp, vp, vp]),
         "cuba_sizes": (C.c_int, [vp, i64p, i64p]),
@@ -114,6 +115,11 @@ def load(build_if_missing=True):
         "cuba_batch_get_step": (C.c_int, [vp, C.c_int32, u32p]),
         "cuba_batch_usage": (C.c_int, [vp, C.POINTER(C.c_int32), i64p, i64p]),
         "cuba_batch_bytes": (C.c_int64, [C.POINTER(cuba_batch_config)]),
+        "cuba_set_small_max": (C.c_int, [vp, C.c_int32]),
+        "cuba_get_small_max": (C.c_int, [vp, C.POINTER(C.c_int32)]),
+        "cuba_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]),
+        "cuba_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]),
+        "cuba_batch_set_small_max": (C.c_int, [vp, C.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -196,6 +202,10 @@ def cuba_init_riemann(sim, n, T_left, T_right, stream=None):
     _check(load().cuba_init_riemann(sim, int(n), float(T_left), float(T_right), _stream_ptr(stream)))
 
 
+def cuba_init_hotspot(sim, n, T0, dT, width, stream=None):
+    _check(load().cuba_init_hotspot(sim, int(n), float(T0), float(dT), float(width), _stream_ptr(stream)))
+
+
 def cuba_set_state(sim, soa, n, stream=None):
     _check(load().cuba_set_state(sim, _ptr(soa), int(n), _stream_ptr(stream)))
 
@@ -272,6 +282,40 @@ def cuba_bin_noalloc(params, xyz, n, perm, cell_start, stream=None):
     with no allocation inside the library (see include/cuba.h)."""
     _check(load().cuba_bin_noalloc(C.byref(params), _ptr(xyz), int(n), _ptr(perm), _ptr(cell_start),
                                    _stream_ptr(stream)))
+
+
+# ---- launch shape and autotuner ---------------------------------------------
+
+TUNE_CANDIDATES = (0, 16, 32, 64, 128, 256, 512, 1024)
+
+
+def cuba_set_small_max(sim, v):
+    _check(load().cuba_set_small_max(sim, int(v)))
+
+
+def cuba_get_small_max(sim):
+    v = C.c_int32()
+    _check(load().cuba_get_small_max(sim, C.byref(v)))
+    return v.value
+
+
+def cuba_autotune(sim, n_steps=2, stream=None):
+    """Returns (chosen small_max, {candidate: ms per step})."""
+    v = C.c_int32()
+    ms = (C.c_double * len(TUNE_CANDIDATES))()
+    _check(load().cuba_autotune(sim, int(n_steps), C.byref(v), ms, _stream_ptr(stream)))
+    return v.value, dict(zip(TUNE_CANDIDATES, list(ms)))
+
+
+def cuba_batch_autotune(b, n_steps=2, stream=None):
+    v = C.c_int32()
+    ms = (C.c_double * len(TUNE_CANDIDATES))()
+    _check(load().cuba_batch_autotune(b, int(n_steps), C.byref(v), ms, _stream_ptr(stream)))
+    return v.value, dict(zip(TUNE_CANDIDATES, list(ms)))
+
+
+def cuba_batch_set_small_max(b, v):
+    _check(load().cuba_batch_set_small_max(b, int(v)))
 
 
 # ---- batches ---------------------------------------------------------------
@@ -465,6 +509,9 @@ class Sim:
 
     def init_riemann(self, n, T_left, T_right, stream=None):
         cuba_init_riemann(self.h, n, T_left, T_right, stream)
+
+    def init_hotspot(self, n, T0, dT, width, stream=None):
+        cuba_init_hotspot(self.h, n, T0, dT, width, stream)
 
     def set_state(self, st, stream=None):
         import numpy as np

@@ -85,3 +85,19 @@ def riemann_1d(n_particles, n_cells, dt, sigma_mb, T_left=0.4, T_right=0.32, L=(
 
 RIEMANN_SMALL = dict(name="riemann-1d-20k", n=20000, n_cells=100, dt=0.05, sigma_mb=10.0, steps=100)
 RIEMANN_16M = dict(name="riemann-1d-16M", n=16_000_000, n_cells=2000, dt=0.0025, sigma_mb=10.0, steps=500)
+
+
+def hotspot_3d(n_particles, cells_per_axis, dt, sigma_mb, L=12.8, T0=0.4, dT=0.2, width=1.0):
+    """3D thermal box with a Gaussian hot spot, T(r) = T0 + dT exp(-r^2/2w^2)
+    about the centre, density ∝ T^3.  N_test from the physical number
+    g/(pi^2 (hbar c)^3) ∫ T(r)^3 dV, the integral in closed form (the Gaussian
+    terms lie well inside the box)."""
+    Z = T0 ** 3 * L ** 3
+    for k, c in ((1, 3), (2, 3), (3, 1)):
+        Z += c * T0 ** (3 - k) * dT ** k * (2 * math.pi * width * width / k) ** 1.5
+    n_phys = GLUON_DOF * Z / (math.pi ** 2 * HBARC_GEV_FM ** 3)
+    return dict(L=(L, L, L), n_cells=(cells_per_axis,) * 3, dt=dt, sigma_fm2=sigma_mb * FM2_PER_MB,
+                n_test=n_particles / n_phys, n=n_particles, T0=T0, dT=dT, width=width)
+
+
+HOTSPOT_64M = dict(name="hotspot-3d-64M", n=64_000_000, cells=128, dt=0.01, sigma_mb=5.0, steps=200)

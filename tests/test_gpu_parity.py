@@ -29,13 +29,15 @@ def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0):
     return p, op
 
 
-def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_index=3):
+def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_index=3, small_max=None):
     p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed)
     dtype = np.float32 if fp32 else np.float64
     st0 = st0.astype(dtype)
     n = st0.shape[1]
     sim = cuba.Sim(p, max(n, 1))
     try:
+        if small_max is not None:
+            cuba.cuba_set_small_max(sim.h, small_max)
         sim.set_state(st0)
         cuba.cuba_trace_enable(sim.h, True)
         cuba.cuba_set_step(sim.h, step_index)
@@ -182,3 +184,106 @@ def test_multi_step_energy_conservation_fp64_and_fp32():
             assert st["steps"] == 100 and st["overflow"] == 0 and st["executed"] > 0
         finally:
             sim.close()
+
+
+def test_init_hotspot_matches_oracle_sampling():
+    L = (6.4, 6.4, 6.4)
+    n = 200000
+    p, op = _pair(L, (32, 32, 32), 0.05, 0.5, 100.0, False, 77)
+    sim = cuba.Sim(p, n)
+    try:
+        sim.init_hotspot(n, 0.4, 0.2, 1.0)
+        g = sim.get_state()
+    finally:
+        sim.close()
+    o = O.init_hotspot(op, n, 0.4, 0.2, 1.0)
+    o, _, _, _ = O.sort(op, o)
+    # positions are exact arithmetic; only an acceptance decision that falls
+    # within an ulp of exp() could differ between the two math libraries
+    differ = np.any(g[:3] != o[:3], axis=0)
+    assert differ.sum() <= max(2, n // 100000)
+    E = np.sqrt((o[3:] ** 2).sum(axis=0))
+    ok = ~differ
+    assert np.max(np.abs(g[3:, ok] - o[3:, ok]).max(axis=0) / E[ok]) < 1e-12
+
+
+def test_full_size_riemann_16M_sampled():
+    """The bench workload at full size (16 M particles, 2000 cells, FP32), one
+    step in the bench's launch configuration: keys, permutation, cell_start and
+    positions of all particles against the oracle's single-precision mirror;
+    accepted pairs of sampled rows and of one whole cell; the executed set of
+    that cell is the greedy matching of its accepted pairs; its momenta follow
+    the oracle's kinematics to 1e-5 of the pair energy."""
+    cfg = W.riemann_1d(16_000_000, 2000, 0.0025, 10.0)
+    st0 = W.thermal_state(16_000_000, cfg["regions"], seed=21).astype(np.float32)
+    p, op = _pair(cfg["L"], cfg["n_cells"], cfg["dt"], cfg["sigma_fm2"], cfg["n_test"], True, 0)
+    sim = cuba.Sim(p, 16_000_000)
+    try:
+        sim.set_state(st0)
+        cuba.cuba_trace_enable(sim.h, True)
+        sim.step(1)
+        g = sim.get_state()
+        keys, perm, cs, pairs, exe = sim.trace()
+    finally:
+        sim.close()
+    # stream + key + sort of every particle: the oracle's step with sigma = 0
+    op0 = O.make_params(L=cfg["L"], n=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=0.0, n_test=cfg["n_test"],
+                        fp32=True, seed=0)
+    o_in, _, _, _ = O.sort(op0, st0.astype(np.float64))
+    mid, r0 = O.step(op0, 0, o_in)
+    assert np.array_equal(keys, r0.keys.astype(np.uint32))
+    assert np.array_equal(perm.astype(np.int64), r0.perm)
+    assert np.array_equal(cs.astype(np.int64), r0.cell_start)
+    assert np.array_equal(g[:3].astype(np.float64), mid[:3])
+    # sampled rows of several cells
+    rng = np.random.default_rng(5)
+    cells = np.concatenate([rng.integers(0, 1000, 3), rng.integers(1000, 2000, 3)])
+    for c in cells:
+        b, e = int(cs[c]), int(cs[c + 1])
+        mom = mid[3:, b:e]
+        gp = pairs[pairs[:, 0] == c]
+        for i in rng.integers(0, e - b - 1, 20):
+            want = O.row_accept(op, 0, int(c), mom, int(i), 0, e - b)
+            got = gp[gp[:, 1] == i][:, 2]
+            assert np.array_equal(np.sort(got), want), (c, i)
+    # one whole cell of the right half: accepted set, greedy matching, momenta
+    c = 1500
+    b, e = int(cs[c]), int(cs[c + 1])
+    mom = mid[3:, b:e]
+    acc = O.cell_accept(op, 0, c, mom)
+    sel = pairs[:, 0] == c
+    assert np.array_equal(pairs[sel][:, 1:], acc)
+    used = set()
+    for (i, j), x in zip(acc.tolist(), exe[sel].tolist()):
+        want = i not in used and j not in used
+        assert x == want
+        if want:
+            used.update((i, j))
+            ok, pi, pj = O.kinematics([0, 0], 0, c, i, j, mom[:, i], mom[:, j])
+            s = np.linalg.norm(mom[:, i]) + np.linalg.norm(mom[:, j])
+            assert np.max(np.abs(g[3:, b + i] - pi)) <= 1e-5 * s
+            assert np.max(np.abs(g[3:, b + j] - pj)) <= 1e-5 * s
+    assert len(used) > 0
+
+
+@pytest.mark.parametrize("small_max", [0, 32, 1024])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_small_cells_both_paths(fp32, small_max):
+    """About 20 particles per cell (3D): the warp-per-cell pair and resolve
+    kernels (small_max >= 32) and the item path (0) give the oracle's step."""
+    L = (1.6, 1.6, 1.6)
+    regs = [((0.0, 0.0, 0.0), L, 0.4)]
+    st0 = W.thermal_state(81920, regs, seed=8)
+    # C = sigma dt / (N_test V_cell) = 0.0125
+    na, ne = _one_step_compare(L, (16, 16, 16), 0.05, 5e-4, 2.0, fp32, 31, st0, step_index=2, small_max=small_max)
+    assert na > 1000
+
+
+def test_small_cells_with_many_accepted_pairs_hand_over():
+    """Small cells whose accepted lists exceed 32 pairs go to the block path."""
+    L = (0.8, 0.8, 0.8)
+    regs = [((0.0, 0.0, 0.0), L, 0.4)]
+    st0 = W.thermal_state(15000, regs, seed=9)
+    # about 29 particles per cell, C = 0.15: about 60 accepted pairs per cell
+    na, ne = _one_step_compare(L, (8, 8, 8), 0.09, 1.0 / 3.0 * 1e-3, 0.2, False, 13, st0, small_max=64)
+    assert na > 32 * 512 * 0.5
