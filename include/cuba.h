@@ -224,6 +224,18 @@ int cuba_trace_get(cuba_sim* sim, uint32_t* keys, uint32_t* perm, uint32_t* cell
 int cuba_step_profiled(cuba_sim* sim, int n_steps, double* phase_ms, void* stream);
 
 /*
+ * The FP32 path's collision kinematics (A7) on given momenta: pair k is
+ * particles (2k, 2k+1) of cell 0 at step `step` (random direction from the
+ * Philox block (step, 0, 2k, 0x80000000 | (2k+1)) under `key`), boosted in
+ * FP32 unless its CM Lorentz factor exceeds gamma_fp64, then in FP64.
+ * pin/pout: device, 6 floats per pair (p_i then p_j); used_fp64: device, one
+ * int per pair.  Async.  For choosing and checking the FP64 threshold.
+ */
+int cuba_kinematics_fp32(const float* pin, int64_t npairs, uint64_t key, uint32_t step, double gamma_fp64,
+                         float* pout, int32_t* used_fp64, void* stream);
+
+/*
+ * Philox4x32-10 of the library's device implementation/*
  * Philox4x32-10 of the library's device implementation for n counters
  * (4 words each) under one key, into out (4 words each).  ctr and out are
  * device pointers.  Async.  For verifying the generator.

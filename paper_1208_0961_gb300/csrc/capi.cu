@@ -756,6 +756,22 @@ int cuba_trace_get(cuba_sim* s, uint32_t* keys, uint32_t* perm, uint32_t* cell_s
     return read_kernel_errors(s->A);
 }
 
+int cuba_kinematics_fp32(const float* pin, int64_t npairs, uint64_t key, uint32_t step, double gamma_fp64, float* pout,
+                         int32_t* used_fp64, void* stream)
+{
+    if (npairs < 0 || (npairs > 0 && (!pin || !pout || !used_fp64))) return fail(CUBA_ERR_INVALID, "bad arguments");
+    if (npairs > (int64_t)1 << 30) return fail(CUBA_ERR_INVALID, "too many pairs");
+    SimDesc S;
+    std::memset(&S, 0, sizeof(S));
+    S.key0 = (uint32_t)key;
+    S.key1 = (uint32_t)(key >> 32);
+    S.step = step;
+    S.gamma_fp64 = (float)gamma_fp64;
+    if (launch_kinematics_check(S, pin, npairs, pout, used_fp64, (cudaStream_t)stream))
+        return fail(CUBA_ERR_CUDA, "kinematics launch failed");
+    return CUBA_OK;
+}
+
 int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, void* stream)
 {
     if (n < 0 || (n > 0 && (!ctr || !out))) return fail(CUBA_ERR_INVALID, "bad arguments");

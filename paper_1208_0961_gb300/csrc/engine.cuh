@@ -157,6 +157,8 @@ int launch_bin_raw(const SimDesc& S, int precision, const void* xyz, uint32_t n,
 int launch_pair_tile(const Arena& A, cudaStream_t st);
 int launch_resolve(const Arena& A, cudaStream_t st);
 int kernels_init();   // attributes and launch shapes; call before any capture
+int launch_kinematics_check(const SimDesc& S, const float* pin, int64_t npairs, float* pout, int32_t* used64,
+                            cudaStream_t st);
 
 // number of radix passes for a key range
 inline int radix_passes(uint32_t ncells)

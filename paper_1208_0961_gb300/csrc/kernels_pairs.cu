@@ -683,6 +683,39 @@ __global__ void __launch_bounds__(256) k_resolve_small(const SimDesc* __restrict
     }
 }
 
+// Kinematics of pairs (2k, 2k+1) of cell 0 in the FP32 path with a given FP64
+// threshold, on caller-given momenta (verification of the threshold).
+__global__ void k_kinematics_check(SimDesc S, const float* __restrict__ pin, int64_t npairs, float* __restrict__ pout,
+                                   int32_t* __restrict__ used64)
+{
+    const PhiloxKey K = philox_schedule(S.key0, S.key1);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < npairs; k += (int64_t)gridDim.x * blockDim.x) {
+        // scratch state of two particles laid out as the SoA state (pcap = 2)
+        float st[12];
+        for (int a = 0; a < 3; ++a) {
+            st[0 + a * 2] = 0.f;
+            st[1 + a * 2] = 0.f;
+            st[6 + a * 2] = pin[6 * k + a];
+            st[7 + a * 2] = pin[6 * k + 3 + a];
+        }
+        const int u = collide_state<float>(S, K, 0u, (uint32_t)(2 * k), (uint32_t)(2 * k + 1), st, 2u, 0u, 1u);
+        for (int a = 0; a < 3; ++a) {
+            pout[6 * k + a] = st[6 + a * 2];
+            pout[6 * k + 3 + a] = st[7 + a * 2];
+        }
+        used64[k] = u;
+    }
+}
+
+int launch_kinematics_check(const SimDesc& S, const float* pin, int64_t npairs, float* pout, int32_t* used64,
+                            cudaStream_t st)
+{
+    if (npairs <= 0) return 0;
+    k_kinematics_check<<<(unsigned)((npairs + 255) / 256 < 4096 ? (npairs + 255) / 256 : 4096), 256, 0, st>>>(
+        S, pin, npairs, pout, used64);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------

@@ -115,6 +115,7 @@ def load(build_if_missing=True):
         "cuba_batch_get_step": (C.c_int, [vp, C.c_int32, u32p]),
         "cuba_batch_usage": (C.c_int, [vp, C.POINTER(C.c_int32), i64p, i64p]),
         "cuba_batch_bytes": (C.c_int64, [C.POINTER(cuba_batch_config)]),
+        "cuba_kinematics_fp32": (C.c_int, [vp, C.c_int64, C.c_uint64, C.c_uint32, C.c_double, vp, vp, vp]),
         "cuba_set_small_max": (C.c_int, [vp, C.c_int32]),
         "cuba_get_small_max": (C.c_int, [vp, C.POINTER(C.c_int32)]),
         "cuba_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]),
@@ -469,6 +470,11 @@ class Batch:
 
     def usage(self):
         return cuba_batch_usage(self.h)
+
+
+def cuba_kinematics_fp32(pin, npairs, key, step, gamma_fp64, pout, used_fp64, stream=None):
+    _check(load().cuba_kinematics_fp32(_ptr(pin), int(npairs), int(key) & 0xFFFFFFFFFFFFFFFF, int(step),
+                                       float(gamma_fp64), _ptr(pout), _ptr(used_fp64), _stream_ptr(stream)))
 
 
 def cuba_last_error():

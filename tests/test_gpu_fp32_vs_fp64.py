@@ -1,0 +1,79 @@
+"""FP32 state against the FP64 oracle (spec: the FP32-vs-FP64 error is
+stated for every result).  One step from the same FP32-representable state:
+  * cell keys: the FP32 positions differ from the FP64 ones by rounding, so a
+    key may differ only for a particle within 1e-5 of a cell face (in units of
+    the cell edge); the number of such particles is reported;
+  * accepted pairs, compared in the cells where both sorted orders agree:
+    every pair accepted on one side only has |u - P22_FP64| < 1e-6 C (the
+    band where FP32 rounding of v_rel can flip the decision);
+  * momenta of pairs executed on both sides: within 1e-5 of the pair energy.
+Run with -s to print the figures."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1208_0961_gb300 import cuba
+from paper_1208_0961_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_one_step_fp32_against_fp64_oracle():
+    cfg = W.riemann_1d(20000, 100, 0.05, 10.0)
+    st0 = W.thermal_state(20000, cfg["regions"], seed=31).astype(np.float32)
+    p = cuba.make_params(L=cfg["L"], n_cells=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
+                         n_test=cfg["n_test"], precision=cuba.CUBA_FP32, seed=9)
+    sim = cuba.Sim(p, 20000)
+    try:
+        sim.set_state(st0)
+        cuba.cuba_trace_enable(sim.h, True)
+        sim.step(1)
+        g = sim.get_state().astype(np.float64)
+        keys, perm, cs, pairs, exe = sim.trace()
+    finally:
+        sim.close()
+    op = O.make_params(L=cfg["L"], n=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
+                       n_test=cfg["n_test"], seed=9)
+    o_in, _, _, _ = O.sort(op, st0.astype(np.float64))
+    o_out, res = O.step(op, 0, o_in)
+    C = O.p22_scale(op)
+    # keys
+    bad_keys = np.nonzero(keys != res.keys)[0]
+    dxc = cfg["L"][0] / cfg["n_cells"][0]
+    # the oracle's streamed position of the mismatching particles lies near a face
+    inv = np.empty_like(res.perm)
+    inv[res.perm] = np.arange(len(res.perm))
+    xo = o_out[0][inv[bad_keys]]
+    frac = np.abs(xo / dxc - np.round(xo / dxc))
+    assert np.all(frac < 1e-5)
+    # accepted pairs in cells whose sorted order is the same on both sides
+    same = np.array([np.array_equal(perm[cs[c]:cs[c + 1]], res.perm[res.cell_start[c]:res.cell_start[c + 1]])
+                     for c in range(100)])
+    acc_g = set(map(tuple, pairs[np.isin(pairs[:, 0], np.nonzero(same)[0])].tolist()))
+    acc_o = set(map(tuple, res.accepted[np.isin(res.accepted[:, 0], np.nonzero(same)[0])].tolist()))
+    flips = acc_g ^ acc_o
+    key = [9, 0]
+    mid, _ = O.step(O.make_params(L=cfg["L"], n=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=0.0,
+                                  n_test=cfg["n_test"], seed=9), 0, o_in)
+    for c, i, j in flips:
+        b = res.cell_start[c]
+        pi, pj = mid[3:, b + i], mid[3:, b + j]
+        ni, nj = pi / np.linalg.norm(pi), pj / np.linalg.norm(pj)
+        P22 = C * 0.5 * np.sum((ni - nj) ** 2)
+        u = O.pair_word(key, 0, c, i, j) * 2.0 ** -32
+        assert abs(u - P22) < 1e-6 * C, (c, i, j, u, P22)
+    # momenta of pairs executed on both sides
+    ex_g = set(map(tuple, pairs[exe].tolist()))
+    both = [e for e in map(tuple, res.executed.tolist()) if e in ex_g and same[e[0]]]
+    worst = 0.0
+    for c, i, j in both:
+        bo = res.cell_start[c]
+        s = np.linalg.norm(o_out[3:, bo + i]) + np.linalg.norm(o_out[3:, bo + j])
+        worst = max(worst, np.abs(g[3:, cs[c] + i] - o_out[3:, bo + i]).max() / s,
+                    np.abs(g[3:, cs[c] + j] - o_out[3:, bo + j]).max() / s)
+    assert worst < 1e-5
+    print("\nFP32 vs FP64: %d of %d keys differ (all within 1e-5 dx of a face); %d of 100 cells compared; "
+          "%d accepted pairs differ, all inside |u - P22| < 1e-6 C; max momentum error %.2e of the pair energy "
+          "over %d pairs executed on both sides" % (len(bad_keys), len(keys), int(same.sum()), len(flips), worst,
+                                                     len(both)))
+    assert same.sum() >= 90 and len(both) > 1000
