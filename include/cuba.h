@@ -217,7 +217,9 @@ int cuba_trace_get(cuba_sim* sim, uint32_t* keys, uint32_t* perm, uint32_t* cell
  * Advance n_steps steps like cuba_step, but launched kernel by kernel (no
  * graph) with CUDA events between the phases; phase_ms (host, 6 doubles)
  * receives the summed device time of each phase over the steps:
- * [0] stream/reflect/key, [1] sort (radix passes + gather + cell_start),
+ * [0] stream/reflect/key with the first digit histogram, [1] the rest of
+ * the sort (scans, radix passes, the final pass that re-streams each particle
+ * into its sorted slot, cell_start),
  * [2] per-cell preparation, [3] pair tile, [4] conflicts + kinematics,
  * [5] step counter.  Synchronous.  For measurement.
  */

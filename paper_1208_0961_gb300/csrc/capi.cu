@@ -96,9 +96,10 @@ void arena_free(Arena& A)
 size_t scan_tmp_needed(uint32_t pcap, uint32_t ccap)
 {
     const size_t tiles = (pcap + kSortTile - 1) / kSortTile + 1;
-    const size_t n1 = (kRadixBins * tiles + kScanTile - 1) / kScanTile;
+    const size_t n1 = (kBinBins * tiles + kScanTile - 1) / kScanTile;
     const size_t n2 = ((size_t)ccap + 1 + kScanTile - 1) / kScanTile;
     size_t need = std::max(n1 * sizeof(uint32_t), n2 * sizeof(uint2));
+    need = std::max(need, bin_scan_bytes());
     return std::max<size_t>(need, 256 * 4 * sizeof(double)) + 256;
 }
 
@@ -121,7 +122,7 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
     if (!rc) rc = dalloc(&A.cell_work, ((size_t)ccap + 1) * sizeof(uint2), "cell_work");
     if (!rc) rc = dalloc(&A.acc_count, (size_t)ccap * 4, "acc_count");
     if (!rc) rc = dalloc(&A.active, (size_t)ccap * 4, "active");
-    A.radix_hist_cap = (uint32_t)(kRadixBins * ((pc + kSortTile - 1) / kSortTile + 1));
+    A.radix_hist_cap = (uint32_t)(2 * kBinBins * ((pc + kSortTile - 1) / kSortTile + 1));
     if (!rc) rc = dalloc(&A.radix_hist, (size_t)A.radix_hist_cap * 4, "radix_hist");
     A.scan_tmp_bytes = scan_tmp_needed(pcap, ccap);
     if (!rc) rc = dalloc(&A.scan_tmp, A.scan_tmp_bytes, "scan_tmp");
@@ -144,8 +145,7 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
 // capture).
 int enqueue_step(Arena& A, cudaStream_t st)
 {
-    if (launch_stream_key(A, st)) return fail(CUBA_ERR_CUDA, "stream/key launch failed");
-    if (launch_sort_and_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
+    if (launch_step_bin(A, st, nullptr)) return fail(CUBA_ERR_CUDA, "stream/sort launch failed");
     if (launch_cell_prep(A, st)) return fail(CUBA_ERR_CUDA, "cell preparation launch failed");
     if (launch_pair_tile(A, st)) return fail(CUBA_ERR_CUDA, "pair tile launch failed");
     if (launch_resolve(A, st)) return fail(CUBA_ERR_CUDA, "resolve launch failed");
@@ -616,9 +616,7 @@ int cuba_step_profiled(cuba_sim* s, int n_steps, double* phase_ms, void* stream)
     int rc = CUBA_OK;
     for (int it = 0; it < n_steps && !rc; ++it) {
         cudaEventRecord(ev[0], st);
-        if (launch_stream_key(A, st)) rc = fail(CUBA_ERR_CUDA, "stream/key launch failed");
-        cudaEventRecord(ev[1], st);
-        if (!rc && launch_sort_and_bin(A, st)) rc = fail(CUBA_ERR_CUDA, "sort launch failed");
+        if (launch_step_bin(A, st, ev[1])) rc = fail(CUBA_ERR_CUDA, "stream/sort launch failed");
         cudaEventRecord(ev[2], st);
         if (!rc && launch_cell_prep(A, st)) rc = fail(CUBA_ERR_CUDA, "cell preparation launch failed");
         cudaEventRecord(ev[3], st);

@@ -53,9 +53,14 @@ enum StatIdx {
 constexpr uint32_t kErrAccOverflow = 1u;   // accepted list ran out of room
 constexpr uint32_t kErrCapacity = 2u;      // list capacity of a step exceeds the allocation
 
-// Radix sort geometry: 8-bit digits, 256 threads x 16 keys per tile.
+// Radix sort geometry: 256 threads x 16 keys per tile; 8-bit digits for the
+// sort of a settled state, 11-bit digits for the sort inside a step (one pass
+// up to 2048 cells, two up to 2^22).
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kBinBits = 11;
+constexpr int kBinBins = 1 << kBinBits;
+constexpr int kBinChunks = 512;   // chunks of tiles of the digit-major histogram scan
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -120,7 +125,7 @@ struct Arena {
     uint32_t* acc_count = nullptr;      // ccap
     unsigned long long* acc = nullptr;  // accepted (i << 32 | j), per-cell segments
     uint64_t acc_capacity = 0;
-    uint32_t* radix_hist = nullptr;     // 256 * tiles
+    uint32_t* radix_hist = nullptr;     // digit histograms and their scan, 2 kBinBins * tiles
     uint32_t radix_hist_cap = 0;
     void* scan_tmp = nullptr;           // scan partial sums
     size_t scan_tmp_bytes = 0;
@@ -142,8 +147,18 @@ int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double*
                         const uint64_t* d_region_first, cudaStream_t st);
 int launch_init_hotspot(const Arena& A, const SimDesc& S, double T0, double dT, double width, cudaStream_t st);
 int launch_keys_only(const Arena& A, cudaStream_t st);
-int launch_stream_key(const Arena& A, cudaStream_t st);
 int launch_sort_and_bin(Arena& A, cudaStream_t st);   // keys in key[0] -> sorted state, cell_start
+int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st);
+int launch_cell_bounds(const uint32_t* skey, uint32_t np, uint32_t* cell_start, uint32_t ncells, cudaStream_t st);
+int scan_u32(uint32_t* data, size_t n, void* tmp, size_t tmp_bytes, cudaStream_t st);
+
+// ---- launchers (kernels_bin.cu) ----
+// A1-A4 of a step: streams st[cur] into the sorted st[cur ^ 1] (cur flips),
+// cell_start and, when tracing, the keys and the permutation.  after_stream
+// (may be null) is recorded once the streaming pass is done.
+int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream);
+int bin_kernels_init();
+size_t bin_scan_bytes();   // scratch the histogram scan needs in scan_tmp
 int launch_cell_prep(const Arena& A, cudaStream_t st, int count_pairs = 1);
 int launch_observables(const Arena& A, int sim, double* T00, double* T0x, int32_t* counts, cudaStream_t st);
 int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st);
@@ -160,12 +175,12 @@ int kernels_init();   // attributes and launch shapes; call before any capture
 int launch_kinematics_check(const SimDesc& S, const float* pin, int64_t npairs, float* pout, int32_t* used64,
                             cudaStream_t st);
 
-// number of radix passes for a key range
-inline int radix_passes(uint32_t ncells)
+// number of radix passes of `digit_bits` bits for keys below ncells
+inline int radix_passes(uint32_t ncells, int digit_bits = kRadixBits)
 {
     int bits = 0;
     while (bits < 32 && (ncells - 1) >> bits) ++bits;
-    return (bits + kRadixBits - 1) / kRadixBits;
+    return (bits + digit_bits - 1) / digit_bits;
 }
 
 int sm_count();

@@ -783,6 +783,7 @@ int kernels_init()
         cudaFuncSetAttribute(k_resolve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResolveSmemBytes) !=
             cudaSuccess)
         return -1;
+    if (bin_kernels_init()) return -1;
     pair_grid<double>();
     pair_grid<float>();
     small_grid<double>();

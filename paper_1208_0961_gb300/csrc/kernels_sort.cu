@@ -14,84 +14,9 @@
 
 #include "engine.cuh"
 #include "fp.cuh"
+#include "stream.cuh"
 
 namespace cuba {
-
-// Cell key: i_a = clamp(floor(x_a / dx_a), 0, n_a - 1); key = ix + nx (iy + ny iz).
-template <typename T>
-__device__ __forceinline__ uint32_t cell_key(const SimDesc& S, const T pos[3])
-{
-    uint32_t id[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const T c = floor_t(div_rn(pos[a], sim_dx<T>(S, a)));
-        uint32_t ic;
-        if (c < T(0)) ic = 0;
-        else if (c >= (T)S.n[a]) ic = (uint32_t)(S.n[a] - 1);
-        else ic = (uint32_t)c;
-        id[a] = ic;
-    }
-    return id[0] + (uint32_t)S.n[0] * (id[1] + (uint32_t)S.n[1] * id[2]);
-}
-
-// Free streaming x <- x + (p/E) dt (Eq. 2, c = 1, E = |p|) and elastic
-// reflection: beyond a wall the position is mirrored and that momentum
-// component flips.  Returns the number of reflections.
-template <typename T>
-__device__ __forceinline__ int stream_one(const SimDesc& S, T pos[3], T mom[3])
-{
-    const T E = sqrt_rn(add_rn(add_rn(mul_rn(mom[0], mom[0]), mul_rn(mom[1], mom[1])), mul_rn(mom[2], mom[2])));
-    const T dt = sim_dt<T>(S);
-    int nref = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const T L = sim_L<T>(S, a);
-        const T v = (E > T(0)) ? div_rn(mom[a], E) : T(0);
-        T x = add_rn(pos[a], mul_rn(v, dt));
-        if (x < T(0)) {
-            x = -x;
-            mom[a] = -mom[a];
-            ++nref;
-        } else if (x > L) {
-            x = sub_rn(add_rn(L, L), x);
-            mom[a] = -mom[a];
-            ++nref;
-        }
-        pos[a] = x;
-    }
-    return nref;
-}
-
-// ---------------------------------------------------------------------------
-// A1-A3: stream, reflect, key (one thread per particle, SoA coalesced)
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_stream_key(const SimDesc* __restrict__ sims, int nsims, T* __restrict__ st,
-                                                    uint32_t pcap, uint32_t np, uint32_t* __restrict__ keys,
-                                                    unsigned long long* __restrict__ stats)
-{
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < np; g += stride) {
-        const int s = sim_of_particle(sims, nsims, g);
-        const SimDesc& S = sims[s];
-        T pos[3] = {st[g], st[pcap + g], st[2 * (size_t)pcap + g]};
-        T mom[3] = {st[3 * (size_t)pcap + g], st[4 * (size_t)pcap + g], st[5 * (size_t)pcap + g]};
-        const int nref = stream_one<T>(S, pos, mom);
-        st[g] = pos[0];
-        st[pcap + g] = pos[1];
-        st[2 * (size_t)pcap + g] = pos[2];
-        if (nref) {
-            st[3 * (size_t)pcap + g] = mom[0];
-            st[4 * (size_t)pcap + g] = mom[1];
-            st[5 * (size_t)pcap + g] = mom[2];
-        }
-        keys[g] = S.cell_off + cell_key<T>(S, pos);
-        // reflections: one atomic per warp and simulation
-        const unsigned peers = __match_any_sync(__activemask(), s);
-        const unsigned tot = __reduce_add_sync(peers, (unsigned)nref);
-        if ((threadIdx.x & 31) == (__ffs(peers) - 1) && tot) atomicAdd(&stats[S.stat_slot * kStatCount + kStatReflections], (unsigned long long)tot);
-    }
-}
 
 // Keys of a state without moving it (after sampling or loading a state).
 template <typename T>
@@ -326,6 +251,11 @@ static int exclusive_scan(V* data, size_t n, V zero, Op op, void* tmp, size_t tm
     k_scan_partials<V, Op><<<1, kScanThreads, 0, st>>>(partial, nb, zero, op);
     k_scan_apply<V, Op><<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, partial, zero, op);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int scan_u32(uint32_t* data, size_t n, void* tmp, size_t tmp_bytes, cudaStream_t st)
+{
+    return exclusive_scan<uint32_t, U32Add>(data, n, 0u, U32Add(), tmp, tmp_bytes, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -677,14 +607,17 @@ int launch_keys_only(const Arena& A, cudaStream_t st)
     return last_err();
 }
 
-int launch_stream_key(const Arena& A, cudaStream_t st)
+int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st)
 {
-    if (A.np == 0) return 0;
-    const unsigned g = grid_for(A.np, 256, 8);
-    if (A.precision == 1)
-        k_stream_key<double><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, A.np, A.key[0], A.stats);
-    else
-        k_stream_key<float><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap, A.np, A.key[0], A.stats);
+    if (n == 0) return 0;
+    k_fill_u32<<<grid_for(n, 256, 4), 256, 0, st>>>(p, n, v);
+    return last_err();
+}
+
+int launch_cell_bounds(const uint32_t* skey, uint32_t np, uint32_t* cell_start, uint32_t ncells, cudaStream_t st)
+{
+    if (np == 0) return launch_fill_u32(cell_start, ncells + 1, 0u, st);
+    k_cell_bounds<<<grid_for(np, 256, 8), 256, 0, st>>>(skey, np, cell_start, ncells);
     return last_err();
 }
 
