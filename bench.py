@@ -159,18 +159,24 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def radix_passes(ncells):
+def bin_passes(ncells):
+    """Radix passes of the in-step sort (11-bit digits)."""
     bits = 0
     while bits < 32 and (ncells - 1) >> bits:
         bits += 1
-    return (bits + 7) // 8
+    return max(1, (bits + 10) // 11)
 
 
-def launches_per_step(ncells):
-    # stream/key, per radix pass (histogram, 3 scan kernels, scatter), gather,
-    # cell prep + 3 scan kernels, pair tile, resolve, step counter
-    p = radix_passes(ncells)
-    return 1 + 5 * p + (1 if p else 2) + 4 + 1 + 1 + 1
+def launches_per_step(ncells, small_max):
+    """Kernels of one step: streaming histogram; per radix pass the digit
+    histogram (passes after the first), 3 scan kernels and the ranking
+    kernel, then (two passes or more) the gather; cell preparation + 3 scan
+    kernels; small-cell and tiled pair kernels; small-cell and per-cell
+    resolve kernels; the step counter."""
+    p = bin_passes(ncells)
+    sort = 1 + 4 * p + (p - 1) + (1 if p > 1 else 0)
+    small = 1 if small_max else 0
+    return sort + 4 + (1 + small) + (1 + small) + 1
 
 
 def peaks():
@@ -526,7 +532,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "small_max": cuba.cuba_get_small_max(sim.h), "autotune_ms": tune_ms},
             "clocks": clk,
-            "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2]) * args.steps,
+            "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2],
+                                              cuba.cuba_get_small_max(sim.h)) * args.steps,
             "roofline": roofline,
             "hbm_phases": hbm,
             "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in zip(phase_names, phase)},

@@ -282,7 +282,7 @@ void StepGraphs::drop()
 int StepGraphs::run(Arena& A, int n, cudaStream_t st)
 {
     if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells ||
-        small_max != A.small_max)
+        small_max != A.small_max || one_key != A.one_key || key0 != A.key_sched.k0[0] || key1 != A.key_sched.k1[0])
         drop();
     for (int k = 0; k < n; ++k) {
         const int which = A.cur;
@@ -309,11 +309,20 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
             nsims = A.nsims;
             ncells = A.ncells;
             small_max = A.small_max;
+            one_key = A.one_key;
+            key0 = A.key_sched.k0[0];
+            key1 = A.key_sched.k1[0];
         }
         CUDA_TRY(cudaGraphLaunch(g[which], st), "graph launch");
         A.cur ^= 1;
     }
     return CUBA_OK;
+}
+
+void set_key_param(Arena& A, const SimDesc* table, int n)
+{
+    A.one_key = n == 1;
+    A.key_sched = n == 1 ? philox_schedule(table[0].key0, table[0].key1) : PhiloxKey{};
 }
 
 int set_small_max(Arena& A, int32_t v)
@@ -417,6 +426,7 @@ namespace {
 int upload_desc(cuba_sim* s, cudaStream_t st)
 {
     CUDA_TRY(cudaMemcpyAsync(s->A.d_sims, &s->desc, sizeof(SimDesc), cudaMemcpyHostToDevice, st), "upload descriptor");
+    set_key_param(s->A, &s->desc, 1);
     return CUBA_OK;
 }
 

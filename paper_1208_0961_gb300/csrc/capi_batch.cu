@@ -80,6 +80,7 @@ int push_table(cuba_batch* b)
     A.nsims = (int)b->members.size();
     if (!t.empty())
         CUDA_TRY(cudaMemcpy(A.d_sims, t.data(), t.size() * sizeof(SimDesc), cudaMemcpyHostToDevice), "upload table");
+    set_key_param(A, t.data(), (int)t.size());
     return CUBA_OK;
 }
 

@@ -73,11 +73,19 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 // Pair tile: one warp per item of 32 rows of one cell.
 constexpr int kPairRows = 32;
 constexpr int kPairThreads = 256;
-constexpr int kPairBlocksPerIter = 2; // Philox blocks each lane draws per loop iteration
-#ifndef CUBA_PAIR_MIN_BLOCKS
-#define CUBA_PAIR_MIN_BLOCKS 0        // > 0: resident blocks per SM the register budget targets
-#endif
-constexpr int kQueueCap = 32 + 32 * kPairBlocksPerIter;  // queued Philox blocks per warp
+// Launch shape of the pair tile: a lane draws four Philox blocks per loop
+// iteration.  With one simulation the round keys are kernel parameters
+// (constant-bank operands) and the register budget is uncapped (about 126
+// registers, two blocks of 256 per SM); with several simulations each warp
+// holds its cell's round keys in registers, capped at 128 (two blocks per SM).
+template <bool kOneKey>
+struct PairShape {
+    static constexpr int nb = 4;                        // Philox blocks per lane and loop iteration
+    static constexpr int min_blocks = kOneKey ? 1 : 2;  // resident blocks per SM the register budget targets
+};
+constexpr int kSmallBlocksPerIter = 2; // the same for the warp-per-small-cell kernel (short rows)
+// Queued Philox blocks per warp for nb blocks per iteration (32 spare slots follow).
+__host__ __device__ constexpr int queue_cap(int nb) { return 32 + 32 * nb; }
 
 // Resolve: per-cell accepted lists up to this size are sorted in shared memory.
 constexpr int kResolveThreads = 256;
@@ -140,6 +148,10 @@ struct Arena {
     // cells with 2 <= n <= small_max take the warp-per-cell pair and resolve
     // kernels (0: every cell takes the row-block path); at most 1024
     uint32_t small_max = 32;
+    // one simulation: its Philox round keys, passed to the pair kernels as a
+    // parameter (set whenever the descriptor table is uploaded)
+    int one_key = 0;
+    PhiloxKey key_sched = {};
 };
 
 // ---- launchers (kernels_sort.cu) ----

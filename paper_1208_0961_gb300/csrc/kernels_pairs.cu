@@ -61,17 +61,6 @@ __device__ __forceinline__ T pair_p22(T C, const T* __restrict__ st, uint32_t pc
     return mul_rn(C, v);
 }
 
-// Nonzero iff some byte of the block is <= thr (thr < 128): a word has a byte
-// below m = thr + 1 iff (x - m * 0x01010101) & ~x & 0x80808080 != 0 (a
-// borrow can only add flags above a true one, so the "any" answer is exact).
-__device__ __forceinline__ uint32_t any_byte_le(uint4 r, uint32_t thr)
-{
-    if (thr >= 128u) return 1u;
-    const uint32_t t = 0x01010101u * (thr + 1u);
-    const uint32_t h = ((r.x - t) & ~r.x) | ((r.y - t) & ~r.y) | ((r.z - t) & ~r.z) | ((r.w - t) & ~r.w);
-    return h & 0x80808080u;
-}
-
 // Exact per-byte test of one word: bit b of the result (b = 0..3) is set iff
 // byte b <= thr.  With bit 7 of every byte forced on, subtracting m cannot
 // borrow across bytes; a byte is below m iff the difference drops bit 7 and
@@ -131,7 +120,7 @@ struct CellCtx {
 template <typename T, bool kMark>
 __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
                                                uint32_t thr16, T C, const T* __restrict__ st, uint32_t pcap,
-                                               const uint4* qw, const uint32_t* qi, const uint32_t* qg, uint32_t e0,
+                                               const uint4* qw, const uint2* qig, uint32_t e0,
                                                uint32_t e1, uint32_t* __restrict__ acc_count,
                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                                uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
@@ -140,7 +129,8 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t e = e0 + lane; e < e1; e += 32) {
         const uint4 r = qw[e];
-        const uint32_t i = qi[e], g = qg[e];
+        const uint2 ig = qig[e];
+        const uint32_t i = ig.x, g = ig.y;
         uint32_t m = block_le_mask(r, thr8) & valid_cols(g, i, cc.n);
         if (!m) continue;
         const uint4 mb = philox4x32_10(make_uint4(step, cc.lc, i, kTagMid | g), K);
@@ -173,16 +163,15 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
 // holding a byte <= thr8 are queued in the warp's shared-memory queue and
 // resolved 32 at a time.  kMark: the first accepted pair of the cell appends
 // it to the active-cell list (the small-cell path finds its cells by scanning).
-template <typename T, bool kMark>
+template <typename T, bool kMark, int NB>
 __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32_t step, uint32_t thr8, uint32_t thr16,
                                           T C, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap, uint4* qw,
-                                          uint32_t* qi, uint32_t* qg, uint32_t* __restrict__ acc_count,
+                                          uint2* qig, uint32_t* __restrict__ acc_count,
                                           unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                           uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
                                           unsigned long long* __restrict__ stats)
 {
-    constexpr int NB = kPairBlocksPerIter;
-    static_assert(kQueueCap >= 32 + 32 * NB, "a warp pushes up to 32 NB blocks onto at most 32 queued ones");
+    constexpr int kQueueCap = queue_cap(NB);  // a warp pushes up to 32 NB blocks onto at most 32 queued ones
     const uint32_t lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t i = rb * kPairRows + lane;
@@ -191,67 +180,65 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
     R.init(step, cc.lc, i, K);
     const uint32_t gfirst = (rb * kPairRows + 1) >> 4;
     const uint32_t glast = (cc.n - 1) >> 4;
+    // Some byte of a word x is below m = thr8 + 1 iff (x - m 0x01010101) & ~x
+    // has a bit 7 set (a borrow only adds flags above a true one, so the
+    // "any" answer is exact); thr8 >= 128 queues every block.
+    const bool all_hit = thr8 >= 128u;
+    const uint32_t t8 = 0x01010101u * (thr8 + 1u);
     uint32_t qn = 0;  // warp-uniform number of queued blocks
     for (uint32_t g = gfirst; g <= glast; g += NB) {
         uint4 r[NB];
         bool h[NB];
         unsigned bal[NB];
-        unsigned any = 0;
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            r[q] = (g + q <= glast) ? R.block(g + q, K)
-                                    : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-            h[q] = row_ok && any_byte_le(r[q], thr8);
+            // a group past the row's end is drawn but never queued
+            r[q] = R.block(g + q, K);
+            const uint32_t x = ((r[q].x - t8) & ~r[q].x) | ((r[q].y - t8) & ~r[q].y) | ((r[q].z - t8) & ~r[q].z) |
+                               ((r[q].w - t8) & ~r[q].w);
+            h[q] = row_ok & (g + q <= glast) & (all_hit | ((x & 0x80808080u) != 0u));
             bal[q] = __ballot_sync(kFull, h[q]);
-            any |= bal[q];
         }
-        if (any) {
-            // up to 32 NB blocks are pushed below: drain to at most 32 first
-            while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
-                __syncwarp();
-                resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qi, qg, qn - 32, qn, acc_count,
-                                         acc, acc_cap, counters, active, stats);
-                __syncwarp();
-                qn -= 32;
-            }
+        // up to 32 NB blocks are pushed below: drain to at most 32 first
+        while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
+            __syncwarp();
+            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qig, qn - 32, qn, acc_count, acc,
+                                     acc_cap, counters, active, stats);
+            __syncwarp();
+            qn -= 32;
+        }
+        // branch-free push: lanes without a hit write their own spare slot
 #pragma unroll
-            for (int q = 0; q < NB; ++q) {
-                if (h[q]) {
-                    const uint32_t slot = qn + (uint32_t)__popc(bal[q] & lt);
-                    qw[slot] = r[q];
-                    qi[slot] = i;
-                    qg[slot] = g + q;
-                }
-                qn += (uint32_t)__popc(bal[q]);
-            }
+        for (int q = 0; q < NB; ++q) {
+            const uint32_t slot = h[q] ? qn + (uint32_t)__popc(bal[q] & lt) : (uint32_t)kQueueCap + lane;
+            qw[slot] = r[q];
+            qig[slot] = make_uint2(i, g + q);
+            qn += (uint32_t)__popc(bal[q]);
         }
     }
     if (qn) {
         __syncwarp();
-        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qi, qg, 0, qn, acc_count, acc, acc_cap,
+        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qig, 0, qn, acc_count, acc, acc_cap,
                                  counters, active, stats);
         __syncwarp();
     }
 }
 
-#if CUBA_PAIR_MIN_BLOCKS > 0
-#define CUBA_PAIR_BOUNDS __launch_bounds__(kPairThreads, CUBA_PAIR_MIN_BLOCKS)
-#else
-#define CUBA_PAIR_BOUNDS __launch_bounds__(kPairThreads)
-#endif
-
-template <typename T>
-__global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, int nsims, const T* __restrict__ st,
-                                            uint32_t pcap, const uint32_t* __restrict__ cell_start,
-                                            const uint2* __restrict__ work, uint32_t ncells,
-                                            uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
-                                            uint64_t acc_cap, uint32_t* __restrict__ counters,
-                                            uint32_t* __restrict__ active, unsigned long long* __restrict__ stats)
+// kOneKey: every cell belongs to one simulation whose round keys come as the
+// kernel parameter Kp (constant-bank operands, no registers); otherwise each
+// cell's key schedule is derived from its descriptor.
+template <typename T, bool kOneKey>
+__global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey>::min_blocks)
+    k_pair_tile(const SimDesc* __restrict__ sims, int nsims, const T* __restrict__ st, uint32_t pcap,
+                const uint32_t* __restrict__ cell_start, const uint2* __restrict__ work, uint32_t ncells,
+                uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                uint32_t* __restrict__ counters, uint32_t* __restrict__ active, unsigned long long* __restrict__ stats,
+                const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    __shared__ uint4 q_w[kWarps][kQueueCap];
-    __shared__ uint32_t q_i[kWarps][kQueueCap];
-    __shared__ uint32_t q_g[kWarps][kQueueCap];
+    constexpr int NB = PairShape<kOneKey>::nb;
+    __shared__ uint4 q_w[kWarps][queue_cap(NB) + 32];
+    __shared__ uint2 q_ig[kWarps][queue_cap(NB) + 32];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t total = work[ncells].x;
@@ -295,15 +282,16 @@ __global__ void CUBA_PAIR_BOUNDS k_pair_tile(const SimDesc* __restrict__ sims, i
         cc.list0 = w0.y;
         cc.room = w1.y - w0.y;
         const uint32_t rb = item - w0.x;
-        const PhiloxKey K = philox_schedule(S.key0, S.key1);
-        pair_rows<T, true>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_i[w], q_g[w],
+        const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
+        const PhiloxKey& K = kOneKey ? Kp : Kl;
+        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_ig[w],
                            acc_count, acc, acc_cap, counters, active, stats);
     }
 }
 
 // Small cells (2 <= n <= small_max): one warp per cell, all its rows, found
 // by a grid-stride scan over the cells (no work queue, no per-cell atomic).
-template <typename T>
+template <typename T, bool kOneKey>
 __global__ void __launch_bounds__(kPairThreads) k_pair_small(const SimDesc* __restrict__ sims, int nsims,
                                                              const T* __restrict__ st, uint32_t pcap,
                                                              const uint32_t* __restrict__ cell_start,
@@ -312,12 +300,13 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_small(const SimDesc* __re
                                                              unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                                              uint32_t* __restrict__ counters,
                                                              uint32_t* __restrict__ active,
-                                                             unsigned long long* __restrict__ stats)
+                                                             unsigned long long* __restrict__ stats,
+                                                             const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    __shared__ uint4 q_w[kWarps][kQueueCap];
-    __shared__ uint32_t q_i[kWarps][kQueueCap];
-    __shared__ uint32_t q_g[kWarps][kQueueCap];
+    constexpr int NB = kSmallBlocksPerIter;
+    __shared__ uint4 q_w[kWarps][queue_cap(NB) + 32];
+    __shared__ uint2 q_ig[kWarps][queue_cap(NB) + 32];
     const int w = threadIdx.x >> 5;
     if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
     const uint32_t nwarps = gridDim.x * kWarps;
@@ -338,10 +327,11 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_small(const SimDesc* __re
         const uint2 w0 = work[c], w1 = work[c + 1];
         cc.list0 = w0.y;
         cc.room = w1.y - w0.y;
-        const PhiloxKey K = philox_schedule(S.key0, S.key1);
+        const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
+        const PhiloxKey& K = kOneKey ? Kp : Kl;
         const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
         for (uint32_t rb = 0; rb < nrb; ++rb)
-            pair_rows<T, false>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_i[w], q_g[w],
+            pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_ig[w],
                                 acc_count, acc, acc_cap, counters, active, stats);
     }
 }
@@ -721,51 +711,51 @@ int launch_kinematics_check(const SimDesc& S, const float* pin, int64_t npairs, 
 // ---------------------------------------------------------------------------
 static int last_err() { return cudaPeekAtLastError() == cudaSuccess ? 0 : -1; }
 
-template <typename T>
+template <typename T, bool kOneKey>
 static unsigned pair_grid()
 {
     static unsigned g = 0;
     if (!g) {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_tile<T>, kPairThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_tile<T, kOneKey>, kPairThreads, 0);
         if (per < 1) per = 1;
         g = (unsigned)(per * sm_count());
     }
     return g;
 }
 
-template <typename T>
+template <typename T, bool kOneKey>
 static unsigned small_grid()
 {
     static unsigned g = 0;
     if (!g) {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_small<T>, kPairThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_small<T, kOneKey>, kPairThreads, 0);
         if (per < 1) per = 1;
         g = (unsigned)(per * sm_count());
     }
     return g;
+}
+
+template <typename T, bool kOneKey>
+static void launch_pairs(const Arena& A, cudaStream_t st)
+{
+    if (A.small_max)
+        k_pair_small<T, kOneKey><<<small_grid<T, kOneKey>(), kPairThreads, 0, st>>>(
+            A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.small_max,
+            A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
+    k_pair_tile<T, kOneKey><<<pair_grid<T, kOneKey>(), kPairThreads, 0, st>>>(
+        A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count, A.acc,
+        A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
 }
 
 int launch_pair_tile(const Arena& A, cudaStream_t st)
 {
     if (A.ncells == 0) return 0;
     if (A.precision == 1) {
-        if (A.small_max)
-            k_pair_small<double><<<small_grid<double>(), kPairThreads, 0, st>>>(
-                A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells,
-                A.small_max, A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats);
-        k_pair_tile<double><<<pair_grid<double>(), kPairThreads, 0, st>>>(
-            A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count,
-            A.acc, A.acc_capacity, A.counters, A.active, A.stats);
+        if (A.one_key) launch_pairs<double, true>(A, st); else launch_pairs<double, false>(A, st);
     } else {
-        if (A.small_max)
-            k_pair_small<float><<<small_grid<float>(), kPairThreads, 0, st>>>(
-                A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells,
-                A.small_max, A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats);
-        k_pair_tile<float><<<pair_grid<float>(), kPairThreads, 0, st>>>(
-            A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count,
-            A.acc, A.acc_capacity, A.counters, A.active, A.stats);
+        if (A.one_key) launch_pairs<float, true>(A, st); else launch_pairs<float, false>(A, st);
     }
     return last_err();
 }
@@ -784,10 +774,14 @@ int kernels_init()
             cudaSuccess)
         return -1;
     if (bin_kernels_init()) return -1;
-    pair_grid<double>();
-    pair_grid<float>();
-    small_grid<double>();
-    small_grid<float>();
+    pair_grid<double, false>();
+    pair_grid<float, false>();
+    pair_grid<double, true>();
+    pair_grid<float, true>();
+    small_grid<double, false>();
+    small_grid<float, false>();
+    small_grid<double, true>();
+    small_grid<float, true>();
     sm_count();
     done = true;
     return 0;
