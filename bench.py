@@ -129,16 +129,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """Join the process group of a torchrun launch (one rank per GPU, NCCL);
+    backend "gloo" joins on the CPU (multi-process tests of the replica
+    logic)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    backend = backend or "nccl"
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif backend == "nccl":
         torch.cuda.set_device(0)
     return world, rank, local
 
@@ -150,13 +155,38 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest x over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    """Sum of x over the ranks."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_seed(seed, rank):
+    """Each rank advances an independent replica with its own seed."""
+    return seed + rank
+
+
+def replica_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank holds the same workload)."""
+    return units_per_rank * world / seconds_max
 
 
 def bin_passes(ncells):
@@ -307,13 +337,19 @@ def ensemble(n_sims, seed=0):
     return out
 
 
+def shard_members(members, rank, world):
+    """Members of an ensemble that rank advances (round robin: independent
+    simulations need no exchange, so ranks share nothing on the data path)."""
+    return members[rank::world]
+
+
 def run_batch_mode(args):
     import torch
     from paper_1208_0961_gb300 import cuba
-    torch.cuda.set_device(0)
+    world, rank, local = dist_setup(args)
     cuba.load()
     prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
-    members = ensemble(args.batch_sims, args.seed)
+    members = shard_members(ensemble(args.batch_sims, args.seed), rank, world)
     N = sum(m["n"] for m in members)
     C = sum(m["n_cells"][0] for m in members)
     cfg = cuba.make_batch_config(prec, max_sims=len(members), max_particles=N, max_cells=C)
@@ -330,11 +366,14 @@ def run_batch_mode(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
     e0.record(stream)
     b.step(args.steps, stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
     ids = list(b.members)
     pair_tests = sum(b.stats(i)["pair_tests"] for i in ids) / (args.warmup + args.steps)
     b.close()
@@ -353,18 +392,35 @@ def run_batch_mode(args):
         torch.cuda.synchronize()
         alone_ms += a0.elapsed_time(a1)
         sim.close()
-    line = {"mode": "batch", "metric": "particle-updates/s (stream+bin+collide), batched ensemble",
-            "value": N * args.steps / (ms / 1000.0), "unit": "particle-updates/s", "steps": args.steps,
-            "ms_per_step": ms / args.steps, "members": len(members), "particles": N, "cells": C,
-            "pair_tests_per_step": pair_tests,
-            "alone": {"value": N * args.steps / (alone_ms / 1000.0), "ms_per_step": alone_ms / args.steps},
-            "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
-    line["speedup_vs_alone"] = line["value"] / line["alone"]["value"]
-    print(json.dumps(line), flush=True)
+    alone_ms = max_over_ranks(alone_ms, world)
+    # the updates of all ranks over the slowest rank's time
+    tot = sum_over_ranks(N, world)
+    if rank == 0:
+        line = {"mode": "batch", "metric": "particle-updates/s (stream+bin+collide), batched ensemble",
+                "value": tot * args.steps / (ms / 1000.0), "unit": "particle-updates/s", "steps": args.steps,
+                "n_gpus": world, "scaling": "weak", "ms_per_step": ms / args.steps, "members": args.batch_sims,
+                "particles": int(tot), "cells": int(sum_over_ranks(C, world)) if world > 1 else C,
+                "pair_tests_per_step": pair_tests,
+                "alone": {"value": tot * args.steps / (alone_ms / 1000.0), "ms_per_step": alone_ms / args.steps},
+                "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
+        line["speedup_vs_alone"] = line["value"] / line["alone"]["value"]
+        print(json.dumps(line), flush=True)
+    elif world > 1:
+        sum_over_ranks(C, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
+
+
+
 def run_serve_mode(args):
+    """One server on one GPU; under torchrun only rank 0 serves (the request
+    stream is one queue) and the other ranks exit at once."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
     import torch
     from paper_1208_0961_gb300 import cuba
     from paper_1208_0961_gb300 import serve as S
@@ -425,7 +481,7 @@ def main():
     cfg = workload(args)
     prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
     p = cuba.make_params(L=cfg["L"], n_cells=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
-                         n_test=cfg["n_test"], precision=prec, seed=args.seed + rank)
+                         n_test=cfg["n_test"], precision=prec, seed=replica_seed(args.seed, rank))
     sim = cuba.Sim(p, args.n)
     stream = torch.cuda.Stream()
     if args.workload == "hotspot3d":
@@ -457,7 +513,7 @@ def main():
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     ms_max = max_over_ranks(ms, world)
-    value = args.n * args.steps * world / (ms_max / 1000.0)
+    value = replica_rate(args.n * args.steps, world, ms_max / 1000.0)
 
     # per-phase device times, kernel by kernel with events on the same stream
     phase = cuba.cuba_step_profiled(sim.h, args.profile_steps, stream)
@@ -510,7 +566,7 @@ def main():
             cuba.cuba_observables(sim.h, T00.data_ptr(), T0x.data_ptr(), cnt.data_ptr(), stream)
         t1 = time.perf_counter()
         e2e_s = max_over_ranks(t1 - t0, world)
-        e2e = {"value": args.n * args.e2e_steps * world / e2e_s, "unit": "particle-updates/s",
+        e2e = {"value": replica_rate(args.n * args.e2e_steps, world, e2e_s), "unit": "particle-updates/s",
                "h2d_bytes_per_step": host.numel() * host.element_size(),
                "d2h_bytes_per_step": nc * (8 + 8 + 4), "steps": args.e2e_steps}
 
