@@ -50,6 +50,7 @@ typedef struct {
     double n_test;    /* test particles per physical particle */
     int32_t fp32;     /* 1: single-precision mirror of stream, key and P22 */
     uint32_t key[2];  /* Philox key (seed low word, seed high word) */
+    int32_t skip;     /* 0: every pair tested (Eq. 3); 1: skip-ahead candidates + thinning */
 } orc_params;
 
 typedef struct {
@@ -67,6 +68,7 @@ typedef struct {
     int64_t exe_cap, n_exe;
     int64_t n_reflections;
     int64_t n_pairs_tested;
+    int64_t n_candidates;  /* skip-ahead: candidate pairs drawn (P22 evaluated) */
 } orc_trace;
 
 /* ------------------------------------------------------------------------ */
@@ -106,6 +108,7 @@ static void philox(uint32_t a, uint32_t b, uint32_t c, uint32_t d, const uint32_
 #define TAG_MID 0x20000000u    /* acceptance: bits 23..16 of u_ij           */
 #define TAG_FINE 0x40000000u   /* acceptance: low 16 bits of u_ij           */
 #define TAG_ANGLE 0x80000000u  /* kinematics: CM-frame direction           */
+#define TAG_SKIP 0xC0000000u   /* skip-ahead: k-th candidate draw of a row   */
 #define STEP_INIT 0xFFFFFFFFu  /* first counter word reserved for sampling */
 
 /* ------------------------------------------------------------------------ */
@@ -136,6 +139,7 @@ static int check_params(const orc_params *p)
         if (!(p->dt < cell_len(p, a))) return ORC_ERR_INVALID;
     }
     if (!(p->dt > 0.0) || !(p->sigma >= 0.0) || !(p->n_test > 0.0)) return ORC_ERR_INVALID;
+    if (p->skip != 0 && p->skip != 1) return ORC_ERR_INVALID;
     return ORC_OK;
 }
 
@@ -512,6 +516,122 @@ static int accept_pair(const orc_params *p, double C, uint32_t step, uint32_t ce
 }
 
 /* ------------------------------------------------------------------------ */
+/* A5, skip-ahead mode: Bernoulli candidates with geometric gaps, thinning   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper tests every pair with its own uniform (Eq. 3).  The skip-ahead
+ * mode draws the same accepted-pair distribution with work proportional to
+ * the number of candidates: along row i (columns j = i+1 .. n-1 in order) a
+ * pair is a candidate with probability P_max >= max P22 independently of the
+ * others, so the gaps between candidates are geometric; a candidate is then
+ * kept with probability P22 / P_max (thinning).  Each pair ends up accepted
+ * with probability P22, independently, as in the all-pairs test; only the
+ * realisation differs.
+ *
+ * Reading (exact, integer-only where it decides an index):
+ *  - P_max: P_fix = floor(2.0001 C 2^64) (at least 1) as a 0.64 fixed-point
+ *    fraction; q = 2^64 - P_fix is 1 - P_max; Q[b] = q^(2^b) by repeated
+ *    truncated fixed-point squaring, b = 0 .. 32;
+ *  - the k-th draw of row i is the Philox block (step, cell, i, TAG_SKIP | k):
+ *    U = word0 2^32 + word1 (64-bit uniform), w = word2 (thinning);
+ *  - gap: with pos the last candidate (i at the start) and M = n - 1 - pos
+ *    columns left, G = the largest integer < 2^(bt+1) whose fixed-point power
+ *    q^G, built greedily from bit bt = ceil(log2 M) down to bit 0, is still
+ *    >= U: P(G >= k) = q^k up to rounding (inverse-CDF of the geometric
+ *    distribution).  G >= M ends the row; otherwise j = pos + 1 + G;
+ *  - thinning: accept iff (unit(w) * P_max) < P22 in the state's precision,
+ *    with P_max = P_fix 2^-64 rounded to that precision and unit(w) = w 2^-32.
+ */
+static uint64_t mulhi64(uint64_t a, uint64_t b)
+{
+    return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+}
+
+int orc_skip_table(double C, uint64_t *p_fix, uint64_t Q[33])
+{
+    double x = 2.0001 * C;
+    if (!(x > 0.0) || !(x < 1.0)) return ORC_ERR_INVALID;
+    uint64_t P = (uint64_t)ldexp(x, 64);
+    if (P == 0) P = 1;
+    *p_fix = P;
+    Q[0] = (uint64_t)0 - P;
+    for (int b = 1; b <= 32; ++b) Q[b] = mulhi64(Q[b - 1], Q[b - 1]);
+    return ORC_OK;
+}
+
+uint64_t orc_skip_gap(const uint64_t Q[33], uint64_t U, uint64_t M)
+{
+    int bt = 0;
+    while (bt < 32 && ((uint64_t)1 << bt) < M) ++bt;
+    uint64_t G = 0, Qc = ~(uint64_t)0;
+    for (int b = bt; b >= 0; --b) {
+        uint64_t t = mulhi64(Qc, Q[b]);
+        if (t >= U) {
+            Qc = t;
+            G += (uint64_t)1 << b;
+        }
+    }
+    return G;
+}
+
+/* Thinning of candidate (i, j) with word w: accept iff unit(w) P_max < P22. */
+static int thin_accept(const orc_params *p, double C, uint64_t P_fix, uint32_t w, const double *mi,
+                       const double *mj)
+{
+    double Pm = (double)P_fix * 0x1p-64;
+    if (p->fp32) {
+        float fi[3] = {(float)mi[0], (float)mi[1], (float)mi[2]};
+        float fj[3] = {(float)mj[0], (float)mj[1], (float)mj[2]};
+        float ui[3], uj[3];
+        unit_f(fi, ui);
+        unit_f(fj, uj);
+        float P22 = (float)C * vrel_f(ui, uj);
+        float u = ((float)w * 0x1p-32f) * (float)Pm;
+        return u < P22;
+    } else {
+        double ui[3], uj[3];
+        unit_d(mi, ui);
+        unit_d(mj, uj);
+        double P22 = C * vrel_d(ui, uj);
+        double u = ((double)w * 0x1p-32) * Pm;
+        return u < P22;
+    }
+}
+
+/*
+ * Candidates of row i of a cell of nc particles (momenta px, py, pz in sorted
+ * order), in increasing j; accepted columns go to out_j (at most cap written).
+ * Returns the number accepted; *n_cand receives the number of candidates.
+ */
+static int64_t skip_row(const orc_params *p, double C, uint64_t P_fix, const uint64_t Q[33], uint32_t step,
+                        uint32_t cell, int64_t nc, int64_t i, const double *px, const double *py,
+                        const double *pz, uint32_t *out_j, int64_t cap, int64_t *n_cand)
+{
+    int64_t pos = i, count = 0, cand = 0;
+    double mi[3] = {px[i], py[i], pz[i]};
+    for (uint32_t k = 0;; ++k) {
+        uint64_t M = (uint64_t)(nc - 1 - pos);
+        if (M == 0) break;
+        uint32_t w[4];
+        philox(step, cell, (uint32_t)i, TAG_SKIP | k, p->key, w);
+        uint64_t U = ((uint64_t)w[0] << 32) | w[1];
+        uint64_t G = orc_skip_gap(Q, U, M);
+        if (G >= M) break;
+        int64_t j = pos + 1 + (int64_t)G;
+        double mj[3] = {px[j], py[j], pz[j]};
+        ++cand;
+        if (thin_accept(p, C, P_fix, w[2], mi, mj)) {
+            if (out_j && count < cap) out_j[count] = (uint32_t)j;
+            ++count;
+        }
+        pos = j;
+    }
+    if (n_cand) *n_cand = cand;
+    return count;
+}
+
+/* ------------------------------------------------------------------------ */
 /* A7: kinematics — boost to the CM frame, isotropic direction, boost back   */
 /* ------------------------------------------------------------------------ */
 
@@ -566,6 +686,7 @@ typedef struct {
     int64_t n_acc, cap;
     uint8_t *exe;  /* executed flag per accepted pair */
     int64_t n_exe;
+    int64_t n_cand; /* skip-ahead candidates */
 } cell_result;
 
 static int push_pair(cell_result *cr, uint32_t i, uint32_t j)
@@ -587,7 +708,8 @@ static int push_pair(cell_result *cr, uint32_t i, uint32_t j)
  * One cell of nc particles whose momenta sit at m[0..nc), m[nc..2nc),
  * m[2nc..3nc) (components px, py, pz), in sorted order:
  *  (1) test every pair i < j in lexicographic order and keep the accepted
- *      ones (A5);
+ *      ones (A5) — or, in the skip-ahead mode, draw each row's candidates and
+ *      thin them, which yields the accepted pairs in the same order;
  *  (2) walk the accepted pairs in that order and execute a pair iff neither
  *      particle has collided yet in this step (A6, greedy reading);
  *  (3) apply the kinematics to each executed pair (A7).
@@ -597,13 +719,30 @@ static int do_cell(const orc_params *p, double C, uint32_t step, uint32_t cell, 
 {
     memset(cr, 0, sizeof(*cr));
     if (nc < 2 || !(C > 0.0)) return ORC_OK;
-    for (int64_t i = 0; i < nc; ++i) {
-        double mi[3] = {px[i], py[i], pz[i]};
-        for (int64_t j = i + 1; j < nc; ++j) {
-            double mj[3] = {px[j], py[j], pz[j]};
-            if (accept_pair(p, C, step, cell, (uint32_t)i, (uint32_t)j, mi, mj)) {
-                int rc = push_pair(cr, (uint32_t)i, (uint32_t)j);
-                if (rc != ORC_OK) return rc;
+    if (p->skip) {
+        uint64_t P_fix, Q[33];
+        if (orc_skip_table(C, &P_fix, Q) != ORC_OK) return ORC_ERR_INVALID;
+        uint32_t *row = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)nc);
+        if (!row) return ORC_ERR_OOM;
+        for (int64_t i = 0; i + 1 < nc; ++i) {
+            int64_t cand = 0;
+            int64_t m = skip_row(p, C, P_fix, Q, step, cell, nc, i, px, py, pz, row, nc, &cand);
+            cr->n_cand += cand;
+            for (int64_t e = 0; e < m; ++e) {
+                int rc = push_pair(cr, (uint32_t)i, row[e]);
+                if (rc != ORC_OK) { free(row); return rc; }
+            }
+        }
+        free(row);
+    } else {
+        for (int64_t i = 0; i < nc; ++i) {
+            double mi[3] = {px[i], py[i], pz[i]};
+            for (int64_t j = i + 1; j < nc; ++j) {
+                double mj[3] = {px[j], py[j], pz[j]};
+                if (accept_pair(p, C, step, cell, (uint32_t)i, (uint32_t)j, mi, mj)) {
+                    int rc = push_pair(cr, (uint32_t)i, (uint32_t)j);
+                    if (rc != ORC_OK) return rc;
+                }
             }
         }
     }
@@ -645,6 +784,23 @@ int64_t orc_cell_accept(const orc_params *p, uint32_t step, uint32_t cell, int64
     double C = orc_p22_scale(p);
     int64_t count = 0;
     if (!(C > 0.0)) return 0;
+    if (p->skip) {
+        uint64_t P_fix, Q[33];
+        if (orc_skip_table(C, &P_fix, Q) != ORC_OK) return ORC_ERR_INVALID;
+        uint32_t *row = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nc > 0 ? nc : 1));
+        if (!row) return ORC_ERR_OOM;
+        for (int64_t i = 0; i + 1 < nc; ++i) {
+            int64_t m = skip_row(p, C, P_fix, Q, step, cell, nc, i, px, py, pz, row, nc, NULL);
+            for (int64_t e = 0; e < m; ++e, ++count) {
+                if (count < cap && out_ij) {
+                    out_ij[2 * count] = (uint32_t)i;
+                    out_ij[2 * count + 1] = row[e];
+                }
+            }
+        }
+        free(row);
+        return count;
+    }
     for (int64_t i = 0; i < nc; ++i) {
         double mi[3] = {px[i], py[i], pz[i]};
         for (int64_t j = i + 1; j < nc; ++j) {
@@ -672,6 +828,22 @@ int64_t orc_row_accept(const orc_params *p, uint32_t step, uint32_t cell, int64_
     if (!(C > 0.0) || i < 0 || i >= nc) return 0;
     if (j0 < i + 1) j0 = i + 1;
     if (j1 > nc) j1 = nc;
+    if (p->skip) {
+        /* the row's candidate process starts at column i + 1 whatever the
+           window: draw the whole row, keep the columns in [j0, j1) */
+        uint64_t P_fix, Q[33];
+        if (orc_skip_table(C, &P_fix, Q) != ORC_OK) return ORC_ERR_INVALID;
+        uint32_t *row = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)nc);
+        if (!row) return ORC_ERR_OOM;
+        int64_t m = skip_row(p, C, P_fix, Q, step, cell, nc, i, px, py, pz, row, nc, NULL);
+        for (int64_t e = 0; e < m; ++e) {
+            if (row[e] < (uint32_t)j0 || row[e] >= (uint32_t)j1) continue;
+            if (count < cap && out_j) out_j[count] = row[e];
+            ++count;
+        }
+        free(row);
+        return count;
+    }
     double mi[3] = {px[i], py[i], pz[i]};
     for (int64_t j = j0; j < j1; ++j) {
         double mj[3] = {px[j], py[j], pz[j]};
@@ -750,12 +922,14 @@ int orc_step(const orc_params *p, uint32_t step, int64_t n, double *st, orc_trac
         tr->n_exe = 0;
         tr->n_reflections = nref;
         tr->n_pairs_tested = 0;
+        tr->n_candidates = 0;
     }
     for (int64_t c = 0; c < ncell; ++c) {
         cell_result *cr = &res[c];
         if (tr) {
             int64_t nc = cs[c + 1] - cs[c];
             tr->n_pairs_tested += (C > 0.0) ? nc * (nc - 1) / 2 : 0;
+            tr->n_candidates += cr->n_cand;
             for (int64_t e = 0; e < cr->n_acc; ++e) {
                 if (tr->acc && tr->n_acc < tr->acc_cap) {
                     tr->acc[3 * tr->n_acc] = (uint32_t)c;

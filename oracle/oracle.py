@@ -27,6 +27,7 @@ class Params(C.Structure):
         ("n_test", C.c_double),
         ("fp32", C.c_int32),
         ("key", C.c_uint32 * 2),
+        ("skip", C.c_int32),
     ]
 
 
@@ -47,6 +48,7 @@ class Trace(C.Structure):
         ("n_exe", C.c_int64),
         ("n_reflections", C.c_int64),
         ("n_pairs_tested", C.c_int64),
+        ("n_candidates", C.c_int64),
     ]
 
 
@@ -94,6 +96,11 @@ def lib():
         L.orc_observables.restype = C.c_int
         L.orc_totals.argtypes = [C.c_int64, dp, dp]
         L.orc_totals.restype = None
+        u64p = C.POINTER(C.c_uint64)
+        L.orc_skip_table.argtypes = [C.c_double, u64p, u64p]
+        L.orc_skip_table.restype = C.c_int
+        L.orc_skip_gap.argtypes = [u64p, C.c_uint64, C.c_uint64]
+        L.orc_skip_gap.restype = C.c_uint64
         L.orc_threads.argtypes = []
         L.orc_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
@@ -107,7 +114,7 @@ def _ptr(a, ct):
 
 
 def make_params(L=(10.0, 1.0, 1.0), n=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_test=1.0,
-                fp32=False, seed=0):
+                fp32=False, seed=0, skip=False):
     p = Params()
     for a in range(3):
         p.L[a] = float(L[a])
@@ -118,6 +125,7 @@ def make_params(L=(10.0, 1.0, 1.0), n=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_tes
     p.fp32 = 1 if fp32 else 0
     p.key[0] = int(seed) & 0xFFFFFFFF
     p.key[1] = (int(seed) >> 32) & 0xFFFFFFFF
+    p.skip = 1 if skip else 0
     return p
 
 
@@ -222,6 +230,23 @@ def kinematics(key, step, cell, i, j, pi, pj):
     return bool(ok), a, b
 
 
+def skip_table(C_scale):
+    """(P_fix, Q[0..32]) of the skip-ahead mode for the P22 scale C."""
+    Q = np.zeros(33, dtype=np.uint64)
+    pf = C.c_uint64()
+    rc = lib().orc_skip_table(float(C_scale), C.byref(pf), _ptr(Q, C.c_uint64))
+    if rc != 0:
+        raise ValueError("orc_skip_table failed: %d" % rc)
+    return int(pf.value), Q
+
+
+def skip_gap(Q, U, M):
+    """Geometric gap of the skip-ahead mode for the 64-bit uniform U with M
+    columns left in the row (a result >= M ends the row)."""
+    Q = np.ascontiguousarray(Q, dtype=np.uint64)
+    return int(lib().orc_skip_gap(_ptr(Q, C.c_uint64), int(U), int(M)))
+
+
 def cell_accept(p, step, cell, mom):
     """Accepted (i, j) pairs of one cell; mom has shape (3, nc) in sorted order."""
     mom = np.ascontiguousarray(mom, dtype=np.float64)
@@ -305,6 +330,7 @@ def step(p, step_index, st, trace=True):
     res.n_exe = tr.n_exe
     res.n_reflections = tr.n_reflections
     res.n_pairs_tested = tr.n_pairs_tested
+    res.n_candidates = tr.n_candidates
     if trace:
         res.accepted = res._acc[:3 * tr.n_acc].reshape(-1, 3).copy()
         res.executed = res._exe[:3 * tr.n_exe].reshape(-1, 3).copy()
