@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--dt", type=float, default=0.0025)
     ap.add_argument("--sigma-mb", type=float, default=10.0)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--acceptance", default="all-pairs", choices=["all-pairs", "skip"],
+                    help="pair test of the paper (every pair draws its uniform) or skip-ahead sampling")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -197,16 +199,18 @@ def bin_passes(ncells):
     return max(1, (bits + 10) // 11)
 
 
-def launches_per_step(ncells, small_max):
+def launches_per_step(ncells, small_max, skip=False):
     """Kernels of one step: streaming histogram; per radix pass the digit
     histogram (passes after the first), 3 scan kernels and the ranking
     kernel, then (two passes or more) the gather; cell preparation + 3 scan
-    kernels; small-cell and tiled pair kernels; small-cell and per-cell
-    resolve kernels; the step counter."""
+    kernels; small-cell and tiled pair kernels (skip-ahead: 3 scan kernels of
+    its row blocks and its pair kernel); small-cell and per-cell resolve
+    kernels; the step counter."""
     p = bin_passes(ncells)
     sort = 1 + 4 * p + (p - 1) + (1 if p > 1 else 0)
     small = 1 if small_max else 0
-    return sort + 4 + (1 + small) + (1 + small) + 1
+    pairs = 3 + 1 if skip else 1 + small
+    return sort + 4 + pairs + (1 + small) + 1
 
 
 def peaks():
@@ -481,7 +485,8 @@ def main():
     cfg = workload(args)
     prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
     p = cuba.make_params(L=cfg["L"], n_cells=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
-                         n_test=cfg["n_test"], precision=prec, seed=replica_seed(args.seed, rank))
+                         n_test=cfg["n_test"], precision=prec, seed=replica_seed(args.seed, rank),
+                         acceptance=cuba.CUBA_ACCEPT_SKIP if args.acceptance == "skip" else cuba.CUBA_ACCEPT_ALL_PAIRS)
     sim = cuba.Sim(p, args.n)
     stream = torch.cuda.Stream()
     if args.workload == "hotspot3d":
@@ -546,6 +551,14 @@ def main():
     hbm = {"phases": "stream_key+sort_bin", "achieved_gbs": args.n * bpu / (sb_ms / 1000.0) / 1e9,
            "peak_gbs": pk.get("hbm_gbs"), "bytes_per_update": bpu}
     hbm["frac"] = hbm["achieved_gbs"] / hbm["peak_gbs"] if hbm["peak_gbs"] else None
+    if args.acceptance == "skip":
+        # skip-ahead: the pair phase draws one Philox block per row plus one
+        # per candidate, far below the stream/bin phases; those (HBM) are the
+        # dominant work and the roofline reported
+        roofline = {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm["peak_gbs"], "unit": "GB/s",
+                    "frac": hbm["frac"], "traffic": None,
+                    "kernel": "k_stream_hist + histogram scan + k_bin_final (stream/bin phases)",
+                    "bytes_per_update": bpu}
 
     # end to end through the C ABI with host buffers: H2D state, one step,
     # D2H observables, every step
@@ -584,16 +597,18 @@ def main():
             "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "n_particles": args.n, "n_cells": args.cells, "dt": args.dt,
                        "sigma_mb": args.sigma_mb, "precision": args.precision, "n_test": cfg["n_test"],
+                       "acceptance": args.acceptance,
                        "l2": "state %.0f MB > L2, no flush" % (args.n * 24 / 1e6 * (2 if prec else 1)),
                        "parallelism": "replicas" if world > 1 else "single",
                        "small_max": cuba.cuba_get_small_max(sim.h), "autotune_ms": tune_ms},
             "clocks": clk,
             "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2],
-                                              cuba.cuba_get_small_max(sim.h)) * args.steps,
+                                              cuba.cuba_get_small_max(sim.h), args.acceptance == "skip") * args.steps,
             "roofline": roofline,
             "hbm_phases": hbm,
             "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in zip(phase_names, phase)},
             "pair_tests_per_step": pairs_per_step,
+            "candidates_per_step": stats["candidates"] / max(1, stats["steps"]),
             "accepted_per_step": stats["accepted"] / max(1, stats["steps"]),
             "executed_per_step": stats["executed"] / max(1, stats["steps"]),
             "e2e": e2e,

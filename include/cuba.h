@@ -74,7 +74,21 @@ typedef struct cuba_params {
     uint64_t seed;        /* Philox key of this simulation */
     double gamma_fp64;    /* CUBA_FP32 only: CM boosts with Lorentz factor
                              above this run in FP64 (<= 0: library default) */
+    int32_t acceptance;   /* CUBA_ACCEPT_ALL_PAIRS (0): every pair i < j of a
+                             cell draws its own uniform and is accepted iff
+                             u < P22 (Sec. 2, Eq. 3), the paper's test.
+                             CUBA_ACCEPT_SKIP (1): skip-ahead sampling of the
+                             same distribution — candidates along each row
+                             with geometric gaps at rate P_max = 2.0001 C,
+                             each kept with probability P22 / P_max (no
+                             counterpart in the paper; needs 2.0001 C < 1).
+                             Each pair is accepted with probability P22
+                             independently in both modes; the realisations
+                             differ. */
 } cuba_params;
+
+#define CUBA_ACCEPT_ALL_PAIRS 0
+#define CUBA_ACCEPT_SKIP 1
 
 /* Thermal region for cuba_init_thermal: an axis-aligned box at temperature T. */
 typedef struct cuba_region {
@@ -91,7 +105,8 @@ typedef struct cuba_counters {
     int64_t reflections;  /* wall reflections, one per axis crossing (A2) */
     int64_t fp64_boosts;  /* CUBA_FP32: collisions done in FP64 (A7) */
     int64_t overflow;     /* accepted pairs dropped for lack of list space */
-    int64_t reserved;
+    int64_t candidates;   /* CUBA_ACCEPT_SKIP: candidate pairs drawn (P22
+                             evaluated); 0 in the all-pairs mode */
 } cuba_counters;
 
 typedef struct cuba_sim cuba_sim;

@@ -80,12 +80,28 @@ int make_desc(const cuba_params* p, SimDesc* S)
     S->thr16 = (pb >= 1.0) ? 65536u : (uint32_t)std::floor(pb * 65536.0);
     S->gamma_fp64 = (float)(p->gamma_fp64 > 0.0 ? p->gamma_fp64 : kDefaultGammaFp64);
     S->step = 0;
+    if (p->acceptance != CUBA_ACCEPT_ALL_PAIRS && p->acceptance != CUBA_ACCEPT_SKIP)
+        return fail(CUBA_ERR_INVALID, "acceptance must be CUBA_ACCEPT_ALL_PAIRS or CUBA_ACCEPT_SKIP");
+    S->skip = p->acceptance == CUBA_ACCEPT_SKIP ? 1u : 0u;
+    if (S->skip && S->C > 0.0) {
+        // P_fix = floor(2.0001 C 2^64) >= 1; q = 1 - P_max; Q[b] = q^(2^b) by
+        // truncated 0.64 fixed-point squaring
+        if (!(pb < 1.0)) return fail(CUBA_ERR_P22, "skip-ahead needs 2.0001 C < 1 (C = %g)", S->C);
+        uint64_t P = (uint64_t)std::ldexp(pb, 64);
+        if (P == 0) P = 1;
+        S->pfix = P;
+        S->pmax = (double)P * 0x1p-64;
+        S->pmaxf = (float)S->pmax;
+        S->skipQ[0] = (uint64_t)0 - P;
+        for (int b = 1; b <= 32; ++b)
+            S->skipQ[b] = (uint64_t)(((unsigned __int128)S->skipQ[b - 1] * S->skipQ[b - 1]) >> 64);
+    }
     return CUBA_OK;
 }
 
 void arena_free(Arena& A)
 {
-    void* ptrs[] = {A.st[0], A.st[1], A.key[0], A.key[1], A.idx[0], A.idx[1], A.cell_start, A.cell_work,
+    void* ptrs[] = {A.st[0], A.st[1], A.key[0], A.key[1], A.idx[0], A.idx[1], A.cell_start, A.cell_work, A.skip_work,
                     A.acc_count, A.acc, A.radix_hist, A.scan_tmp, A.counters, A.active, A.used_bits, A.stats,
                     A.d_sims, A.trace_keys};
     for (void* p : ptrs)
@@ -120,6 +136,7 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
     if (!rc) rc = dalloc(&A.idx[1], pc * 4, "perm");
     if (!rc) rc = dalloc(&A.cell_start, ((size_t)ccap + 1) * 4, "cell_start");
     if (!rc) rc = dalloc(&A.cell_work, ((size_t)ccap + 1) * sizeof(uint2), "cell_work");
+    if (!rc) rc = dalloc(&A.skip_work, ((size_t)ccap + 1) * sizeof(uint32_t), "skip_work");
     if (!rc) rc = dalloc(&A.acc_count, (size_t)ccap * 4, "acc_count");
     if (!rc) rc = dalloc(&A.active, (size_t)ccap * 4, "active");
     A.radix_hist_cap = (uint32_t)(2 * kBinBins * ((pc + kSortTile - 1) / kSortTile + 1));
@@ -282,7 +299,8 @@ void StepGraphs::drop()
 int StepGraphs::run(Arena& A, int n, cudaStream_t st)
 {
     if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells ||
-        small_max != A.small_max || one_key != A.one_key || key0 != A.key_sched.k0[0] || key1 != A.key_sched.k1[0])
+        small_max != A.small_max || one_key != A.one_key || key0 != A.key_sched.k0[0] || key1 != A.key_sched.k1[0] ||
+        modes != A.any_skip * 2 + A.any_all_pairs)
         drop();
     for (int k = 0; k < n; ++k) {
         const int which = A.cur;
@@ -312,6 +330,7 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
             one_key = A.one_key;
             key0 = A.key_sched.k0[0];
             key1 = A.key_sched.k1[0];
+            modes = A.any_skip * 2 + A.any_all_pairs;
         }
         CUDA_TRY(cudaGraphLaunch(g[which], st), "graph launch");
         A.cur ^= 1;
@@ -323,6 +342,11 @@ void set_key_param(Arena& A, const SimDesc* table, int n)
 {
     A.one_key = n == 1;
     A.key_sched = n == 1 ? philox_schedule(table[0].key0, table[0].key1) : PhiloxKey{};
+    A.any_skip = 0;
+    A.any_all_pairs = 0;
+    for (int k = 0; k < n; ++k) {
+        if (table[k].skip) A.any_skip = 1; else A.any_all_pairs = 1;
+    }
 }
 
 int set_small_max(Arena& A, int32_t v)
@@ -709,7 +733,7 @@ int cuba_stats(cuba_sim* s, cuba_counters* out)
     out->reflections = (int64_t)h[kStatReflections];
     out->fp64_boosts = (int64_t)h[kStatFp64Boosts];
     out->overflow = (int64_t)h[kStatOverflow];
-    out->reserved = 0;
+    out->candidates = (int64_t)h[kStatCandidates];
     return read_kernel_errors(s->A);
 }
 

@@ -145,7 +145,8 @@ int64_t cuba_batch_bytes(const cuba_batch_config* cfg)
     const int64_t es = cfg->precision == CUBA_FP64 ? 8 : 4;
     const int64_t p = cfg->max_particles, c = cfg->max_cells;
     return 2 * 6 * p * es + 4 * 4 * p + p / 8 + 4 * (3 * c + 3) + 8 * (c + 1) + 20 * c +
-           4 * 256 * (p / kSortTile + 2) + (int64_t)cfg->max_sims * (kStatCount * 8 + (int64_t)sizeof(SimDesc));
+           4 * 2 * kBinBins * (p / kSortTile + 2) + (int64_t)bin_scan_bytes() +
+           (int64_t)cfg->max_sims * (kStatCount * 8 + (int64_t)sizeof(SimDesc));
 }
 
 int cuba_batch_create(const cuba_batch_config* cfg, cuba_batch** out)
@@ -313,7 +314,7 @@ int cuba_batch_stats(cuba_batch* b, int32_t id, cuba_counters* out)
     out->reflections = (int64_t)h[kStatReflections];
     out->fp64_boosts = (int64_t)h[kStatFp64Boosts];
     out->overflow = (int64_t)h[kStatOverflow];
-    out->reserved = 0;
+    out->candidates = (int64_t)h[kStatCandidates];
     return read_kernel_errors(b->A);
 }
 

@@ -35,6 +35,14 @@ struct SimDesc {
     uint32_t thr16;   // top 16 bits above thr16 reject a pair; 65536 = never
     float gamma_fp64; // FP32 path: CM boosts with gamma above this use FP64
     uint32_t stat_slot; // row of the counters array (stable while the simulation lives)
+    // skip-ahead acceptance (skip = 1): P_max = 2.0001 C as a 0.64 fixed-point
+    // fraction and rounded to double and float; skipQ[b] = (1 - P_max)^(2^b)
+    // in 0.64 fixed point, b = 0 .. 32
+    uint32_t skip;
+    float pmaxf;
+    uint64_t pfix;
+    double pmax;
+    uint64_t skipQ[33];
 };
 
 // Per-simulation counters (unsigned long long for atomics).
@@ -46,6 +54,7 @@ enum StatIdx {
     kStatReflections,
     kStatFp64Boosts,
     kStatOverflow,
+    kStatCandidates,  // skip-ahead candidates
     kStatCount = 8
 };
 
@@ -130,6 +139,7 @@ struct Arena {
     uint32_t* idx[2] = {nullptr, nullptr};
     uint32_t* cell_start = nullptr;     // ccap + 1
     uint2* cell_work = nullptr;         // ccap + 1: (pair items, list capacity) -> scanned
+    uint32_t* skip_work = nullptr;      // ccap + 1: skip-ahead row blocks per cell -> scanned
     uint32_t* acc_count = nullptr;      // ccap
     unsigned long long* acc = nullptr;  // accepted (i << 32 | j), per-cell segments
     uint64_t acc_capacity = 0;
@@ -152,6 +162,8 @@ struct Arena {
     // parameter (set whenever the descriptor table is uploaded)
     int one_key = 0;
     PhiloxKey key_sched = {};
+    // which acceptance modes the resident simulations use
+    int any_all_pairs = 1, any_skip = 0;
 };
 
 // ---- launchers (kernels_sort.cu) ----

@@ -51,7 +51,8 @@ int settle_arena(Arena& A, cudaStream_t st, int* realloc);
 int read_kernel_errors(Arena& A);
 int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms);
 int set_small_max(Arena& A, int32_t v);
-// Record the descriptor table's key for the pair kernels (after every upload).
+// Record the descriptor table's key and acceptance modes for the pair
+// kernels (after every upload).
 void set_key_param(Arena& A, const SimDesc* table, int n);
 
 // Captured step graphs (one per ping-pong buffer) and what they were
@@ -60,7 +61,7 @@ struct StepGraphs {
     cudaGraphExec_t g[2] = {nullptr, nullptr};
     cudaStream_t capture = nullptr;
     uint32_t np = 0, ncells = 0, small_max = 0;
-    int one_key = 0;
+    int one_key = 0, modes = 0;
     uint32_t key0 = 0, key1 = 0;
     const void* acc = nullptr;
     int trace = 0, nsims = 0;

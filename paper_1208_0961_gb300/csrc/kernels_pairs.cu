@@ -51,14 +51,20 @@ __device__ __forceinline__ void unit_dir(const T* __restrict__ st, uint32_t pcap
 
 // P22 = C v_rel with v_rel = s / (2 E_i E_j) = |n_i - n_j|^2 / 2 (massless).
 template <typename T>
+__device__ __forceinline__ T p22_of_units(T C, const T ui[3], const T uj[3])
+{
+    const T d0 = sub_rn(ui[0], uj[0]), d1 = sub_rn(ui[1], uj[1]), d2 = sub_rn(ui[2], uj[2]);
+    const T v = mul_rn(T(0.5), add_rn(add_rn(mul_rn(d0, d0), mul_rn(d1, d1)), mul_rn(d2, d2)));
+    return mul_rn(C, v);
+}
+
+template <typename T>
 __device__ __forceinline__ T pair_p22(T C, const T* __restrict__ st, uint32_t pcap, uint32_t gi, uint32_t gj)
 {
     T ui[3], uj[3];
     unit_dir<T>(st, pcap, gi, ui);
     unit_dir<T>(st, pcap, gj, uj);
-    const T d0 = sub_rn(ui[0], uj[0]), d1 = sub_rn(ui[1], uj[1]), d2 = sub_rn(ui[2], uj[2]);
-    const T v = mul_rn(T(0.5), add_rn(add_rn(mul_rn(d0, d0), mul_rn(d1, d1)), mul_rn(d2, d2)));
-    return mul_rn(C, v);
+    return p22_of_units<T>(C, ui, uj);
 }
 
 // Exact per-byte test of one word: bit b of the result (b = 0..3) is set iff
@@ -110,6 +116,25 @@ struct CellCtx {
     uint32_t slot;    // its counters row
 };
 
+// Append accepted pair (i, j) to its cell's list; kMark: the cell's first
+// accepted pair enters it in the active-cell list.
+template <bool kMark>
+__device__ __forceinline__ void append_accepted(const CellCtx& cc, uint32_t i, uint32_t j,
+                                                uint32_t* __restrict__ acc_count,
+                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                unsigned long long* __restrict__ stats)
+{
+    const uint32_t slot = atomicAdd(&acc_count[cc.c], 1u);
+    if (kMark && slot == 0) active[atomicAdd(&counters[2], 1u)] = cc.c;
+    if (slot < cc.room && (uint64_t)cc.list0 + slot < acc_cap) {
+        acc[(size_t)cc.list0 + slot] = ((unsigned long long)i << 32) | j;
+    } else {
+        atomicOr(&counters[1], kErrAccOverflow);
+        atomicAdd(&stats[cc.slot * kStatCount + kStatOverflow], 1ull);
+    }
+}
+
 // Resolve queued blocks [e0, e1) of the warp, one block per lane.  The bytes
 // <= thr8 at real pairs j (i < j < n) are first refined by the pair's middle
 // byte, drawn from the block (step, cell, i, TAG_MID | g) shared by the 16
@@ -144,16 +169,7 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
             const uint32_t rw = (r16 << 16) | (fine >> 16);
             const T u = unit_u<T>(rw);
             const T P = pair_p22<T>(C, st, pcap, cc.cbase + i, cc.cbase + j);
-            if (u < P) {
-                const uint32_t slot = atomicAdd(&acc_count[cc.c], 1u);
-                if (kMark && slot == 0) active[atomicAdd(&counters[2], 1u)] = cc.c;
-                if (slot < cc.room && (uint64_t)cc.list0 + slot < acc_cap) {
-                    acc[(size_t)cc.list0 + slot] = ((unsigned long long)i << 32) | j;
-                } else {
-                    atomicOr(&counters[1], kErrAccOverflow);
-                    atomicAdd(&stats[cc.slot * kStatCount + kStatOverflow], 1ull);
-                }
-            }
+            if (u < P) append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
         }
     }
 }
@@ -222,6 +238,145 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
                                  counters, active, stats);
         __syncwarp();
     }
+}
+
+// ---------------------------------------------------------------------------
+// A5, skip-ahead mode
+// ---------------------------------------------------------------------------
+// Gap of the skip-ahead mode: with M columns left after the last candidate,
+// the largest G < 2^(bt+1), bt = ceil(log2 M), whose 0.64 fixed-point power
+// q^G — built greedily from bit bt down with the table Q[b] = q^(2^b) — is
+// still >= U.  P(G >= k) = q^k up to rounding: the inverse CDF of the
+// geometric distribution of the gap between Bernoulli(1 - q) candidates.
+// G >= M means no candidate is left in the row.
+__device__ __forceinline__ uint64_t skip_gap(const uint64_t* __restrict__ Q, uint64_t U, uint32_t M)
+{
+    const int bt = M <= 1u ? 0 : 32 - __clz(M - 1u);
+    uint64_t G = 0, Qc = ~0ull;
+    for (int b = bt; b >= 0; --b) {
+        const uint64_t t = __umul64hi(Qc, Q[b]);
+        if (t >= U) {
+            Qc = t;
+            G += 1ull << b;
+            if (G >= M) break;  // G only grows: the row has ended
+        }
+    }
+    return G;
+}
+
+template <typename T> __device__ __forceinline__ T skip_pmax(const SimDesc& S);
+template <> __device__ __forceinline__ double skip_pmax<double>(const SimDesc& S) { return S.pmax; }
+template <> __device__ __forceinline__ float skip_pmax<float>(const SimDesc& S) { return S.pmaxf; }
+
+// Rows [32 rb, 32 rb + 32) of one cell in the skip-ahead mode, one row per
+// lane: the k-th draw of row i is the Philox block (step, cell, i,
+// TAG_SKIP | k) — words 0 and 1 the 64-bit uniform of the gap, word 2 the
+// thinning uniform; candidate j is kept iff (w 2^-32) P_max < P22 in the
+// state's precision, i.e. with probability P22 / P_max.
+// Returns this lane's number of candidates.
+template <typename T, bool kMark>
+__device__ __forceinline__ uint32_t skip_rows(const CellCtx& cc, uint32_t rb, const SimDesc& S, T C,
+                                              const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap,
+                                              uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
+                                              uint64_t acc_cap, uint32_t* __restrict__ counters,
+                                              uint32_t* __restrict__ active, unsigned long long* __restrict__ stats)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t i = rb * kPairRows + lane;
+    uint32_t cand = 0;
+    if (i + 1 < cc.n) {
+        T ui[3];
+        unit_dir<T>(st, pcap, cc.cbase + i, ui);  // row particle, loaded once (coalesced over the lanes)
+        PhiloxRow R;
+        R.init(S.step, cc.lc, i, K);
+        const T pm = skip_pmax<T>(S);
+        uint32_t pos = i;
+        for (uint32_t k = 0;; ++k) {
+            const uint32_t M = cc.n - 1u - pos;
+            if (M == 0) break;
+            const uint4 w = R.block(kTagSkip | k, K);
+            const uint64_t G = skip_gap(S.skipQ, ((uint64_t)w.x << 32) | w.y, M);
+            if (G >= M) break;
+            const uint32_t j = pos + 1u + (uint32_t)G;
+            ++cand;
+            const T u = mul_rn(unit_u<T>(w.z), pm);
+            T uj[3];
+            unit_dir<T>(st, pcap, cc.cbase + j, uj);
+            if (u < p22_of_units<T>(C, ui, uj))
+                append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
+            pos = j;
+        }
+    }
+    return cand;
+}
+
+// Skip-ahead cells (A5 in the skip-ahead mode): one warp per 32-row block,
+// blocks taken grid-stride from the scanned per-cell counts skip_work (no
+// work counter: the rows cost about the same).  Cells above small_max enter
+// the active list (the per-cell resolve), smaller ones are found by the
+// warp-per-cell resolve.  Candidates are summed per warp and simulation.
+template <typename T, bool kOneKey>
+__global__ void __launch_bounds__(kPairThreads, 4)
+    k_pair_skip(const SimDesc* __restrict__ sims, int nsims, const T* __restrict__ st, uint32_t pcap,
+                const uint32_t* __restrict__ cell_start, const uint2* __restrict__ work,
+                const uint32_t* __restrict__ skip_work, uint32_t ncells, uint32_t small_max,
+                uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                uint32_t* __restrict__ counters, uint32_t* __restrict__ active, unsigned long long* __restrict__ stats,
+                const PhiloxKey Kp)
+{
+    if ((uint64_t)work[ncells].y > acc_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&counters[1], kErrCapacity);
+        return;
+    }
+    const uint32_t total = skip_work[ncells];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    // a contiguous range of row blocks per warp: consecutive rows of a cell
+    const uint32_t per = (total + nw - 1) / nw;
+    const uint32_t i0 = min(total, gw * per), i1 = min(total, i0 + per);
+    uint32_t cur_slot = 0xFFFFFFFFu, cand = 0;
+    uint32_t c = 0;
+    if (i0 < i1) {
+        // cell of the first item: the last c with skip_work[c] <= i0
+        uint32_t lo = 0, hi = ncells - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (skip_work[mid] <= i0) lo = mid; else hi = mid - 1;
+        }
+        c = lo;
+    }
+    for (uint32_t item = i0; item < i1; ++item) {
+        while (skip_work[c + 1] <= item) ++c;
+        CellCtx cc;
+        cc.c = c;
+        cc.s = sim_of_cell(sims, nsims, c);
+        const SimDesc& S = sims[cc.s];
+        cc.slot = S.stat_slot;
+        cc.lc = c - S.cell_off;
+        cc.cbase = cell_start[c];
+        cc.n = cell_start[c + 1] - cc.cbase;
+        const uint2 w0 = work[c], w1 = work[c + 1];
+        cc.list0 = w0.y;
+        cc.room = w1.y - w0.y;
+        if (cc.slot != cur_slot) {
+            const unsigned tot = __reduce_add_sync(kFull, cand);
+            if (lane == 0 && tot) atomicAdd(&stats[cur_slot * kStatCount + kStatCandidates], (unsigned long long)tot);
+            cand = 0;
+            cur_slot = cc.slot;
+        }
+        const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
+        const PhiloxKey& K = kOneKey ? Kp : Kl;
+        const uint32_t rb = item - skip_work[c];
+        if (cc.n > small_max)
+            cand += skip_rows<T, true>(cc, rb, S, sim_C<T>(S), K, st, pcap, acc_count, acc, acc_cap, counters,
+                                       active, stats);
+        else
+            cand += skip_rows<T, false>(cc, rb, S, sim_C<T>(S), K, st, pcap, acc_count, acc, acc_cap, counters,
+                                        active, stats);
+    }
+    const unsigned tot = __reduce_add_sync(kFull, cand);
+    if (lane == 0 && tot) atomicAdd(&stats[cur_slot * kStatCount + kStatCandidates], (unsigned long long)tot);
 }
 
 // kOneKey: every cell belongs to one simulation whose round keys come as the
@@ -316,7 +471,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_small(const SimDesc* __re
         if (n < 2 || n > small_max) continue;
         const int s = sim_of_cell(sims, nsims, c);
         const SimDesc& S = sims[s];
-        if (!(S.C > 0.0)) continue;
+        if (!(S.C > 0.0) || S.skip) continue;  // skip-ahead cells: k_pair_skip
         CellCtx cc;
         cc.c = c;
         cc.s = s;
@@ -738,8 +893,26 @@ static unsigned small_grid()
 }
 
 template <typename T, bool kOneKey>
+static unsigned skip_grid()
+{
+    static unsigned g = 0;
+    if (!g) {
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_skip<T, kOneKey>, kPairThreads, 0);
+        if (per < 1) per = 1;
+        g = (unsigned)(per * sm_count());
+    }
+    return g;
+}
+
+template <typename T, bool kOneKey>
 static void launch_pairs(const Arena& A, cudaStream_t st)
 {
+    if (A.any_skip)
+        k_pair_skip<T, kOneKey><<<skip_grid<T, kOneKey>(), kPairThreads, 0, st>>>(
+            A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.skip_work, A.ncells,
+            A.small_max, A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
+    if (!A.any_all_pairs) return;
     if (A.small_max)
         k_pair_small<T, kOneKey><<<small_grid<T, kOneKey>(), kPairThreads, 0, st>>>(
             A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.small_max,
@@ -782,6 +955,10 @@ int kernels_init()
     small_grid<float, false>();
     small_grid<double, true>();
     small_grid<float, true>();
+    skip_grid<double, false>();
+    skip_grid<float, false>();
+    skip_grid<double, true>();
+    skip_grid<float, true>();
     sm_count();
     done = true;
     return 0;

@@ -381,8 +381,11 @@ __device__ __forceinline__ uint32_t list_room(double C, uint32_t n)
     return room > 4.0e9 ? 0xFFFFFFFFu : (uint32_t)room;
 }
 
+// work[c] = (row-block items of the all-pairs tile, list room); skip_work[c]
+// = row blocks of a skip-ahead cell (null when no simulation uses that mode).
 __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ sims, int nsims,
                                                    const uint32_t* __restrict__ cell_start, uint2* __restrict__ work,
+                                                   uint32_t* __restrict__ skip_work,
                                                    uint32_t* __restrict__ acc_count, uint32_t ncells, uint32_t small_max,
                                                    uint32_t* __restrict__ counters, unsigned long long* __restrict__ stats,
                                                    int count_pairs)
@@ -393,6 +396,7 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
         counters[0] = 0;  // pair work counter
         counters[2] = 0;  // active cells
         work[ncells] = make_uint2(0, 0);
+        if (skip_work) skip_work[ncells] = 0;
     }
     // pair tests summed per thread and simulation, flushed on a change
     uint32_t cur_slot = 0xFFFFFFFFu;
@@ -401,9 +405,10 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
         const int s = sim_of_cell(sims, nsims, c);
         const SimDesc& S = sims[s];
         const uint32_t n = cell_start[c + 1] - cell_start[c];
-        uint32_t items = 0, room = 0;
+        uint32_t items = 0, room = 0, skip_items = 0;
         if (n >= 2 && S.C > 0.0) {
-            if (n > small_max) items = (n - 1 + kPairRows - 1) / kPairRows;
+            if (S.skip) skip_items = (n - 1 + kPairRows - 1) / kPairRows;
+            else if (n > small_max) items = (n - 1 + kPairRows - 1) / kPairRows;
             room = list_room(S.C, n);
             if (count_pairs) {
                 if (S.stat_slot != cur_slot) {
@@ -415,6 +420,7 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
             }
         }
         work[c] = make_uint2(items, room);
+        if (skip_work) skip_work[c] = skip_items;
         acc_count[c] = 0;
     }
     // one atomic per warp and simulation
@@ -664,11 +670,17 @@ int launch_sort_and_bin(Arena& A, cudaStream_t st)
 int launch_cell_prep(const Arena& A, cudaStream_t st, int count_pairs)
 {
     const unsigned g = grid_for(A.ncells, 256, 8);
-    k_cell_prep<<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.cell_start, A.cell_work, A.acc_count, A.ncells, A.small_max,
-                                   A.counters, A.stats, count_pairs);
+    uint32_t* skip_work = A.any_skip ? A.skip_work : nullptr;
+    k_cell_prep<<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.cell_start, A.cell_work, skip_work, A.acc_count, A.ncells,
+                                   A.small_max, A.counters, A.stats, count_pairs);
     if (last_err()) return -1;
-    return exclusive_scan<uint2, Uint2Add>(A.cell_work, (size_t)A.ncells + 1, make_uint2(0, 0), Uint2Add(), A.scan_tmp,
-                                           A.scan_tmp_bytes, st);
+    if (exclusive_scan<uint2, Uint2Add>(A.cell_work, (size_t)A.ncells + 1, make_uint2(0, 0), Uint2Add(), A.scan_tmp,
+                                        A.scan_tmp_bytes, st))
+        return -1;
+    if (skip_work && exclusive_scan<uint32_t, U32Add>(skip_work, (size_t)A.ncells + 1, 0u, U32Add(), A.scan_tmp,
+                                                      A.scan_tmp_bytes, st))
+        return -1;
+    return 0;
 }
 
 int launch_observables(const Arena& A, int sim, double* T00, double* T0x, int32_t* counts, cudaStream_t st)

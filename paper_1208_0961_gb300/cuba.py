@@ -21,6 +21,8 @@ CUBA_ERR_P22 = -5
 CUBA_ERR_CAPACITY = -6
 CUBA_FP32 = 0
 CUBA_FP64 = 1
+CUBA_ACCEPT_ALL_PAIRS = 0
+CUBA_ACCEPT_SKIP = 1
 
 FM2_PER_MB = 0.1
 
@@ -35,6 +37,7 @@ class cuba_params(C.Structure):
         ("precision", C.c_int32),
         ("seed", C.c_uint64),
         ("gamma_fp64", C.c_double),
+        ("acceptance", C.c_int32),
     ]
 
 
@@ -45,7 +48,7 @@ class cuba_region(C.Structure):
 class cuba_counters(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("steps", "pair_tests", "accepted", "executed", "reflections", "fp64_boosts", "overflow",
-                 "reserved")]
+                 "candidates")]
 
 
 class cuba_batch_config(C.Structure):
@@ -157,7 +160,7 @@ def _ptr(x):
 
 
 def make_params(L=(10.0, 1.0, 1.0), n_cells=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_test=1.0,
-                precision=CUBA_FP64, seed=0, gamma_fp64=0.0):
+                precision=CUBA_FP64, seed=0, gamma_fp64=0.0, acceptance=0):
     p = cuba_params()
     for a in range(3):
         p.L[a] = float(L[a])
@@ -168,6 +171,7 @@ def make_params(L=(10.0, 1.0, 1.0), n_cells=(100, 1, 1), dt=0.05, sigma_fm2=1.0,
     p.precision = int(precision)
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.gamma_fp64 = float(gamma_fp64)
+    p.acceptance = int(acceptance)
     return p
 
 

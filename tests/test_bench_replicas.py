@@ -84,3 +84,5 @@ def test_launch_count():
     # no small-cell kernels) and 20 (64 M, 128^3 cells, small-cell kernels)
     assert bench.launches_per_step(2000, 0) == 12
     assert bench.launches_per_step(128 ** 3, 64) == 20
+    # skip-ahead (15 per step of the 16 M workload in its ncu launch list)
+    assert bench.launches_per_step(2000, 0, skip=True) == 15

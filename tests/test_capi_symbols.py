@@ -3,6 +3,7 @@ include/cuba.h declares; the binding's struct layouts match the header."""
 import ctypes
 import os
 import re
+import subprocess
 
 from paper_1208_0961_gb300 import cuba
 
@@ -23,11 +24,27 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
-def test_struct_sizes_match_header_layout():
-    # cuba_params: 3 doubles, 3 int32 (+4 pad), 3 doubles, int32 (+4 pad), uint64, double
-    assert ctypes.sizeof(cuba.cuba_params) == 24 + 16 + 24 + 8 + 8 + 8
-    assert ctypes.sizeof(cuba.cuba_region) == 56
-    assert ctypes.sizeof(cuba.cuba_counters) == 64
+def test_struct_sizes_match_header_layout(tmp_path):
+    # the C compiler's layout of the header's structs against the binding's
+    structs = {"cuba_params": cuba.cuba_params, "cuba_region": cuba.cuba_region,
+               "cuba_counters": cuba.cuba_counters, "cuba_batch_config": cuba.cuba_batch_config}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cuba.h"', 'int main(void) {']
+    for name, ct in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in ct._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name, ct in structs.items():
+        assert int(got[name]) == ctypes.sizeof(ct), name
+        for f, _ in ct._fields_:
+            assert int(got["%s.%s" % (name, f)]) == getattr(ct, f).offset, (name, f)
 
 
 def test_invalid_parameters_are_rejected_without_a_gpu():

@@ -22,15 +22,17 @@ from paper_1208_0961_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0):
+def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0, skip=False):
     p = cuba.make_params(L=L, n_cells=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test,
-                         precision=cuba.CUBA_FP32 if fp32 else cuba.CUBA_FP64, seed=seed, gamma_fp64=gamma_fp64)
-    op = O.make_params(L=L, n=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test, fp32=fp32, seed=seed)
+                         precision=cuba.CUBA_FP32 if fp32 else cuba.CUBA_FP64, seed=seed, gamma_fp64=gamma_fp64,
+                         acceptance=cuba.CUBA_ACCEPT_SKIP if skip else cuba.CUBA_ACCEPT_ALL_PAIRS)
+    op = O.make_params(L=L, n=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test, fp32=fp32, seed=seed, skip=skip)
     return p, op
 
 
-def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_index=3, small_max=None):
-    p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed)
+def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_index=3, small_max=None,
+                      skip=False):
+    p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, skip=skip)
     dtype = np.float32 if fp32 else np.float64
     st0 = st0.astype(dtype)
     n = st0.shape[1]
@@ -81,6 +83,7 @@ def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_i
     assert stats["executed"] == len(exe_o)
     assert stats["reflections"] == res.n_reflections
     assert stats["pair_tests"] == res.n_pairs_tested
+    assert stats["candidates"] == res.n_candidates
     return len(acc_o), len(exe_o)
 
 
