@@ -544,7 +544,14 @@ def main():
                 "ops_per_pair": ops_per_pair,
                 "peak_basis": "%d SMs x 128 lanes x %.0f MHz (sampled median)" % (n_sm, sm_mhz),
                 "multiply_pipe_peak_pair_tests_per_s": pipe_peak,
-                "multiply_pipe_frac": pairs_per_step / pair_s / pipe_peak}
+                "multiply_pipe_frac": pairs_per_step / pair_s / pipe_peak,
+                # the pair-test rate against the FP32 peak, at the 9 flops per
+                # pair an FP32 all-pairs tile would spend (dot product, P22,
+                # uniform conversion, compare)
+                "fp32_equivalent": {"flops_per_pair": 9,
+                                    "achieved_tflops": 9.0 * pairs_per_step / pair_s / 1e12,
+                                    "peak_tflops": n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12,
+                                    "frac": 9.0 * pairs_per_step / pair_s / (n_sm * 128 * 2 * sm_mhz * 1e6)}}
     # stream/bin phases against HBM: 56 algorithmic bytes per update (FP32)
     bpu = 56.0 if prec == cuba.CUBA_FP32 else 104.0
     sb_ms = (phase[0] + phase[1]) / max(1, args.profile_steps)

@@ -445,9 +445,11 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey>::min_blocks)
 }
 
 // Small cells (2 <= n <= small_max): one warp per cell, all its rows, found
-// by a grid-stride scan over the cells (no work queue, no per-cell atomic).
+// by a grid-stride scan over groups of 32 cells (no work queue, no per-cell
+// atomic); the bounds and list rooms of a group are read in one coalesced
+// round, one cell per lane, and handed to the cells' turns by shuffles.
 template <typename T, bool kOneKey>
-__global__ void __launch_bounds__(kPairThreads) k_pair_small(const SimDesc* __restrict__ sims, int nsims,
+__global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* __restrict__ sims, int nsims,
                                                              const T* __restrict__ st, uint32_t pcap,
                                                              const uint32_t* __restrict__ cell_start,
                                                              const uint2* __restrict__ work, uint32_t ncells,
@@ -464,30 +466,43 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_small(const SimDesc* __re
     __shared__ uint2 q_ig[kWarps][queue_cap(NB) + 32];
     const int w = threadIdx.x >> 5;
     if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kWarps;
-    for (uint32_t c = blockIdx.x * kWarps + w; c < ncells; c += nwarps) {
-        const uint32_t cbase = cell_start[c];
-        const uint32_t n = cell_start[c + 1] - cbase;
-        if (n < 2 || n > small_max) continue;
-        const int s = sim_of_cell(sims, nsims, c);
-        const SimDesc& S = sims[s];
-        if (!(S.C > 0.0) || S.skip) continue;  // skip-ahead cells: k_pair_skip
-        CellCtx cc;
-        cc.c = c;
-        cc.s = s;
-        cc.slot = S.stat_slot;
-        cc.lc = c - S.cell_off;
-        cc.cbase = cbase;
-        cc.n = n;
-        const uint2 w0 = work[c], w1 = work[c + 1];
-        cc.list0 = w0.y;
-        cc.room = w1.y - w0.y;
-        const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
-        const PhiloxKey& K = kOneKey ? Kp : Kl;
-        const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
-        for (uint32_t rb = 0; rb < nrb; ++rb)
-            pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_ig[w],
-                                acc_count, acc, acc_cap, counters, active, stats);
+    for (uint32_t c0 = (blockIdx.x * kWarps + w) * 32u; c0 < ncells; c0 += nwarps * 32u) {
+        const uint32_t cl = c0 + lane;
+        uint32_t my_base = 0, my_n = 0, my_list0 = 0, my_room = 0;
+        if (cl < ncells) {
+            my_base = cell_start[cl];
+            my_n = cell_start[cl + 1] - my_base;
+            const uint2 w0 = work[cl], w1 = work[cl + 1];
+            my_list0 = w0.y;
+            my_room = w1.y - w0.y;
+        }
+        unsigned todo = __ballot_sync(kFull, cl < ncells && my_n >= 2 && my_n <= small_max);
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t c = c0 + (uint32_t)k;
+            const uint32_t n = __shfl_sync(kFull, my_n, k);
+            const int s = sim_of_cell(sims, nsims, c);
+            const SimDesc& S = sims[s];
+            if (!(S.C > 0.0) || S.skip) continue;  // skip-ahead cells: k_pair_skip
+            CellCtx cc;
+            cc.c = c;
+            cc.s = s;
+            cc.slot = S.stat_slot;
+            cc.lc = c - S.cell_off;
+            cc.cbase = __shfl_sync(kFull, my_base, k);
+            cc.n = n;
+            cc.list0 = __shfl_sync(kFull, my_list0, k);
+            cc.room = __shfl_sync(kFull, my_room, k);
+            const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
+            const PhiloxKey& K = kOneKey ? Kp : Kl;
+            const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
+            for (uint32_t rb = 0; rb < nrb; ++rb)
+                pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_ig[w],
+                                        acc_count, acc, acc_cap, counters, active, stats);
+        }
     }
 }
 
@@ -732,13 +747,38 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(const SimDesc* __re
     }
 }
 
-// A6-A7 for small cells (n <= small_max <= 1024) with at most 32 accepted
-// pairs: one warp per cell, found by a grid-stride scan.  The list is sorted
-// by rank counting across the lanes, the greedy matching taken by lane 0 on a
-// shared-memory bitmap of the cell, and the kinematics applied one pair per
-// lane.  Small cells with more accepted pairs are handed to the block path by
-// appending them to the active-cell list.  Counters are summed per warp and
-// flushed once per simulation change.
+// A6-A7 for small cells (n <= small_max <= 1024) with at most kLaneList
+// accepted pairs: one lane per cell, 32 consecutive cells per warp (their
+// counts and bounds read in one coalesced round).  A lane walks its cell's
+// list in increasing (i, j) order (the lists are tiny: repeated minimum
+// search) and takes the greedy matching on a list of used particles; the
+// executed pairs of the 32 cells go to a per-warp shared-memory queue and
+// their kinematics run one pair per lane (executed pairs share no particle,
+// so their order does not matter).  Cells with longer lists are handed to the
+// block path through the active-cell list.  Counters are summed per lane and
+// flushed per simulation (one atomic per warp and simulation).
+constexpr uint32_t kLaneList = 8;
+constexpr uint32_t kResolveQueue = 32 * kLaneList;  // executed pairs of 32 cells at most
+
+__device__ __forceinline__ void flush_resolve_stats(uint32_t slot, unsigned long long& a_acc,
+                                                    unsigned long long& a_exe,
+                                                    unsigned long long* __restrict__ stats)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(kFull, slot);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long sa = 0, se = 0;
+    for (unsigned m = peers; m; m &= m - 1) {
+        sa += __shfl_sync(peers, a_acc, __ffs(m) - 1);
+        se += __shfl_sync(peers, a_exe, __ffs(m) - 1);
+    }
+    if ((int)lane == leader && slot != 0xFFFFFFFFu) {
+        if (sa) atomicAdd(&stats[slot * kStatCount + kStatAccepted], sa);
+        if (se) atomicAdd(&stats[slot * kStatCount + kStatExecuted], se);
+    }
+    a_acc = a_exe = 0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_resolve_small(const SimDesc* __restrict__ sims, int nsims, T* __restrict__ st,
                                                        uint32_t pcap, const uint32_t* __restrict__ cell_start,
@@ -749,83 +789,84 @@ __global__ void __launch_bounds__(256) k_resolve_small(const SimDesc* __restrict
                                                        unsigned long long* __restrict__ stats)
 {
     constexpr int kWarps = 8;
-    __shared__ unsigned long long sl[kWarps][32];
-    __shared__ uint32_t sbits[kWarps][32];
+    __shared__ uint4 q[kWarps][kResolveQueue];  // (cell, i, j, first particle of the cell)
+    __shared__ uint32_t qn[kWarps];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kWarps;
     uint32_t cur_slot = 0xFFFFFFFFu;
-    unsigned long long a_acc = 0, a_exe = 0, a_64 = 0;
-    for (uint32_t c = blockIdx.x * kWarps + w; c < ncells; c += nwarps) {
-        const uint32_t cnt = acc_count[c];
-        if (cnt == 0) continue;
-        const uint32_t cbase = cell_start[c];
-        const uint32_t n = cell_start[c + 1] - cbase;
-        if (n < 2 || n > small_max) continue;
-        const uint2 w0 = work[c], w1 = work[c + 1];
-        const uint32_t room = w1.y - w0.y;
-        uint32_t m = cnt < room ? cnt : room;
-        if ((uint64_t)w0.y + m > acc_cap) m = (w0.y < acc_cap) ? (uint32_t)(acc_cap - w0.y) : 0u;
-        if (m > 32) {
-            if (lane == 0) active[atomicAdd(&counters[2], 1u)] = c;
-            continue;
-        }
-        const int s = sim_of_cell(sims, nsims, c);
-        const SimDesc& S = sims[s];
-        const uint32_t slot = S.stat_slot;
-        if (slot != cur_slot) {
-            if (lane == 0 && cur_slot != 0xFFFFFFFFu) {
-                atomicAdd(&stats[cur_slot * kStatCount + kStatAccepted], a_acc);
-                atomicAdd(&stats[cur_slot * kStatCount + kStatExecuted], a_exe);
-                if (a_64) atomicAdd(&stats[cur_slot * kStatCount + kStatFp64Boosts], a_64);
+    unsigned long long a_acc = 0, a_exe = 0;
+    for (uint32_t c0 = (blockIdx.x * kWarps + w) * 32u; c0 < ncells; c0 += nwarps * 32u) {
+        if (lane == 0) qn[w] = 0;
+        __syncwarp();
+        const uint32_t c = c0 + lane;
+        uint32_t cnt = 0, cbase = 0, n = 0, m = 0, list0 = 0;
+        bool mine = false;
+        if (c < ncells) {
+            cnt = acc_count[c];
+            if (cnt) {
+                cbase = cell_start[c];
+                n = cell_start[c + 1] - cbase;
+                if (n >= 2 && n <= small_max) {
+                    const uint2 w0 = work[c], w1 = work[c + 1];
+                    const uint32_t room = w1.y - w0.y;
+                    m = cnt < room ? cnt : room;
+                    if ((uint64_t)w0.y + m > acc_cap) m = (w0.y < acc_cap) ? (uint32_t)(acc_cap - w0.y) : 0u;
+                    list0 = w0.y;
+                    if (m > kLaneList) active[atomicAdd(&counters[2], 1u)] = c;
+                    else mine = true;
+                }
             }
-            a_acc = a_exe = a_64 = 0;
+        }
+        uint32_t slot = 0xFFFFFFFFu;
+        if (mine) slot = sims[sim_of_cell(sims, nsims, c)].stat_slot;
+        if (__any_sync(kFull, mine && slot != cur_slot && cur_slot != 0xFFFFFFFFu)) flush_resolve_stats(cur_slot, a_acc, a_exe, stats);
+        if (mine) {
             cur_slot = slot;
-        }
-        unsigned long long* gl = acc + w0.y;
-        const unsigned long long v = lane < m ? gl[lane] : ~0ull;
-        uint32_t rank = 0;
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) rank += (__shfl_sync(kFull, v, k) < v) ? 1u : 0u;
-        if (lane < m) sl[w][rank] = v;
-        for (uint32_t k = lane; k < (n + 31) / 32; k += 32) sbits[w][k] = 0u;
-        __syncwarp();
-        uint32_t ne = 0;
-        if (lane == 0) {
-            for (uint32_t k = 0; k < m; ++k) {
-                const unsigned long long e = sl[w][k];
-                const uint32_t i = (uint32_t)(e >> 32), j = (uint32_t)e;
-                const uint32_t bi = (sbits[w][i >> 5] >> (i & 31)) & 1u;
-                const uint32_t bj = (sbits[w][j >> 5] >> (j & 31)) & 1u;
-                if (bi | bj) continue;
-                sbits[w][i >> 5] |= 1u << (i & 31);
-                sbits[w][j >> 5] |= 1u << (j & 31);
-                sl[w][k] = e | kExecFlag;
-                ++ne;
+            // greedy in lexicographic order: repeatedly the smallest unvisited
+            // entry; the list is written back sorted, executed pairs flagged
+            unsigned long long* gl = acc + list0;
+            unsigned long long v[kLaneList];
+            for (uint32_t k = 0; k < m; ++k) v[k] = gl[k];
+            uint32_t used[2 * kLaneList];
+            uint32_t nused = 0, done = 0;  // done: bit k = entry k visited
+            for (uint32_t r = 0; r < m; ++r) {
+                unsigned long long best = ~0ull;
+                uint32_t kb = 0;
+                for (uint32_t k = 0; k < m; ++k) {
+                    if (!((done >> k) & 1u) && v[k] < best) {
+                        best = v[k];
+                        kb = k;
+                    }
+                }
+                done |= 1u << kb;
+                const uint32_t i = (uint32_t)(best >> 32), j = (uint32_t)best;
+                bool free_ij = true;
+                for (uint32_t u = 0; u < nused; ++u) free_ij &= (used[u] != i) & (used[u] != j);
+                if (free_ij) {
+                    used[nused++] = i;
+                    used[nused++] = j;
+                    best |= kExecFlag;
+                    const uint32_t qs = atomicAdd(&qn[w], 1u);
+                    q[w][qs] = make_uint4(c, i, j, cbase);
+                }
+                gl[r] = best;
             }
+            a_acc += cnt;
+            a_exe += nused / 2;
         }
         __syncwarp();
-        uint32_t n64 = 0;
-        if (lane < m) {
-            const unsigned long long e = sl[w][lane];
-            if (e & kExecFlag) {
-                const uint32_t i = (uint32_t)(e >> 32) & 0x7FFFFFFFu, j = (uint32_t)e;
-                const PhiloxKey K = philox_schedule(S.key0, S.key1);
-                n64 = (uint32_t)collide_state<T>(S, K, c - S.cell_off, i, j, st, pcap, cbase + i, cbase + j);
-            }
-            gl[lane] = e;
+        const uint32_t ne = qn[w];
+        for (uint32_t k = lane; k < ne; k += 32) {
+            const uint4 e = q[w][k];
+            const SimDesc& S = sims[sim_of_cell(sims, nsims, e.x)];
+            const PhiloxKey K = philox_schedule(S.key0, S.key1);
+            const int u64 = collide_state<T>(S, K, e.x - S.cell_off, e.y, e.z, st, pcap, e.w + e.y, e.w + e.z);
+            if (u64) atomicAdd(&stats[S.stat_slot * kStatCount + kStatFp64Boosts], 1ull);
         }
-        n64 = __reduce_add_sync(kFull, n64);
-        a_acc += cnt;
-        a_exe += __shfl_sync(kFull, ne, 0);
-        a_64 += n64;
         __syncwarp();
     }
-    if (lane == 0 && cur_slot != 0xFFFFFFFFu) {
-        atomicAdd(&stats[cur_slot * kStatCount + kStatAccepted], a_acc);
-        atomicAdd(&stats[cur_slot * kStatCount + kStatExecuted], a_exe);
-        if (a_64) atomicAdd(&stats[cur_slot * kStatCount + kStatFp64Boosts], a_64);
-    }
+    flush_resolve_stats(cur_slot, a_acc, a_exe, stats);
 }
 
 // Kinematics of pairs (2k, 2k+1) of cell 0 in the FP32 path with a given FP64
