@@ -93,7 +93,7 @@ struct PairShape {
     static constexpr int min_blocks = kOneKey ? 1 : 2;  // resident blocks per SM the register budget targets
 };
 constexpr int kSmallBlocksPerIter = 2; // the same for the warp-per-small-cell kernel (short rows)
-// Queued Philox blocks per warp for nb blocks per iteration (32 spare slots follow).
+// Queued Philox blocks per warp for nb blocks per iteration.
 __host__ __device__ constexpr int queue_cap(int nb) { return 32 + 32 * nb; }
 
 // Resolve: per-cell accepted lists up to this size are sorted in shared memory.

@@ -116,6 +116,21 @@ struct CellCtx {
     uint32_t slot;    // its counters row
 };
 
+// Store a queue entry (block r, row and group ig) iff p, without a branch.
+__device__ __forceinline__ void st_shared_if(bool p, uint4* w, uint4 r, uint2 ig, uint2* wig)
+{
+    const uint32_t aw = (uint32_t)__cvta_generic_to_shared(w);
+    const uint32_t ai = (uint32_t)__cvta_generic_to_shared(wig);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.u32 q, %0, 0;\n\t"
+        "@q st.shared.v4.u32 [%1], {%2, %3, %4, %5};\n\t"
+        "@q st.shared.v2.u32 [%6], {%7, %8};\n\t}"
+        :
+        : "r"((uint32_t)p), "r"(aw), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(ai), "r"(ig.x), "r"(ig.y)
+        : "memory");
+}
+
 // Append accepted pair (i, j) to its cell's list; kMark: the cell's first
 // accepted pair enters it in the active-cell list.
 template <bool kMark>
@@ -223,12 +238,12 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
             __syncwarp();
             qn -= 32;
         }
-        // branch-free push: lanes without a hit write their own spare slot
+        // branch-free push: predicated shared-memory stores of the lanes
+        // with a candidate block
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const uint32_t slot = h[q] ? qn + (uint32_t)__popc(bal[q] & lt) : (uint32_t)kQueueCap + lane;
-            qw[slot] = r[q];
-            qig[slot] = make_uint2(i, g + q);
+            const uint32_t slot = qn + (uint32_t)__popc(bal[q] & lt);
+            st_shared_if(h[q], &qw[slot], r[q], make_uint2(i, g + q), &qig[slot]);
             qn += (uint32_t)__popc(bal[q]);
         }
     }
@@ -392,8 +407,8 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey>::min_blocks)
 {
     constexpr int kWarps = kPairThreads / 32;
     constexpr int NB = PairShape<kOneKey>::nb;
-    __shared__ uint4 q_w[kWarps][queue_cap(NB) + 32];
-    __shared__ uint2 q_ig[kWarps][queue_cap(NB) + 32];
+    __shared__ uint4 q_w[kWarps][queue_cap(NB)];
+    __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t total = work[ncells].x;
@@ -462,8 +477,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
 {
     constexpr int kWarps = kPairThreads / 32;
     constexpr int NB = kSmallBlocksPerIter;
-    __shared__ uint4 q_w[kWarps][queue_cap(NB) + 32];
-    __shared__ uint2 q_ig[kWarps][queue_cap(NB) + 32];
+    __shared__ uint4 q_w[kWarps][queue_cap(NB)];
+    __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
     const int w = threadIdx.x >> 5;
     if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
     const uint32_t lane = threadIdx.x & 31;
