@@ -51,6 +51,7 @@ typedef struct {
     int32_t fp32;     /* 1: single-precision mirror of stream, key and P22 */
     uint32_t key[2];  /* Philox key (seed low word, seed high word) */
     int32_t skip;     /* 0: every pair tested (Eq. 3); 1: skip-ahead candidates + thinning */
+    double kappa;     /* > 0: adaptive time step, dt is its upper bound (see orc_adaptive_dt) */
 } orc_params;
 
 typedef struct {
@@ -69,6 +70,7 @@ typedef struct {
     int64_t n_reflections;
     int64_t n_pairs_tested;
     int64_t n_candidates;  /* skip-ahead: candidate pairs drawn (P22 evaluated) */
+    double dt;             /* the step's time step */
 } orc_trace;
 
 /* ------------------------------------------------------------------------ */
@@ -140,6 +142,7 @@ static int check_params(const orc_params *p)
     }
     if (!(p->dt > 0.0) || !(p->sigma >= 0.0) || !(p->n_test > 0.0)) return ORC_ERR_INVALID;
     if (p->skip != 0 && p->skip != 1) return ORC_ERR_INVALID;
+    if (!(p->kappa >= 0.0) || p->kappa > 0.5) return ORC_ERR_INVALID;
     return ORC_OK;
 }
 
@@ -856,6 +859,45 @@ int64_t orc_row_accept(const orc_params *p, uint32_t step, uint32_t cell, int64_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Adaptive time step                                                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper leaves a variable dt to future work (Sec. 6).  Reading: with
+ * kappa > 0 each step's dt is taken at its start from the sorted state so that
+ * a particle of the most populated cell (n_max particles) expects about kappa
+ * collisions in the step: (n_max - 1) C <v_rel> = kappa with <v_rel> = 1 for
+ * an isotropic massless gas and C = sigma dt / (N_test V_cell) (Eq. 3), i.e.
+ *   dt = ((kappa N_test) V_cell) / (sigma (n_max - 1)),
+ * capped by the given dt (below every cell edge, Sec. 5).  Without
+ * collisions (sigma = 0, or n_max < 2) the cap is used.  kappa <= 1/2 keeps
+ * 2 C <= 1.
+ */
+double orc_adaptive_dt(const orc_params *p, int64_t n_max)
+{
+    if (!(p->kappa > 0.0) || !(p->sigma > 0.0) || n_max < 2) return p->dt;
+    double dt = ((p->kappa * p->n_test) * cell_volume(p)) / (p->sigma * (double)(n_max - 1));
+    return dt < p->dt ? dt : p->dt;
+}
+
+/* Largest cell population of a state (keys in the state's precision). */
+static int64_t max_cell_count(const orc_params *p, int64_t n, const double *st)
+{
+    int64_t ncell = orc_ncells(p);
+    int64_t *cnt = (int64_t *)calloc((size_t)ncell, sizeof(int64_t));
+    if (!cnt) return -1;
+    for (int64_t k = 0; k < n; ++k) {
+        uint32_t key = p->fp32 ? key_f(p, (float)st[k], (float)st[n + k], (float)st[2 * n + k])
+                               : key_d(p, st[k], st[n + k], st[2 * n + k]);
+        cnt[key] += 1;
+    }
+    int64_t m = 0;
+    for (int64_t c = 0; c < ncell; ++c) m = cnt[c] > m ? cnt[c] : m;
+    free(cnt);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One full time step                                                        */
 /* ------------------------------------------------------------------------ */
 
@@ -865,9 +907,18 @@ int64_t orc_row_accept(const orc_params *p, uint32_t step, uint32_t cell, int64_
  * every particle, A4 stable sort, A5-A7 collisions cell by cell.  Positions
  * are not changed by collisions.  The optional trace receives the details.
  */
-int orc_step(const orc_params *p, uint32_t step, int64_t n, double *st, orc_trace *tr)
+int orc_step(const orc_params *p_in, uint32_t step, int64_t n, double *st, orc_trace *tr)
 {
-    if (check_params(p) != ORC_OK) return ORC_ERR_INVALID;
+    if (check_params(p_in) != ORC_OK) return ORC_ERR_INVALID;
+    /* the step's dt: the given one, or the adaptive choice from the state */
+    orc_params q = *p_in;
+    if (q.kappa > 0.0) {
+        int64_t nmax = max_cell_count(p_in, n, st);
+        if (nmax < 0) return ORC_ERR_OOM;
+        q.dt = orc_adaptive_dt(p_in, nmax);
+    }
+    const orc_params *p = &q;
+    if (tr) tr->dt = q.dt;
     int64_t ncell = orc_ncells(p);
     uint32_t *keys = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     int64_t *cs = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncell + 1));

@@ -28,6 +28,7 @@ class Params(C.Structure):
         ("fp32", C.c_int32),
         ("key", C.c_uint32 * 2),
         ("skip", C.c_int32),
+        ("kappa", C.c_double),
     ]
 
 
@@ -49,6 +50,7 @@ class Trace(C.Structure):
         ("n_reflections", C.c_int64),
         ("n_pairs_tested", C.c_int64),
         ("n_candidates", C.c_int64),
+        ("dt", C.c_double),
     ]
 
 
@@ -101,6 +103,8 @@ def lib():
         L.orc_skip_table.restype = C.c_int
         L.orc_skip_gap.argtypes = [u64p, C.c_uint64, C.c_uint64]
         L.orc_skip_gap.restype = C.c_uint64
+        L.orc_adaptive_dt.argtypes = [C.POINTER(Params), C.c_int64]
+        L.orc_adaptive_dt.restype = C.c_double
         L.orc_threads.argtypes = []
         L.orc_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
@@ -114,7 +118,7 @@ def _ptr(a, ct):
 
 
 def make_params(L=(10.0, 1.0, 1.0), n=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_test=1.0,
-                fp32=False, seed=0, skip=False):
+                fp32=False, seed=0, skip=False, kappa=0.0):
     p = Params()
     for a in range(3):
         p.L[a] = float(L[a])
@@ -126,6 +130,7 @@ def make_params(L=(10.0, 1.0, 1.0), n=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_tes
     p.key[0] = int(seed) & 0xFFFFFFFF
     p.key[1] = (int(seed) >> 32) & 0xFFFFFFFF
     p.skip = 1 if skip else 0
+    p.kappa = float(kappa)
     return p
 
 
@@ -230,6 +235,11 @@ def kinematics(key, step, cell, i, j, pi, pj):
     return bool(ok), a, b
 
 
+def adaptive_dt(p, n_max):
+    """The time step the adaptive rule takes for a largest cell population n_max."""
+    return float(lib().orc_adaptive_dt(C.byref(p), int(n_max)))
+
+
 def skip_table(C_scale):
     """(P_fix, Q[0..32]) of the skip-ahead mode for the P22 scale C."""
     Q = np.zeros(33, dtype=np.uint64)
@@ -331,6 +341,7 @@ def step(p, step_index, st, trace=True):
     res.n_reflections = tr.n_reflections
     res.n_pairs_tested = tr.n_pairs_tested
     res.n_candidates = tr.n_candidates
+    res.dt = tr.dt
     if trace:
         res.accepted = res._acc[:3 * tr.n_acc].reshape(-1, 3).copy()
         res.executed = res._exe[:3 * tr.n_exe].reshape(-1, 3).copy()
