@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--acceptance", default="all-pairs", choices=["all-pairs", "skip"],
                     help="pair test of the paper (every pair draws its uniform) or skip-ahead sampling")
+    ap.add_argument("--kappa", type=float, default=0.0,
+                    help="> 0: adaptive time step (kappa collisions per particle of the fullest cell per "
+                         "step, dt as its cap)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -199,7 +202,7 @@ def bin_passes(ncells):
     return max(1, (bits + 10) // 11)
 
 
-def launches_per_step(ncells, small_max, skip=False):
+def launches_per_step(ncells, small_max, skip=False, adaptive=False):
     """Kernels of one step: streaming histogram; per radix pass the digit
     histogram (passes after the first), 3 scan kernels and the ranking
     kernel, then (two passes or more) the gather; cell preparation + 3 scan
@@ -210,7 +213,7 @@ def launches_per_step(ncells, small_max, skip=False):
     sort = 1 + 4 * p + (p - 1) + (1 if p > 1 else 0)
     small = 1 if small_max else 0
     pairs = 3 + 1 if skip else 1 + small
-    return sort + 4 + pairs + (1 + small) + 1
+    return (1 if adaptive else 0) + sort + 4 + pairs + (1 + small) + 1
 
 
 def peaks():
@@ -486,7 +489,8 @@ def main():
     prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
     p = cuba.make_params(L=cfg["L"], n_cells=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
                          n_test=cfg["n_test"], precision=prec, seed=replica_seed(args.seed, rank),
-                         acceptance=cuba.CUBA_ACCEPT_SKIP if args.acceptance == "skip" else cuba.CUBA_ACCEPT_ALL_PAIRS)
+                         acceptance=cuba.CUBA_ACCEPT_SKIP if args.acceptance == "skip" else cuba.CUBA_ACCEPT_ALL_PAIRS,
+                         kappa=args.kappa)
     sim = cuba.Sim(p, args.n)
     stream = torch.cuda.Stream()
     if args.workload == "hotspot3d":
@@ -503,6 +507,7 @@ def main():
     else:
         tune_ms = None
 
+    t_sim0 = cuba.cuba_get_time(sim.h)[0]
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
@@ -517,6 +522,7 @@ def main():
     barrier(world)
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    sim_fm_per_step = (cuba.cuba_get_time(sim.h)[0] - t_sim0) / args.steps
     ms_max = max_over_ranks(ms, world)
     value = replica_rate(args.n * args.steps, world, ms_max / 1000.0)
 
@@ -604,13 +610,15 @@ def main():
             "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "n_particles": args.n, "n_cells": args.cells, "dt": args.dt,
                        "sigma_mb": args.sigma_mb, "precision": args.precision, "n_test": cfg["n_test"],
-                       "acceptance": args.acceptance,
+                       "acceptance": args.acceptance, "kappa": args.kappa,
+                       "simulated_fm_per_step": sim_fm_per_step,
                        "l2": "state %.0f MB > L2, no flush" % (args.n * 24 / 1e6 * (2 if prec else 1)),
                        "parallelism": "replicas" if world > 1 else "single",
                        "small_max": cuba.cuba_get_small_max(sim.h), "autotune_ms": tune_ms},
             "clocks": clk,
             "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2],
-                                              cuba.cuba_get_small_max(sim.h), args.acceptance == "skip") * args.steps,
+                                              cuba.cuba_get_small_max(sim.h), args.acceptance == "skip",
+                                              args.kappa > 0) * args.steps,
             "roofline": roofline,
             "hbm_phases": hbm,
             "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in zip(phase_names, phase)},

@@ -85,6 +85,15 @@ typedef struct cuba_params {
                              Each pair is accepted with probability P22
                              independently in both modes; the realisations
                              differ. */
+    double kappa;         /* > 0: adaptive time step (no counterpart in the
+                             paper, which names a variable dt as future work,
+                             Sec. 6): each step takes
+                             dt = ((kappa N_test) V_cell) / (sigma (n_max - 1))
+                             with n_max the most populated cell at the start
+                             of the step, so that its particles expect kappa
+                             collisions; capped by dt (the field above), which
+                             is used as is without collisions.  0: fixed dt.
+                             At most 1/2 (keeps 2 C <= 1). */
 } cuba_params;
 
 #define CUBA_ACCEPT_ALL_PAIRS 0
@@ -169,6 +178,11 @@ int cuba_sizes(const cuba_sim* sim, int64_t* n_particles, int64_t* n_cells);
    numbers).  set_step lets a resumed run continue its random sequence. */
 int cuba_get_step(const cuba_sim* sim, uint32_t* step);
 int cuba_set_step(cuba_sim* sim, uint32_t step);
+
+/* Simulated time (FP64 sum of the steps' dt since the last init or
+   set_state, fm/c) and the dt of the last step taken (the fixed dt before the
+   first one).  Synchronous.  Either pointer may be NULL. */
+int cuba_get_time(const cuba_sim* sim, double* time, double* last_dt);
 
 /*
  * Advance n_steps time steps A1-A7.  Async on `stream`: the work is replayed
@@ -313,6 +327,7 @@ int cuba_batch_totals(cuba_batch* b, int32_t id, double out[4], int64_t* n_parti
 int cuba_batch_stats(cuba_batch* b, int32_t id, cuba_counters* out);
 int cuba_batch_get_state(cuba_batch* b, int32_t id, void* soa_out, void* stream);
 int cuba_batch_get_step(cuba_batch* b, int32_t id, uint32_t* step);
+int cuba_batch_get_time(cuba_batch* b, int32_t id, double* time, double* last_dt);
 
 /* Autotuner and launch shape of a batch, as cuba_autotune / cuba_set_small_max
    (all resident members are timed together; none advances). */

@@ -65,37 +65,26 @@ int make_desc(const cuba_params* p, SimDesc* S)
     if (!(p->n_test > 0.0) || !std::isfinite(p->n_test)) return fail(CUBA_ERR_INVALID, "n_test must be > 0");
     if (p->precision != CUBA_FP32 && p->precision != CUBA_FP64) return fail(CUBA_ERR_INVALID, "bad precision");
     S->ncells = (uint32_t)nc;
-    S->dt = p->dt;
-    S->dtf = (float)p->dt;
-    const double V = (S->dx[0] * S->dx[1]) * S->dx[2];
-    S->C = (p->sigma_fm2 * p->dt) / (p->n_test * V);
-    S->Cf = (float)S->C;
-    S->norm = p->n_test * V;
-    if (2.0 * S->C > 1.0) return fail(CUBA_ERR_P22, "P22 can reach 2C = %g > 1", 2.0 * S->C);
-    S->key0 = (uint32_t)p->seed;
-    S->key1 = (uint32_t)(p->seed >> 32);
-    // A top byte above thr8 proves u >= (thr8 + 1) / 256 > 2.0001 C >= P22.
-    const double pb = 2.0001 * S->C;
-    S->thr8 = (pb >= 0.5) ? 256u : (uint32_t)std::floor(pb * 256.0);
-    S->thr16 = (pb >= 1.0) ? 65536u : (uint32_t)std::floor(pb * 65536.0);
-    S->gamma_fp64 = (float)(p->gamma_fp64 > 0.0 ? p->gamma_fp64 : kDefaultGammaFp64);
-    S->step = 0;
     if (p->acceptance != CUBA_ACCEPT_ALL_PAIRS && p->acceptance != CUBA_ACCEPT_SKIP)
         return fail(CUBA_ERR_INVALID, "acceptance must be CUBA_ACCEPT_ALL_PAIRS or CUBA_ACCEPT_SKIP");
+    if (!(p->kappa >= 0.0) || p->kappa > 0.5) return fail(CUBA_ERR_INVALID, "kappa must lie in [0, 1/2]");
     S->skip = p->acceptance == CUBA_ACCEPT_SKIP ? 1u : 0u;
-    if (S->skip && S->C > 0.0) {
-        // P_fix = floor(2.0001 C 2^64) >= 1; q = 1 - P_max; Q[b] = q^(2^b) by
-        // truncated 0.64 fixed-point squaring
-        if (!(pb < 1.0)) return fail(CUBA_ERR_P22, "skip-ahead needs 2.0001 C < 1 (C = %g)", S->C);
-        uint64_t P = (uint64_t)std::ldexp(pb, 64);
-        if (P == 0) P = 1;
-        S->pfix = P;
-        S->pmax = (double)P * 0x1p-64;
-        S->pmaxf = (float)S->pmax;
-        S->skipQ[0] = (uint64_t)0 - P;
-        for (int b = 1; b <= 32; ++b)
-            S->skipQ[b] = (uint64_t)(((unsigned __int128)S->skipQ[b - 1] * S->skipQ[b - 1]) >> 64);
-    }
+    S->V = (S->dx[0] * S->dx[1]) * S->dx[2];
+    S->sigma = p->sigma_fm2;
+    S->n_test = p->n_test;
+    S->kappa = p->kappa;
+    S->dt_max = p->dt;
+    S->dt = p->dt;
+    S->time = 0.0;
+    S->norm = p->n_test * S->V;
+    derive_step_constants(*S);
+    if (2.0 * S->C > 1.0) return fail(CUBA_ERR_P22, "P22 can reach 2C = %g > 1", 2.0 * S->C);
+    if (S->skip && S->C > 0.0 && !(2.0001 * S->C < 1.0))
+        return fail(CUBA_ERR_P22, "skip-ahead needs 2.0001 C < 1 (C = %g)", S->C);
+    S->key0 = (uint32_t)p->seed;
+    S->key1 = (uint32_t)(p->seed >> 32);
+    S->gamma_fp64 = (float)(p->gamma_fp64 > 0.0 ? p->gamma_fp64 : kDefaultGammaFp64);
+    S->step = 0;
     return CUBA_OK;
 }
 
@@ -162,6 +151,7 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
 // capture).
 int enqueue_step(Arena& A, cudaStream_t st)
 {
+    if (A.any_adapt && launch_adapt_dt(A, st)) return fail(CUBA_ERR_CUDA, "adaptive dt launch failed");
     if (launch_step_bin(A, st, nullptr)) return fail(CUBA_ERR_CUDA, "stream/sort launch failed");
     if (launch_cell_prep(A, st)) return fail(CUBA_ERR_CUDA, "cell preparation launch failed");
     if (launch_pair_tile(A, st)) return fail(CUBA_ERR_CUDA, "pair tile launch failed");
@@ -300,7 +290,7 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
 {
     if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells ||
         small_max != A.small_max || one_key != A.one_key || key0 != A.key_sched.k0[0] || key1 != A.key_sched.k1[0] ||
-        modes != A.any_skip * 2 + A.any_all_pairs)
+        modes != A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs)
         drop();
     for (int k = 0; k < n; ++k) {
         const int which = A.cur;
@@ -330,7 +320,7 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
             one_key = A.one_key;
             key0 = A.key_sched.k0[0];
             key1 = A.key_sched.k1[0];
-            modes = A.any_skip * 2 + A.any_all_pairs;
+            modes = A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs;
         }
         CUDA_TRY(cudaGraphLaunch(g[which], st), "graph launch");
         A.cur ^= 1;
@@ -344,8 +334,10 @@ void set_key_param(Arena& A, const SimDesc* table, int n)
     A.key_sched = n == 1 ? philox_schedule(table[0].key0, table[0].key1) : PhiloxKey{};
     A.any_skip = 0;
     A.any_all_pairs = 0;
+    A.any_adapt = 0;
     for (int k = 0; k < n; ++k) {
         if (table[k].skip) A.any_skip = 1; else A.any_all_pairs = 1;
+        if (table[k].kappa > 0.0) A.any_adapt = 1;
     }
 }
 
@@ -633,6 +625,17 @@ int cuba_set_step(cuba_sim* s, uint32_t step)
     return CUBA_OK;
 }
 
+int cuba_get_time(const cuba_sim* s, double* time, double* last_dt)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    double v[2];
+    CUDA_TRY(cudaMemcpy(&v[0], &s->A.d_sims[0].time, sizeof(double), cudaMemcpyDeviceToHost), "read time");
+    CUDA_TRY(cudaMemcpy(&v[1], &s->A.d_sims[0].dt, sizeof(double), cudaMemcpyDeviceToHost), "read dt");
+    if (time) *time = v[0];
+    if (last_dt) *last_dt = v[1];
+    return CUBA_OK;
+}
+
 int cuba_step(cuba_sim* s, int n_steps, void* stream)
 {
     if (!s || n_steps < 0) return fail(CUBA_ERR_INVALID, "bad arguments");
@@ -650,7 +653,8 @@ int cuba_step_profiled(cuba_sim* s, int n_steps, double* phase_ms, void* stream)
     int rc = CUBA_OK;
     for (int it = 0; it < n_steps && !rc; ++it) {
         cudaEventRecord(ev[0], st);
-        if (launch_step_bin(A, st, ev[1])) rc = fail(CUBA_ERR_CUDA, "stream/sort launch failed");
+        if (A.any_adapt && launch_adapt_dt(A, st)) rc = fail(CUBA_ERR_CUDA, "adaptive dt launch failed");
+        if (!rc && launch_step_bin(A, st, ev[1])) rc = fail(CUBA_ERR_CUDA, "stream/sort launch failed");
         cudaEventRecord(ev[2], st);
         if (!rc && launch_cell_prep(A, st)) rc = fail(CUBA_ERR_CUDA, "cell preparation launch failed");
         cudaEventRecord(ev[3], st);

@@ -49,7 +49,8 @@ int find_member(const cuba_batch* b, int32_t id)
     return -1;
 }
 
-// Refresh the host copies of the descriptors (step counters) from the device.
+// Refresh the host copies of the descriptors from the device (step counters,
+// simulated time, the adaptive step's constants).
 int pull_table(cuba_batch* b)
 {
     const size_t n = b->members.size();
@@ -57,7 +58,9 @@ int pull_table(cuba_batch* b)
     std::vector<SimDesc> t(n);
     CUDA_TRY(cudaDeviceSynchronize(), "sync");
     CUDA_TRY(cudaMemcpy(t.data(), b->A.d_sims, n * sizeof(SimDesc), cudaMemcpyDeviceToHost), "read table");
-    for (size_t k = 0; k < n; ++k) b->members[k].desc.step = t[k].step;
+    // the device advances the step counter, the simulated time and (adaptive
+    // dt) the step's constants; the layout fields agree with the host's
+    for (size_t k = 0; k < n; ++k) b->members[k].desc = t[k];
     return CUBA_OK;
 }
 
@@ -346,6 +349,18 @@ int cuba_batch_get_step(cuba_batch* b, int32_t id, uint32_t* step)
     int rc = pull_table(b);
     if (rc) return rc;
     *step = b->members[k].desc.step;
+    return CUBA_OK;
+}
+
+int cuba_batch_get_time(cuba_batch* b, int32_t id, double* time, double* last_dt)
+{
+    if (!b) return fail(CUBA_ERR_INVALID, "bad arguments");
+    const int k = find_member(b, id);
+    if (k < 0) return fail(CUBA_ERR_INVALID, "no member with id %d", id);
+    int rc = pull_table(b);
+    if (rc) return rc;
+    if (time) *time = b->members[k].desc.time;
+    if (last_dt) *last_dt = b->members[k].desc.dt;
     return CUBA_OK;
 }
 

@@ -6,6 +6,7 @@
 // the whole arena by global key keeps every simulation inside its own range.
 // A single simulation is an arena with one entry.
 #pragma once
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -43,7 +44,46 @@ struct SimDesc {
     uint64_t pfix;
     double pmax;
     uint64_t skipQ[33];
+    // adaptive time step (kappa > 0): dt_max caps it; sigma, n_test and V
+    // enter the rule; time is the sum of the steps taken
+    double kappa;
+    double dt_max;
+    double sigma, n_test, V;
+    double time;
 };
+
+// C, its FP32 copy, the byte thresholds and the skip-ahead tables of a
+// descriptor from its dt (host and device: the same IEEE operations).
+__host__ __device__ inline void derive_step_constants(SimDesc& S)
+{
+    S.dtf = (float)S.dt;
+    S.C = (S.sigma * S.dt) / (S.n_test * S.V);
+    S.Cf = (float)S.C;
+    // a top byte above thr8 proves u >= (thr8 + 1) / 256 > 2.0001 C >= P22
+    const double pb = 2.0001 * S.C;
+    S.thr8 = (pb >= 0.5) ? 256u : (uint32_t)floor(pb * 256.0);
+    S.thr16 = (pb >= 1.0) ? 65536u : (uint32_t)floor(pb * 65536.0);
+    S.pfix = 0;
+    S.pmax = 0.0;
+    S.pmaxf = 0.f;
+    if (S.skip && S.C > 0.0 && pb < 1.0) {
+        // P_fix = floor(2.0001 C 2^64) >= 1; q = 1 - P_max; Q[b] = q^(2^b)
+        // by truncated 0.64 fixed-point squaring
+        uint64_t P = (uint64_t)(pb * 18446744073709551616.0);
+        if (P == 0) P = 1;
+        S.pfix = P;
+        S.pmax = (double)P * 0x1p-64;
+        S.pmaxf = (float)S.pmax;
+        S.skipQ[0] = (uint64_t)0 - P;
+        for (int b = 1; b <= 32; ++b) {
+#ifdef __CUDA_ARCH__
+            S.skipQ[b] = __umul64hi(S.skipQ[b - 1], S.skipQ[b - 1]);
+#else
+            S.skipQ[b] = (uint64_t)(((unsigned __int128)S.skipQ[b - 1] * S.skipQ[b - 1]) >> 64);
+#endif
+        }
+    }
+}
 
 // Per-simulation counters (unsigned long long for atomics).
 enum StatIdx {
@@ -162,8 +202,8 @@ struct Arena {
     // parameter (set whenever the descriptor table is uploaded)
     int one_key = 0;
     PhiloxKey key_sched = {};
-    // which acceptance modes the resident simulations use
-    int any_all_pairs = 1, any_skip = 0;
+    // which acceptance modes the resident simulations use; any adaptive dt
+    int any_all_pairs = 1, any_skip = 0, any_adapt = 0;
 };
 
 // ---- launchers (kernels_sort.cu) ----
@@ -187,6 +227,7 @@ int launch_cell_prep(const Arena& A, cudaStream_t st, int count_pairs = 1);
 int launch_observables(const Arena& A, int sim, double* T00, double* T0x, int32_t* counts, cudaStream_t st);
 int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st);
 int launch_advance(const Arena& A, cudaStream_t st);
+int launch_adapt_dt(const Arena& A, cudaStream_t st);   // adaptive dt of the coming step
 int launch_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, cudaStream_t st);
 int launch_bin_raw(const SimDesc& S, int precision, const void* xyz, uint32_t n, uint32_t* key_a, uint32_t* key_b,
                    uint32_t* idx_a, uint32_t* idx_b, uint32_t* hist, void* partials, size_t partial_bytes,

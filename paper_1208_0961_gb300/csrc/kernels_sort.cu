@@ -510,7 +510,37 @@ __global__ void k_advance(SimDesc* sims, int nsims, unsigned long long* stats)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < nsims) {
         sims[s].step += 1;
+        sims[s].time += sims[s].dt;
         stats[sims[s].stat_slot * kStatCount + kStatSteps] += 1;
+    }
+}
+
+// Adaptive time step of the coming step (one block per simulation): the most
+// populated cell n_max of the sorted state, dt = ((kappa N_test) V_cell) /
+// (sigma (n_max - 1)) capped by dt_max (the cap without collisions), and the
+// constants that follow from dt.
+__global__ void __launch_bounds__(256) k_adapt_dt(SimDesc* __restrict__ sims, const uint32_t* __restrict__ cell_start)
+{
+    __shared__ uint32_t red[8];
+    SimDesc& S = sims[blockIdx.x];
+    if (!(S.kappa > 0.0)) return;
+    uint32_t m = 0;
+    for (uint32_t c = threadIdx.x; c < S.ncells; c += blockDim.x) {
+        const uint32_t g = S.cell_off + c;
+        m = max(m, cell_start[g + 1] - cell_start[g]);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+        double dt = S.dt_max;
+        if (S.sigma > 0.0 && m >= 2) {
+            const double a = __ddiv_rn(__dmul_rn(__dmul_rn(S.kappa, S.n_test), S.V), __dmul_rn(S.sigma, (double)(m - 1)));
+            dt = a < S.dt_max ? a : S.dt_max;
+        }
+        S.dt = dt;
+        derive_step_constants(S);
     }
 }
 
@@ -707,6 +737,13 @@ int launch_totals(const Arena& A, int sim, double* d_out4, cudaStream_t st)
     else
         k_totals_partial<float><<<nb, 256, 0, st>>>(S, (const float*)A.st[A.cur], A.pcap, part);
     k_totals_final<<<1, 32, 0, st>>>(part, nb, d_out4);
+    return last_err();
+}
+
+int launch_adapt_dt(const Arena& A, cudaStream_t st)
+{
+    if (A.nsims == 0) return 0;
+    k_adapt_dt<<<A.nsims, 256, 0, st>>>(A.d_sims, A.cell_start);
     return last_err();
 }
 

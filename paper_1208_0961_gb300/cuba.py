@@ -38,6 +38,7 @@ class cuba_params(C.Structure):
         ("seed", C.c_uint64),
         ("gamma_fp64", C.c_double),
         ("acceptance", C.c_int32),
+        ("kappa", C.c_double),
     ]
 
 
@@ -94,6 +95,7 @@ def load(build_if_missing=True):
         "cuba_sizes": (C.c_int, [vp, i64p, i64p]),
         "cuba_get_step": (C.c_int, [vp, u32p]),
         "cuba_set_step": (C.c_int, [vp, C.c_uint32]),
+        "cuba_get_time": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "cuba_step": (C.c_int, [vp, C.c_int, vp]),
         "cuba_observables": (C.c_int, [vp, vp, vp, vp, vp]),
         "cuba_totals": (C.c_int, [vp, C.POINTER(C.c_double), i64p, vp]),
@@ -116,6 +118,7 @@ def load(build_if_missing=True):
         "cuba_batch_stats": (C.c_int, [vp, C.c_int32, C.POINTER(cuba_counters)]),
         "cuba_batch_get_state": (C.c_int, [vp, C.c_int32, vp, vp]),
         "cuba_batch_get_step": (C.c_int, [vp, C.c_int32, u32p]),
+        "cuba_batch_get_time": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "cuba_batch_usage": (C.c_int, [vp, C.POINTER(C.c_int32), i64p, i64p]),
         "cuba_batch_bytes": (C.c_int64, [C.POINTER(cuba_batch_config)]),
         "cuba_kinematics_fp32": (C.c_int, [vp, C.c_int64, C.c_uint64, C.c_uint32, C.c_double, vp, vp, vp]),
@@ -160,7 +163,7 @@ def _ptr(x):
 
 
 def make_params(L=(10.0, 1.0, 1.0), n_cells=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_test=1.0,
-                precision=CUBA_FP64, seed=0, gamma_fp64=0.0, acceptance=0):
+                precision=CUBA_FP64, seed=0, gamma_fp64=0.0, acceptance=0, kappa=0.0):
     p = cuba_params()
     for a in range(3):
         p.L[a] = float(L[a])
@@ -172,6 +175,7 @@ def make_params(L=(10.0, 1.0, 1.0), n_cells=(100, 1, 1), dt=0.05, sigma_fm2=1.0,
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.gamma_fp64 = float(gamma_fp64)
     p.acceptance = int(acceptance)
+    p.kappa = float(kappa)
     return p
 
 
@@ -230,6 +234,14 @@ def cuba_get_step(sim):
     s = C.c_uint32()
     _check(load().cuba_get_step(sim, C.byref(s)))
     return s.value
+
+
+def cuba_get_time(sim):
+    """(simulated time, dt of the last step)."""
+    t = C.c_double()
+    dt = C.c_double()
+    _check(load().cuba_get_time(sim, C.byref(t), C.byref(dt)))
+    return t.value, dt.value
 
 
 def cuba_set_step(sim, step):
@@ -386,6 +398,13 @@ def cuba_batch_get_state(b, sim_id, out, stream=None):
     _check(load().cuba_batch_get_state(b, int(sim_id), _ptr(out), _stream_ptr(stream)))
 
 
+def cuba_batch_get_time(b, sim_id):
+    t = C.c_double()
+    dt = C.c_double()
+    _check(load().cuba_batch_get_time(b, int(sim_id), C.byref(t), C.byref(dt)))
+    return t.value, dt.value
+
+
 def cuba_batch_get_step(b, sim_id):
     s = C.c_uint32()
     _check(load().cuba_batch_get_step(b, int(sim_id), C.byref(s)))
@@ -472,6 +491,9 @@ class Batch:
     def get_step(self, sim_id):
         return cuba_batch_get_step(self.h, sim_id)
 
+    def get_time(self, sim_id):
+        return cuba_batch_get_time(self.h, sim_id)
+
     def usage(self):
         return cuba_batch_usage(self.h)
 
@@ -536,6 +558,9 @@ class Sim:
 
     def step(self, n_steps=1, stream=None):
         cuba_step(self.h, n_steps, stream)
+
+    def time(self):
+        return cuba_get_time(self.h)
 
     def observables(self, stream=None):
         import numpy as np

@@ -22,17 +22,18 @@ from paper_1208_0961_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0, skip=False):
+def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0, skip=False, kappa=0.0):
     p = cuba.make_params(L=L, n_cells=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test,
                          precision=cuba.CUBA_FP32 if fp32 else cuba.CUBA_FP64, seed=seed, gamma_fp64=gamma_fp64,
-                         acceptance=cuba.CUBA_ACCEPT_SKIP if skip else cuba.CUBA_ACCEPT_ALL_PAIRS)
-    op = O.make_params(L=L, n=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test, fp32=fp32, seed=seed, skip=skip)
+                         acceptance=cuba.CUBA_ACCEPT_SKIP if skip else cuba.CUBA_ACCEPT_ALL_PAIRS, kappa=kappa)
+    op = O.make_params(L=L, n=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test, fp32=fp32, seed=seed, skip=skip,
+                       kappa=kappa)
     return p, op
 
 
 def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_index=3, small_max=None,
-                      skip=False):
-    p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, skip=skip)
+                      skip=False, kappa=0.0):
+    p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, skip=skip, kappa=kappa)
     dtype = np.float32 if fp32 else np.float64
     st0 = st0.astype(dtype)
     n = st0.shape[1]
@@ -48,6 +49,7 @@ def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_i
         g_out = sim.get_state()
         keys, perm, cs, pairs, exe = sim.trace()
         stats = sim.stats()
+        t_gpu, dt_gpu = sim.time()
         assert cuba.cuba_get_step(sim.h) == step_index + 1
     finally:
         sim.close()
@@ -55,6 +57,7 @@ def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_i
     o_in, _, _, _ = O.sort(op, st0.astype(np.float64))
     assert np.array_equal(g_in.astype(np.float64), o_in), "set_state sort differs"
     o_out, res = O.step(op, step_index, o_in)
+    assert dt_gpu == res.dt and t_gpu == res.dt, "time step differs"
     assert np.array_equal(keys, res.keys.astype(np.uint32)), "keys differ"
     assert np.array_equal(perm.astype(np.int64), res.perm), "permutation differs"
     assert np.array_equal(cs.astype(np.int64), res.cell_start), "cell_start differs"
