@@ -503,7 +503,7 @@ def main():
     torch.cuda.synchronize()
     tuned = None
     if args.autotune:
-        tuned, tune_ms = cuba.cuba_autotune(sim.h, 2, stream)
+        tuned, tune_ms = cuba.cuba_autotune_shape(sim.h, 2, stream)
     else:
         tune_ms = None
 
@@ -614,7 +614,7 @@ def main():
                        "simulated_fm_per_step": sim_fm_per_step,
                        "l2": "state %.0f MB > L2, no flush" % (args.n * 24 / 1e6 * (2 if prec else 1)),
                        "parallelism": "replicas" if world > 1 else "single",
-                       "small_max": cuba.cuba_get_small_max(sim.h), "autotune_ms": tune_ms},
+                       "launch_shape": cuba.cuba_get_launch_shape(sim.h), "autotune_ms": tune_ms},
             "clocks": clk,
             "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2],
                                               cuba.cuba_get_small_max(sim.h), args.acceptance == "skip",

@@ -226,6 +226,34 @@ int cuba_get_small_max(const cuba_sim* sim, int32_t* small_max);
  */
 int cuba_autotune(cuba_sim* sim, int n_steps, int32_t* chosen, double* ms_per_candidate, void* stream);
 
+/*
+ * The whole launch shape of the collision step: small_max as above, and the
+ * Philox blocks a lane draws per loop iteration in the warp-per-cell pair
+ * kernel (small_blocks: 1 or 2, default 2) and in the 32-row item kernel
+ * (tile_blocks: 2 or 4, default 4).  Results do not depend on it.
+ */
+typedef struct cuba_launch_shape {
+    int32_t small_max;
+    int32_t small_blocks;
+    int32_t tile_blocks;
+} cuba_launch_shape;
+
+int cuba_set_launch_shape(cuba_sim* sim, const cuba_launch_shape* shape);
+int cuba_get_launch_shape(const cuba_sim* sim, cuba_launch_shape* shape);
+
+/*
+ * Autotuner of the whole shape, by coordinates: small_max over the eight
+ * candidates of cuba_autotune, then small_blocks in {1, 2}, then tile_blocks
+ * in {2, 4}, each candidate timed over n_steps steps from the same saved
+ * state (the simulation does not advance); the fastest value of each
+ * coordinate is kept before the next.  *chosen (optional) receives the shape,
+ * ms_per_candidate (optional, host, 12 doubles) the device time per step of
+ * the eight small_max candidates, then small_blocks 1, 2, then tile_blocks
+ * 2, 4.  Synchronous; allocates a temporary copy of the state.
+ */
+int cuba_autotune_shape(cuba_sim* sim, int n_steps, cuba_launch_shape* chosen, double* ms_per_candidate,
+                        void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* cuba_last_error(void);
 
@@ -333,6 +361,10 @@ int cuba_batch_get_time(cuba_batch* b, int32_t id, double* time, double* last_dt
    (all resident members are timed together; none advances). */
 int cuba_batch_autotune(cuba_batch* b, int n_steps, int32_t* chosen, double* ms_per_candidate, void* stream);
 int cuba_batch_set_small_max(cuba_batch* b, int32_t small_max);
+int cuba_batch_set_launch_shape(cuba_batch* b, const cuba_launch_shape* shape);
+int cuba_batch_get_launch_shape(cuba_batch* b, cuba_launch_shape* shape);
+int cuba_batch_autotune_shape(cuba_batch* b, int n_steps, cuba_launch_shape* chosen, double* ms_per_candidate,
+                              void* stream);
 
 /* Occupancy: resident simulations, particles and cells in use. */
 int cuba_batch_usage(const cuba_batch* b, int32_t* n_sims, int64_t* n_particles, int64_t* n_cells);

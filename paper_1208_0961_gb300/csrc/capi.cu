@@ -290,7 +290,8 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
 {
     if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells ||
         small_max != A.small_max || one_key != A.one_key || key0 != A.key_sched.k0[0] || key1 != A.key_sched.k1[0] ||
-        modes != A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs)
+        modes != A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs || tile_nb != A.tile_nb ||
+        small_nb != A.small_nb)
         drop();
     for (int k = 0; k < n; ++k) {
         const int which = A.cur;
@@ -321,6 +322,8 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
             key0 = A.key_sched.k0[0];
             key1 = A.key_sched.k1[0];
             modes = A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs;
+            tile_nb = A.tile_nb;
+            small_nb = A.small_nb;
         }
         CUDA_TRY(cudaGraphLaunch(g[which], st), "graph launch");
         A.cur ^= 1;
@@ -353,10 +356,12 @@ static const int32_t kTuneCandidates[] = {0, 16, 32, 64, 128, 256, 512, 1024};
 static const int kTuneCount = (int)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0]));
 
 // Time n_steps steps of the arena for every candidate threshold, each from
-// the same saved state (positions, momenta, step counters, counters), then
-// restore that state and keep the fastest threshold.  The simulations do not
-// advance.  ms (optional) receives kTuneCount timings in candidate order.
-int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms)
+// the same saved state (positions, momenta, descriptors, counters), then
+// restore that state and keep the fastest threshold; with shape_too, then the
+// blocks per iteration of the small-cell and the item pair kernel, in that
+// order.  The simulations do not advance.  ms (optional) receives the
+// timings in candidate order (kTuneCount, then 2 + 2 with shape_too).
+static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms, bool shape_too)
 {
     if (n_steps < 1) return fail(CUBA_ERR_INVALID, "n_steps must be >= 1");
     if (A.np == 0 || A.nsims == 0) {
@@ -388,33 +393,98 @@ int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, doub
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // device time per step of the present shape, from the saved state
+    auto time_shape = [&](double* out) -> int {
+        restore();
+        int r = enqueue_step(A, st);  // warm-up step (also loads the kernels)
+        cudaEventRecord(e0, st);
+        for (int it = 0; it < n_steps && !r; ++it) r = enqueue_step(A, st);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (!r && e != cudaSuccess) r = cuda_fail(e, "autotune");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        *out = t / n_steps;
+        return r;
+    };
+    // coordinate 1: small_max
     double best = 1e300;
     int32_t best_v = (int32_t)keep;
     for (int k = 0; k < kTuneCount && !rc; ++k) {
-        restore();
         A.small_max = (uint32_t)kTuneCandidates[k];
-        rc = enqueue_step(A, st);  // warm-up step (also loads the kernels)
-        cudaEventRecord(e0, st);
-        for (int it = 0; it < n_steps && !rc; ++it) rc = enqueue_step(A, st);
-        cudaEventRecord(e1, st);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "autotune");
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (ms) ms[k] = t / n_steps;
+        double t = 0.0;
+        rc = time_shape(&t);
+        if (ms) ms[k] = t;
         if (!rc && t < best) {
             best = t;
             best_v = kTuneCandidates[k];
         }
     }
+    A.small_max = rc ? keep : (uint32_t)best_v;
+    // coordinates 2 and 3: blocks per iteration of the two pair kernels
+    if (shape_too && !rc) {
+        const uint32_t small_c[2] = {1u, 2u}, tile_c[2] = {2u, 4u};
+        const uint32_t keep_s = A.small_nb, keep_t = A.tile_nb;
+        double bs = 1e300, bt = 1e300;
+        uint32_t vs = keep_s, vt = keep_t;
+        for (int k = 0; k < 2 && !rc; ++k) {
+            A.small_nb = small_c[k];
+            double t = 0.0;
+            rc = time_shape(&t);
+            if (ms) ms[kTuneCount + k] = t;
+            if (!rc && t < bs) { bs = t; vs = small_c[k]; }
+        }
+        A.small_nb = rc ? keep_s : vs;
+        for (int k = 0; k < 2 && !rc; ++k) {
+            A.tile_nb = tile_c[k];
+            double t = 0.0;
+            rc = time_shape(&t);
+            if (ms) ms[kTuneCount + 2 + k] = t;
+            if (!rc && t < bt) { bt = t; vt = tile_c[k]; }
+        }
+        A.tile_nb = rc ? keep_t : vt;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     restore();
     cudaFree(saved);
-    A.small_max = rc ? keep : (uint32_t)best_v;
     if (chosen) *chosen = (int32_t)A.small_max;
     if (rc) return rc;
     return read_kernel_errors(A);
+}
+
+int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms)
+{
+    return tune_arena(A, n_steps, st, chosen, ms, false);
+}
+
+int autotune_shape(Arena& A, int n_steps, cudaStream_t st, cuba_launch_shape* chosen, double* ms)
+{
+    int32_t sm = 0;
+    const int rc = tune_arena(A, n_steps, st, &sm, ms, true);
+    if (chosen) get_launch_shape(A, chosen);
+    return rc;
+}
+
+int set_launch_shape(Arena& A, const cuba_launch_shape* shape)
+{
+    if (!shape) return fail(CUBA_ERR_INVALID, "shape is NULL");
+    if (shape->small_blocks != 1 && shape->small_blocks != 2)
+        return fail(CUBA_ERR_INVALID, "small_blocks must be 1 or 2");
+    if (shape->tile_blocks != 2 && shape->tile_blocks != 4)
+        return fail(CUBA_ERR_INVALID, "tile_blocks must be 2 or 4");
+    int rc = set_small_max(A, shape->small_max);
+    if (rc) return rc;
+    A.small_nb = (uint32_t)shape->small_blocks;
+    A.tile_nb = (uint32_t)shape->tile_blocks;
+    return CUBA_OK;
+}
+
+void get_launch_shape(const Arena& A, cuba_launch_shape* shape)
+{
+    shape->small_max = (int32_t)A.small_max;
+    shape->small_blocks = (int32_t)A.small_nb;
+    shape->tile_blocks = (int32_t)A.tile_nb;
 }
 
 StepGraphs::~StepGraphs()
@@ -689,6 +759,26 @@ int cuba_get_small_max(const cuba_sim* s, int32_t* small_max)
     if (!s || !small_max) return fail(CUBA_ERR_INVALID, "bad arguments");
     *small_max = (int32_t)s->A.small_max;
     return CUBA_OK;
+}
+
+int cuba_set_launch_shape(cuba_sim* s, const cuba_launch_shape* shape)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    return set_launch_shape(s->A, shape);
+}
+
+int cuba_get_launch_shape(const cuba_sim* s, cuba_launch_shape* shape)
+{
+    if (!s || !shape) return fail(CUBA_ERR_INVALID, "bad arguments");
+    get_launch_shape(s->A, shape);
+    return CUBA_OK;
+}
+
+int cuba_autotune_shape(cuba_sim* s, int n_steps, cuba_launch_shape* chosen, double* ms_per_candidate, void* stream)
+{
+    if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
+    return autotune_shape(s->A, n_steps, (cudaStream_t)stream, chosen, ms_per_candidate);
 }
 
 int cuba_autotune(cuba_sim* s, int n_steps, int32_t* chosen, double* ms_per_candidate, void* stream)

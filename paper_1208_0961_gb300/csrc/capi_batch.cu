@@ -377,6 +377,27 @@ int cuba_batch_set_small_max(cuba_batch* b, int32_t small_max)
     return set_small_max(b->A, small_max);
 }
 
+int cuba_batch_set_launch_shape(cuba_batch* b, const cuba_launch_shape* shape)
+{
+    if (!b) return fail(CUBA_ERR_INVALID, "batch is NULL");
+    CUDA_TRY(cudaDeviceSynchronize(), "sync");
+    return set_launch_shape(b->A, shape);
+}
+
+int cuba_batch_get_launch_shape(cuba_batch* b, cuba_launch_shape* shape)
+{
+    if (!b || !shape) return fail(CUBA_ERR_INVALID, "bad arguments");
+    get_launch_shape(b->A, shape);
+    return CUBA_OK;
+}
+
+int cuba_batch_autotune_shape(cuba_batch* b, int n_steps, cuba_launch_shape* chosen, double* ms_per_candidate,
+                              void* stream)
+{
+    if (!b) return fail(CUBA_ERR_INVALID, "batch is NULL");
+    return autotune_shape(b->A, n_steps, (cudaStream_t)stream, chosen, ms_per_candidate);
+}
+
 int cuba_batch_usage(const cuba_batch* b, int32_t* n_sims, int64_t* n_particles, int64_t* n_cells)
 {
     if (!b) return fail(CUBA_ERR_INVALID, "batch is NULL");

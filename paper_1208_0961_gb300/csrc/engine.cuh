@@ -122,17 +122,17 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 // Pair tile: one warp per item of 32 rows of one cell.
 constexpr int kPairRows = 32;
 constexpr int kPairThreads = 256;
-// Launch shape of the pair tile: a lane draws four Philox blocks per loop
-// iteration.  With one simulation the round keys are kernel parameters
-// (constant-bank operands) and the register budget is uncapped (about 126
-// registers, two blocks of 256 per SM); with several simulations each warp
-// holds its cell's round keys in registers, capped at 128 (two blocks per SM).
-template <bool kOneKey>
+// Launch shape of the pair kernels: Philox blocks a lane draws per loop
+// iteration (tile: 4 or 2, warp-per-small-cell: 2 or 1; chosen at run time,
+// by the autotuner) and the register budget.  With one simulation the round
+// keys are kernel parameters (constant-bank operands) and four blocks run
+// uncapped (about 126 registers, two blocks of 256 per SM); with several
+// simulations each warp holds its cell's round keys in registers, capped at
+// 128 (four blocks) or 80 (two).
+template <bool kOneKey, int NB>
 struct PairShape {
-    static constexpr int nb = 4;                        // Philox blocks per lane and loop iteration
-    static constexpr int min_blocks = kOneKey ? 1 : 2;  // resident blocks per SM the register budget targets
+    static constexpr int min_blocks = kOneKey ? 1 : (NB >= 4 ? 2 : 3);  // resident blocks per SM targeted
 };
-constexpr int kSmallBlocksPerIter = 2; // the same for the warp-per-small-cell kernel (short rows)
 // Queued Philox blocks per warp for nb blocks per iteration.
 __host__ __device__ constexpr int queue_cap(int nb) { return 32 + 32 * nb; }
 
@@ -198,6 +198,8 @@ struct Arena {
     // cells with 2 <= n <= small_max take the warp-per-cell pair and resolve
     // kernels (0: every cell takes the row-block path); at most 1024
     uint32_t small_max = 32;
+    // Philox blocks per lane and loop iteration of the pair kernels
+    uint32_t tile_nb = 4, small_nb = 2;
     // one simulation: its Philox round keys, passed to the pair kernels as a
     // parameter (set whenever the descriptor table is uploaded)
     int one_key = 0;

@@ -51,6 +51,9 @@ int settle_arena(Arena& A, cudaStream_t st, int* realloc);
 int read_kernel_errors(Arena& A);
 int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms);
 int set_small_max(Arena& A, int32_t v);
+int set_launch_shape(Arena& A, const cuba_launch_shape* shape);
+void get_launch_shape(const Arena& A, cuba_launch_shape* shape);
+int autotune_shape(Arena& A, int n_steps, cudaStream_t st, cuba_launch_shape* chosen, double* ms);
 // Record the descriptor table's key and acceptance modes for the pair
 // kernels (after every upload).
 void set_key_param(Arena& A, const SimDesc* table, int n);
@@ -62,6 +65,7 @@ struct StepGraphs {
     cudaStream_t capture = nullptr;
     uint32_t np = 0, ncells = 0, small_max = 0;
     int one_key = 0, modes = 0;
+    uint32_t tile_nb = 0, small_nb = 0;
     uint32_t key0 = 0, key1 = 0;
     const void* acc = nullptr;
     int trace = 0, nsims = 0;

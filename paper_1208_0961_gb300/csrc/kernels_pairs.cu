@@ -397,8 +397,8 @@ __global__ void __launch_bounds__(kPairThreads, 4)
 // kOneKey: every cell belongs to one simulation whose round keys come as the
 // kernel parameter Kp (constant-bank operands, no registers); otherwise each
 // cell's key schedule is derived from its descriptor.
-template <typename T, bool kOneKey>
-__global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey>::min_blocks)
+template <typename T, bool kOneKey, int NB>
+__global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_blocks)
     k_pair_tile(const SimDesc* __restrict__ sims, int nsims, const T* __restrict__ st, uint32_t pcap,
                 const uint32_t* __restrict__ cell_start, const uint2* __restrict__ work, uint32_t ncells,
                 uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc, uint64_t acc_cap,
@@ -406,7 +406,6 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey>::min_blocks)
                 const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    constexpr int NB = PairShape<kOneKey>::nb;
     __shared__ uint4 q_w[kWarps][queue_cap(NB)];
     __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
     const int w = threadIdx.x >> 5;
@@ -463,7 +462,7 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey>::min_blocks)
 // by a grid-stride scan over groups of 32 cells (no work queue, no per-cell
 // atomic); the bounds and list rooms of a group are read in one coalesced
 // round, one cell per lane, and handed to the cells' turns by shuffles.
-template <typename T, bool kOneKey>
+template <typename T, bool kOneKey, int NB>
 __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* __restrict__ sims, int nsims,
                                                              const T* __restrict__ st, uint32_t pcap,
                                                              const uint32_t* __restrict__ cell_start,
@@ -476,7 +475,6 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
                                                              const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    constexpr int NB = kSmallBlocksPerIter;
     __shared__ uint4 q_w[kWarps][queue_cap(NB)];
     __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
     const int w = threadIdx.x >> 5;
@@ -922,26 +920,26 @@ int launch_kinematics_check(const SimDesc& S, const float* pin, int64_t npairs, 
 // ---------------------------------------------------------------------------
 static int last_err() { return cudaPeekAtLastError() == cudaSuccess ? 0 : -1; }
 
-template <typename T, bool kOneKey>
+template <typename T, bool kOneKey, int NB>
 static unsigned pair_grid()
 {
     static unsigned g = 0;
     if (!g) {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_tile<T, kOneKey>, kPairThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_tile<T, kOneKey, NB>, kPairThreads, 0);
         if (per < 1) per = 1;
         g = (unsigned)(per * sm_count());
     }
     return g;
 }
 
-template <typename T, bool kOneKey>
+template <typename T, bool kOneKey, int NB>
 static unsigned small_grid()
 {
     static unsigned g = 0;
     if (!g) {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_small<T, kOneKey>, kPairThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_small<T, kOneKey, NB>, kPairThreads, 0);
         if (per < 1) per = 1;
         g = (unsigned)(per * sm_count());
     }
@@ -961,6 +959,22 @@ static unsigned skip_grid()
     return g;
 }
 
+template <typename T, bool kOneKey, int NB>
+static void launch_small(const Arena& A, cudaStream_t st)
+{
+    k_pair_small<T, kOneKey, NB><<<small_grid<T, kOneKey, NB>(), kPairThreads, 0, st>>>(
+        A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.small_max,
+        A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
+}
+
+template <typename T, bool kOneKey, int NB>
+static void launch_tile(const Arena& A, cudaStream_t st)
+{
+    k_pair_tile<T, kOneKey, NB><<<pair_grid<T, kOneKey, NB>(), kPairThreads, 0, st>>>(
+        A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count, A.acc,
+        A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
+}
+
 template <typename T, bool kOneKey>
 static void launch_pairs(const Arena& A, cudaStream_t st)
 {
@@ -969,13 +983,16 @@ static void launch_pairs(const Arena& A, cudaStream_t st)
             A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.skip_work, A.ncells,
             A.small_max, A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
     if (!A.any_all_pairs) return;
-    if (A.small_max)
-        k_pair_small<T, kOneKey><<<small_grid<T, kOneKey>(), kPairThreads, 0, st>>>(
-            A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.small_max,
-            A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
-    k_pair_tile<T, kOneKey><<<pair_grid<T, kOneKey>(), kPairThreads, 0, st>>>(
-        A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count, A.acc,
-        A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
+    if (A.small_max) {
+        if (A.small_nb == 1)
+            launch_small<T, kOneKey, 1>(A, st);
+        else
+            launch_small<T, kOneKey, 2>(A, st);
+    }
+    if (A.tile_nb == 2)
+        launch_tile<T, kOneKey, 2>(A, st);
+    else
+        launch_tile<T, kOneKey, 4>(A, st);
 }
 
 int launch_pair_tile(const Arena& A, cudaStream_t st)
@@ -1003,14 +1020,22 @@ int kernels_init()
             cudaSuccess)
         return -1;
     if (bin_kernels_init()) return -1;
-    pair_grid<double, false>();
-    pair_grid<float, false>();
-    pair_grid<double, true>();
-    pair_grid<float, true>();
-    small_grid<double, false>();
-    small_grid<float, false>();
-    small_grid<double, true>();
-    small_grid<float, true>();
+    pair_grid<double, false, 4>();
+    pair_grid<float, false, 4>();
+    pair_grid<double, true, 4>();
+    pair_grid<float, true, 4>();
+    pair_grid<double, false, 2>();
+    pair_grid<float, false, 2>();
+    pair_grid<double, true, 2>();
+    pair_grid<float, true, 2>();
+    small_grid<double, false, 2>();
+    small_grid<float, false, 2>();
+    small_grid<double, true, 2>();
+    small_grid<float, true, 2>();
+    small_grid<double, false, 1>();
+    small_grid<float, false, 1>();
+    small_grid<double, true, 1>();
+    small_grid<float, true, 1>();
     skip_grid<double, false>();
     skip_grid<float, false>();
     skip_grid<double, true>();

@@ -57,6 +57,10 @@ class cuba_batch_config(C.Structure):
                 ("max_cells", C.c_int64)]
 
 
+class cuba_launch_shape(C.Structure):
+    _fields_ = [("small_max", C.c_int32), ("small_blocks", C.c_int32), ("tile_blocks", C.c_int32)]
+
+
 class CubaError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("cuba error %d: %s" % (code, msg))
@@ -126,6 +130,13 @@ def load(build_if_missing=True):
         "cuba_get_small_max": (C.c_int, [vp, C.POINTER(C.c_int32)]),
         "cuba_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]),
         "cuba_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]),
+        "cuba_set_launch_shape": (C.c_int, [vp, C.POINTER(cuba_launch_shape)]),
+        "cuba_get_launch_shape": (C.c_int, [vp, C.POINTER(cuba_launch_shape)]),
+        "cuba_autotune_shape": (C.c_int, [vp, C.c_int, C.POINTER(cuba_launch_shape), C.POINTER(C.c_double), vp]),
+        "cuba_batch_set_launch_shape": (C.c_int, [vp, C.POINTER(cuba_launch_shape)]),
+        "cuba_batch_get_launch_shape": (C.c_int, [vp, C.POINTER(cuba_launch_shape)]),
+        "cuba_batch_autotune_shape": (C.c_int, [vp, C.c_int, C.POINTER(cuba_launch_shape), C.POINTER(C.c_double),
+                                                vp]),
         "cuba_batch_set_small_max": (C.c_int, [vp, C.c_int32]),
     }
     for name, (res, args) in sig.items():
@@ -314,6 +325,41 @@ def cuba_get_small_max(sim):
     v = C.c_int32()
     _check(load().cuba_get_small_max(sim, C.byref(v)))
     return v.value
+
+
+SHAPE_CANDIDATES = tuple("small_max=%d" % v for v in TUNE_CANDIDATES) + (
+    "small_blocks=1", "small_blocks=2", "tile_blocks=2", "tile_blocks=4")
+
+
+def _shape_dict(sh):
+    return {"small_max": sh.small_max, "small_blocks": sh.small_blocks, "tile_blocks": sh.tile_blocks}
+
+
+def cuba_set_launch_shape(sim, small_max, small_blocks=2, tile_blocks=4):
+    sh = cuba_launch_shape(int(small_max), int(small_blocks), int(tile_blocks))
+    _check(load().cuba_set_launch_shape(sim, C.byref(sh)))
+
+
+def cuba_get_launch_shape(sim):
+    sh = cuba_launch_shape()
+    _check(load().cuba_get_launch_shape(sim, C.byref(sh)))
+    return _shape_dict(sh)
+
+
+def cuba_autotune_shape(sim, n_steps=2, stream=None):
+    """Tune small_max, then the small-cell and the item kernel's blocks per
+    iteration; returns (shape dict, {candidate: ms per step})."""
+    sh = cuba_launch_shape()
+    ms = (C.c_double * len(SHAPE_CANDIDATES))()
+    _check(load().cuba_autotune_shape(sim, int(n_steps), C.byref(sh), ms, _stream_ptr(stream)))
+    return _shape_dict(sh), dict(zip(SHAPE_CANDIDATES, list(ms)))
+
+
+def cuba_batch_autotune_shape(b, n_steps=2, stream=None):
+    sh = cuba_launch_shape()
+    ms = (C.c_double * len(SHAPE_CANDIDATES))()
+    _check(load().cuba_batch_autotune_shape(b, int(n_steps), C.byref(sh), ms, _stream_ptr(stream)))
+    return _shape_dict(sh), dict(zip(SHAPE_CANDIDATES, list(ms)))
 
 
 def cuba_autotune(sim, n_steps=2, stream=None):
