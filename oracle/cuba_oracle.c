@@ -52,6 +52,8 @@ typedef struct {
     uint32_t key[2];  /* Philox key (seed low word, seed high word) */
     int32_t skip;     /* 0: every pair tested (Eq. 3); 1: skip-ahead candidates + thinning */
     double kappa;     /* > 0: adaptive time step, dt is its upper bound (see orc_adaptive_dt) */
+    double mass;      /* particle mass, GeV (0: massless gluons) */
+    double mu;        /* > 0: screened forward-peaked angular distribution (see kin_general) */
 } orc_params;
 
 typedef struct {
@@ -111,6 +113,7 @@ static void philox(uint32_t a, uint32_t b, uint32_t c, uint32_t d, const uint32_
 #define TAG_FINE 0x40000000u   /* acceptance: low 16 bits of u_ij           */
 #define TAG_ANGLE 0x80000000u  /* kinematics: CM-frame direction           */
 #define TAG_SKIP 0xC0000000u   /* skip-ahead: k-th candidate draw of a row   */
+#define TAG_MASS 0x40000000u   /* sampling of a massive momentum: try k      */
 #define STEP_INIT 0xFFFFFFFFu  /* first counter word reserved for sampling */
 
 /* ------------------------------------------------------------------------ */
@@ -143,6 +146,7 @@ static int check_params(const orc_params *p)
     if (!(p->dt > 0.0) || !(p->sigma >= 0.0) || !(p->n_test > 0.0)) return ORC_ERR_INVALID;
     if (p->skip != 0 && p->skip != 1) return ORC_ERR_INVALID;
     if (!(p->kappa >= 0.0) || p->kappa > 0.5) return ORC_ERR_INVALID;
+    if (!(p->mass >= 0.0) || !(p->mu >= 0.0)) return ORC_ERR_INVALID;
     return ORC_OK;
 }
 
@@ -152,6 +156,31 @@ static int check_params(const orc_params *p)
 
 /* Uniform variate in the open interval (0, 1) from a 32-bit word. */
 static double open01(uint32_t r) { return ((double)r + 0.5) * 0x1p-32; }
+
+/*
+ * Momentum magnitude of a thermal particle at temperature T.  Massless: the
+ * given Gamma(3, T) variate p0 (E = |p|, density p^2 exp(-p/T)).  Massive
+ * (mass m > 0), the Juttner density p^2 exp(-sqrt(p^2 + m^2)/T) by rejection
+ * from the massless one: try k draws the block (STEP_INIT, g_lo, g_hi,
+ * TAG_MASS | k), proposes q = -T ln(u0 u1 u2) and keeps it iff
+ * u3 < exp(-(sqrt(q^2 + m^2) - q) / T) (the ratio of the two densities, at
+ * most 1; the difference written m^2 / (sqrt(q^2 + m^2) + q)).  After 64
+ * rejected tries the last proposal is kept.
+ */
+static double sample_pmag(const orc_params *p, double T, uint32_t glo, uint32_t ghi, double p0)
+{
+    if (!(p->mass > 0.0)) return p0;
+    const double m2 = p->mass * p->mass;
+    double q = p0;
+    for (uint32_t k = 0; k < 64; ++k) {
+        uint32_t w[4];
+        philox(STEP_INIT, glo, ghi, TAG_MASS | k, p->key, w);
+        q = -T * log(open01(w[0]) * open01(w[1]) * open01(w[2]));
+        double acc = exp(-(m2 / (sqrt(q * q + m2) + q)) / T);
+        if (open01(w[3]) < acc) break;
+    }
+    return q;
+}
 
 /*
  * Number of particles per region: proportional to T^3 V (a Boltzmann gas has
@@ -197,7 +226,8 @@ int orc_region_counts(int64_t n, const orc_region *R, int nreg, int64_t *counts)
  * two Philox blocks with counters (STEP_INIT, g_lo, g_hi, 0) and (…, 1):
  * words a0..a2 place it uniformly in its region, E = -T ln(u1 u2 u3) with
  * (a3, b0, b1) samples the massless Boltzmann spectrum E^2 exp(-E/T)
- * (a Gamma(3, T) variate), and (b2, b3) give an isotropic direction.
+ * (a Gamma(3, T) variate; massive particles: sample_pmag), and (b2, b3) give
+ * an isotropic direction.
  * State layout: st[0..n) = x, [n..2n) = y, [2n..3n) = z, then px, py, pz.
  */
 int orc_init_thermal(const orc_params *p, int64_t n, const orc_region *R, int nreg, double *st)
@@ -218,7 +248,8 @@ int orc_init_thermal(const orc_params *p, int64_t n, const orc_region *R, int nr
             double pos[3];
             for (int ax = 0; ax < 3; ++ax)
                 pos[ax] = reg->lo[ax] + open01(a[ax]) * (reg->hi[ax] - reg->lo[ax]);
-            double E = -reg->T * log(open01(a[3]) * open01(b[0]) * open01(b[1]));
+            double E = sample_pmag(p, reg->T, (uint32_t)g, (uint32_t)((uint64_t)g >> 32),
+                                   -reg->T * log(open01(a[3]) * open01(b[0]) * open01(b[1])));
             double ct = 2.0 * open01(b[2]) - 1.0;
             double stt = sqrt((1.0 - ct) * (1.0 + ct));
             double phi = 2.0 * M_PI * open01(b[3]);
@@ -273,7 +304,7 @@ int orc_init_hotspot(const orc_params *p, int64_t n, double T0, double dT, doubl
         uint32_t a[4], b[4];
         philox(STEP_INIT, glo, ghi, 0u, p->key, a);
         philox(STEP_INIT, glo, ghi, 1u, p->key, b);
-        double E = -T * log(open01(a[3]) * open01(b[0]) * open01(b[1]));
+        double E = sample_pmag(p, T, glo, ghi, -T * log(open01(a[3]) * open01(b[0]) * open01(b[1])));
         double ct = 2.0 * open01(b[2]) - 1.0;
         double stt = sqrt((1.0 - ct) * (1.0 + ct));
         double phi = 2.0 * M_PI * open01(b[3]);
@@ -340,14 +371,14 @@ int orc_keys(const orc_params *p, int64_t n, const double *st, uint32_t *keys)
 
 /*
  * Stream one particle for dt and reflect it at the walls, FP64.
- * x <- x + (p_x / E) dt (Eq. 2 with c = 1, E = |p| for massless particles);
+ * x <- x + (p_x / E) dt (Eq. 2 with c = 1, E = sqrt(|p|^2 + m^2));
  * a particle beyond a wall is mirrored back and its momentum component flips
  * (elastic reflection, Sec. 2).  A particle exactly on a wall stays there.
  * Returns the number of reflections.
  */
 static int stream_d(const orc_params *p, double *pos, double *mom)
 {
-    double E = sqrt((mom[0] * mom[0] + mom[1] * mom[1]) + mom[2] * mom[2]);
+    double E = sqrt(((mom[0] * mom[0] + mom[1] * mom[1]) + mom[2] * mom[2]) + p->mass * p->mass);
     int nref = 0;
     for (int a = 0; a < 3; ++a) {
         double v = (E > 0.0) ? (mom[a] / E) : 0.0;
@@ -366,10 +397,10 @@ static int stream_d(const orc_params *p, double *pos, double *mom)
     return nref;
 }
 
-/* Same in single precision (dt and L rounded to float once). */
+/* Same in single precision (dt, L and m^2 rounded to float once). */
 static int stream_f(const orc_params *p, float *pos, float *mom)
 {
-    float E = sqrtf((mom[0] * mom[0] + mom[1] * mom[1]) + mom[2] * mom[2]);
+    float E = sqrtf(((mom[0] * mom[0] + mom[1] * mom[1]) + mom[2] * mom[2]) + (float)(p->mass * p->mass));
     float dt = (float)p->dt;
     int nref = 0;
     for (int a = 0; a < 3; ++a) {
@@ -494,27 +525,65 @@ static float vrel_f(const float *ui, const float *uj)
     return 0.5f * ((d0 * d0 + d1 * d1) + d2 * d2);
 }
 
+/*
+ * v_rel of massive particles (mass m): s / (2 E_i E_j) generalises to the
+ * Moller velocity sqrt((p_i.p_j)^2 - m^4) / (E_i E_j) with the four-vector
+ * product p_i.p_j = E_i E_j - p_i.p_j (3-vectors), written
+ * sqrt((F - m^2)(F + m^2)) / (E_i E_j); 0 where rounding makes F < m^2.
+ */
+static double vrel_massive_d(double m2, const double *mi, const double *mj)
+{
+    double Ei = sqrt(((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]) + m2);
+    double Ej = sqrt(((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]) + m2);
+    double F = Ei * Ej - ((mi[0] * mj[0] + mi[1] * mj[1]) + mi[2] * mj[2]);
+    double a = F - m2;
+    if (!(a > 0.0)) return 0.0;
+    return sqrt(a * (F + m2)) / (Ei * Ej);
+}
+
+static float vrel_massive_f(float m2, const float *mi, const float *mj)
+{
+    float Ei = sqrtf(((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]) + m2);
+    float Ej = sqrtf(((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]) + m2);
+    float F = Ei * Ej - ((mi[0] * mj[0] + mi[1] * mj[1]) + mi[2] * mj[2]);
+    float a = F - m2;
+    if (!(a > 0.0f)) return 0.0f;
+    return sqrtf(a * (F + m2)) / (Ei * Ej);
+}
+
+/* P22 = C v_rel of a pair in the state's precision (massless: the unit-vector
+   form; massive: the Moller velocity). */
+static double p22_d(const orc_params *p, double C, const double *mi, const double *mj)
+{
+    if (p->mass > 0.0) return C * vrel_massive_d(p->mass * p->mass, mi, mj);
+    double ui[3], uj[3];
+    unit_d(mi, ui);
+    unit_d(mj, uj);
+    return C * vrel_d(ui, uj);
+}
+
+static float p22_f(const orc_params *p, double C, const double *mi, const double *mj)
+{
+    float fi[3] = {(float)mi[0], (float)mi[1], (float)mi[2]};
+    float fj[3] = {(float)mj[0], (float)mj[1], (float)mj[2]};
+    if (p->mass > 0.0) return (float)C * vrel_massive_f((float)(p->mass * p->mass), fi, fj);
+    float ui[3], uj[3];
+    unit_f(fi, ui);
+    unit_f(fj, uj);
+    return (float)C * vrel_f(ui, uj);
+}
+
 /* Accept pair (i, j) iff u_ij < P22, evaluated in the state's precision. */
 static int accept_pair(const orc_params *p, double C, uint32_t step, uint32_t cell, uint32_t i,
                        uint32_t j, const double *mi, const double *mj)
 {
     uint32_t r = orc_pair_word(p->key, step, cell, i, j);
     if (p->fp32) {
-        float fi[3] = {(float)mi[0], (float)mi[1], (float)mi[2]};
-        float fj[3] = {(float)mj[0], (float)mj[1], (float)mj[2]};
-        float ui[3], uj[3];
-        unit_f(fi, ui);
-        unit_f(fj, uj);
-        float P22 = (float)C * vrel_f(ui, uj);
         float u = (float)r * 0x1p-32f;
-        return u < P22;
+        return u < p22_f(p, C, mi, mj);
     } else {
-        double ui[3], uj[3];
-        unit_d(mi, ui);
-        unit_d(mj, uj);
-        double P22 = C * vrel_d(ui, uj);
         double u = (double)r * 0x1p-32;
-        return u < P22;
+        return u < p22_d(p, C, mi, mj);
     }
 }
 
@@ -584,21 +653,11 @@ static int thin_accept(const orc_params *p, double C, uint64_t P_fix, uint32_t w
 {
     double Pm = (double)P_fix * 0x1p-64;
     if (p->fp32) {
-        float fi[3] = {(float)mi[0], (float)mi[1], (float)mi[2]};
-        float fj[3] = {(float)mj[0], (float)mj[1], (float)mj[2]};
-        float ui[3], uj[3];
-        unit_f(fi, ui);
-        unit_f(fj, uj);
-        float P22 = (float)C * vrel_f(ui, uj);
         float u = ((float)w * 0x1p-32f) * (float)Pm;
-        return u < P22;
+        return u < p22_f(p, C, mi, mj);
     } else {
-        double ui[3], uj[3];
-        unit_d(mi, ui);
-        unit_d(mj, uj);
-        double P22 = C * vrel_d(ui, uj);
         double u = ((double)w * 0x1p-32) * Pm;
-        return u < P22;
+        return u < p22_d(p, C, mi, mj);
     }
 }
 
@@ -640,37 +699,86 @@ static int64_t skip_row(const orc_params *p, double C, uint64_t P_fix, const uin
 
 /*
  * New momenta of an executed pair (Sec. 2).  With P = p_i + p_j,
- * E_t = E_i + E_j, s = 2 E_i E_j v_rel, beta = P / E_t, gamma = E_t / sqrt(s):
- * in the CM frame both particles carry E* = sqrt(s)/2 and momenta +-p*,
- * p* = E* (sin t cos f, sin t sin f, cos t) with cos t = 2 u1 - 1, f = 2 pi u2
- * from the Philox block (step, cell, i, TAG_ANGLE | j).  Boosting back:
- * p' = p* + beta (gamma^2/(gamma+1) (beta . p*) + gamma E*).
- * Returns 0 if s <= 0 (collinear pair; nothing happens).
+ * E_t = E_i + E_j, beta = P / E_t, gamma = E_t / sqrt(s): in the CM frame
+ * both particles carry E* = sqrt(s)/2 and momenta +-p*, |p*| =
+ * sqrt(E*^2 - m^2) (massless: s = 2 E_i E_j v_rel and |p*| = E*).  Boosting
+ * back: p' = p* + beta (gamma^2/(gamma+1) (beta . p*) + gamma E*).
+ * The direction of p* comes from the Philox block (step, cell, i,
+ * TAG_ANGLE | j), u1 = word0 2^-32, u2 = word1 2^-32, phi = 2 pi u2:
+ *  - isotropic (mu = 0, the paper's case): cos t = 2 u1 - 1 about the z axis;
+ *  - screened forward peak (mu > 0, no counterpart in the paper; the
+ *    pQCD-like dsigma/dt ~ 1/(t - mu^2)^2 with t = -2 |p*|^2 (1 - cos t)):
+ *    x = 1 - cos t by inverting its CDF in closed form, with a = 2 |p*|^2,
+ *    A = 1/mu^2, B = 1/(2a + mu^2): x = (1/(A - u1 (A - B)) - mu^2) / a, the
+ *    angle measured from the incoming CM direction of particle i (its
+ *    momentum boosted by -beta: p_i + beta (gamma^2/(gamma+1) (beta . p_i)
+ *    - gamma E_i)), phi about it in the basis e1 = unit(h x e),
+ *    e2 = e x e1 with h = x^ if |e_x| < 0.9, else y^.
+ * The total cross section (and P22) is the same in both cases.  Returns 0
+ * if s <= 4 m^2 (nothing happens).
  */
-int orc_kinematics(const uint32_t key[2], uint32_t step, uint32_t cell, uint32_t i, uint32_t j,
-                   double *mi, double *mj)
+static int kin_general(const uint32_t key[2], double mass, double mu, uint32_t step, uint32_t cell, uint32_t i,
+                       uint32_t j, double *mi, double *mj)
 {
-    double Ei = sqrt((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]);
-    double Ej = sqrt((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]);
-    double ui[3], uj[3];
-    unit_d(mi, ui);
-    unit_d(mj, uj);
-    double s = ((2.0 * Ei) * Ej) * vrel_d(ui, uj);
-    if (!(s > 0.0)) return 0;
+    const double m2 = mass * mass;
+    double Ei = sqrt(((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]) + m2);
+    double Ej = sqrt(((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]) + m2);
+    double s;
+    if (mass > 0.0) {
+        double F = Ei * Ej - ((mi[0] * mj[0] + mi[1] * mj[1]) + mi[2] * mj[2]);
+        s = 2.0 * m2 + 2.0 * F;
+        if (!(s > 4.0 * m2)) return 0;
+    } else {
+        double ui[3], uj[3];
+        unit_d(mi, ui);
+        unit_d(mj, uj);
+        s = ((2.0 * Ei) * Ej) * vrel_d(ui, uj);
+        if (!(s > 0.0)) return 0;
+    }
     double rs = sqrt(s);
     double Es = 0.5 * rs;
+    double ps_mag = mass > 0.0 ? sqrt((Es - mass) * (Es + mass)) : Es;
     double Et = Ei + Ej;
     double beta[3] = {(mi[0] + mj[0]) / Et, (mi[1] + mj[1]) / Et, (mi[2] + mj[2]) / Et};
     double gamma = Et / rs;
+    double a = (gamma * gamma) / (gamma + 1.0);
     uint32_t w[4];
     philox(step, cell, i, TAG_ANGLE | j, key, w);
     double u1 = (double)w[0] * 0x1p-32, u2 = (double)w[1] * 0x1p-32;
-    double ct = 2.0 * u1 - 1.0;
-    double stt = sqrt((1.0 - ct) * (1.0 + ct));
     double phi = 2.0 * M_PI * u2;
-    double ps[3] = {Es * (stt * cos(phi)), Es * (stt * sin(phi)), Es * ct};
+    double ps[3];
+    if (!(mu > 0.0)) {
+        double ct = 2.0 * u1 - 1.0;
+        double stt = sqrt((1.0 - ct) * (1.0 + ct));
+        ps[0] = ps_mag * (stt * cos(phi));
+        ps[1] = ps_mag * (stt * sin(phi));
+        ps[2] = ps_mag * ct;
+    } else {
+        /* incoming CM direction of particle i */
+        double bpi = (beta[0] * mi[0] + beta[1] * mi[1]) + beta[2] * mi[2];
+        double fi_in = a * bpi - gamma * Ei;
+        double e[3] = {mi[0] + beta[0] * fi_in, mi[1] + beta[1] * fi_in, mi[2] + beta[2] * fi_in};
+        double en = sqrt((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2]);
+        for (int ax = 0; ax < 3; ++ax) e[ax] = e[ax] / en;
+        double h[3] = {0.0, 0.0, 0.0};
+        if (fabs(e[0]) < 0.9) h[0] = 1.0; else h[1] = 1.0;
+        double e1[3] = {h[1] * e[2] - h[2] * e[1], h[2] * e[0] - h[0] * e[2], h[0] * e[1] - h[1] * e[0]};
+        double n1 = sqrt((e1[0] * e1[0] + e1[1] * e1[1]) + e1[2] * e1[2]);
+        for (int ax = 0; ax < 3; ++ax) e1[ax] = e1[ax] / n1;
+        double e2[3] = {e[1] * e1[2] - e[2] * e1[1], e[2] * e1[0] - e[0] * e1[2], e[0] * e1[1] - e[1] * e1[0]};
+        double aa = 2.0 * (ps_mag * ps_mag);
+        double mu2 = mu * mu;
+        double A = 1.0 / mu2, B = 1.0 / (2.0 * aa + mu2);
+        double x = (1.0 / (A - u1 * (A - B)) - mu2) / aa;
+        if (x < 0.0) x = 0.0;
+        if (x > 2.0) x = 2.0;
+        double ct = 1.0 - x;
+        double stt = sqrt(x * (2.0 - x));
+        double cp = cos(phi), sp = sin(phi);
+        for (int ax = 0; ax < 3; ++ax)
+            ps[ax] = ps_mag * (ct * e[ax] + stt * (cp * e1[ax] + sp * e2[ax]));
+    }
     double bp = (beta[0] * ps[0] + beta[1] * ps[1]) + beta[2] * ps[2];
-    double a = (gamma * gamma) / (gamma + 1.0);
     double fi = a * bp + gamma * Es;
     double fj = -a * bp + gamma * Es;
     for (int ax = 0; ax < 3; ++ax) {
@@ -678,6 +786,20 @@ int orc_kinematics(const uint32_t key[2], uint32_t step, uint32_t cell, uint32_t
         mj[ax] = -ps[ax] + beta[ax] * fj;
     }
     return 1;
+}
+
+/* Massless particles, isotropic direction (the paper's case). */
+int orc_kinematics(const uint32_t key[2], uint32_t step, uint32_t cell, uint32_t i, uint32_t j, double *mi,
+                   double *mj)
+{
+    return kin_general(key, 0.0, 0.0, step, cell, i, j, mi, mj);
+}
+
+/* Any mass and angular distribution (mass, mu as in orc_params). */
+int orc_kinematics_ex(const uint32_t key[2], double mass, double mu, uint32_t step, uint32_t cell, uint32_t i,
+                      uint32_t j, double *mi, double *mj)
+{
+    return kin_general(key, mass, mu, step, cell, i, j, mi, mj);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -762,7 +884,7 @@ static int do_cell(const orc_params *p, double C, uint32_t step, uint32_t cell, 
         cr->n_exe += 1;
         double mi[3] = {px[i], py[i], pz[i]};
         double mj[3] = {px[j], py[j], pz[j]};
-        orc_kinematics(p->key, step, cell, i, j, mi, mj);
+        kin_general(p->key, p->mass, p->mu, step, cell, i, j, mi, mj);
         if (p->fp32) {
             for (int a = 0; a < 3; ++a) { mi[a] = (double)(float)mi[a]; mj[a] = (double)(float)mj[a]; }
         }
@@ -1025,7 +1147,7 @@ int orc_observables(const orc_params *p, int64_t n, const double *st, const int6
         double e = 0.0, m = 0.0;
         for (int64_t k = cell_start[c]; k < cell_start[c + 1]; ++k) {
             double qx = st[3 * n + k], qy = st[4 * n + k], qz = st[5 * n + k];
-            e += sqrt((qx * qx + qy * qy) + qz * qz);
+            e += sqrt(((qx * qx + qy * qy) + qz * qz) + p->mass * p->mass);
             m += qx;
         }
         if (T00) T00[c] = e / norm;
@@ -1035,13 +1157,13 @@ int orc_observables(const orc_params *p, int64_t n, const double *st, const int6
     return ORC_OK;
 }
 
-/* Total energy and momentum (FP64): out = {E, Px, Py, Pz}. */
-void orc_totals(int64_t n, const double *st, double out[4])
+/* Total energy and momentum (FP64, particles of the given mass): out = {E, Px, Py, Pz}. */
+void orc_totals(int64_t n, const double *st, double mass, double out[4])
 {
     double e = 0.0, x = 0.0, y = 0.0, z = 0.0;
     for (int64_t k = 0; k < n; ++k) {
         double qx = st[3 * n + k], qy = st[4 * n + k], qz = st[5 * n + k];
-        e += sqrt((qx * qx + qy * qy) + qz * qz);
+        e += sqrt(((qx * qx + qy * qy) + qz * qz) + mass * mass);
         x += qx;
         y += qy;
         z += qz;

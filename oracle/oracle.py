@@ -29,6 +29,8 @@ class Params(C.Structure):
         ("key", C.c_uint32 * 2),
         ("skip", C.c_int32),
         ("kappa", C.c_double),
+        ("mass", C.c_double),
+        ("mu", C.c_double),
     ]
 
 
@@ -85,6 +87,9 @@ def lib():
         L.orc_pair_word.restype = C.c_uint32
         L.orc_kinematics.argtypes = [u32p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, dp, dp]
         L.orc_kinematics.restype = C.c_int
+        L.orc_kinematics_ex.argtypes = [u32p, C.c_double, C.c_double, C.c_uint32, C.c_uint32, C.c_uint32,
+                                        C.c_uint32, dp, dp]
+        L.orc_kinematics_ex.restype = C.c_int
         L.orc_cell_accept.argtypes = [C.POINTER(Params), C.c_uint32, C.c_uint32, C.c_int64,
                                       dp, dp, dp, u32p, C.c_int64]
         L.orc_cell_accept.restype = C.c_int64
@@ -96,7 +101,7 @@ def lib():
         L.orc_observables.argtypes = [C.POINTER(Params), C.c_int64, dp, i64p, dp, dp,
                                       C.POINTER(C.c_int32)]
         L.orc_observables.restype = C.c_int
-        L.orc_totals.argtypes = [C.c_int64, dp, dp]
+        L.orc_totals.argtypes = [C.c_int64, dp, C.c_double, dp]
         L.orc_totals.restype = None
         u64p = C.POINTER(C.c_uint64)
         L.orc_skip_table.argtypes = [C.c_double, u64p, u64p]
@@ -118,7 +123,7 @@ def _ptr(a, ct):
 
 
 def make_params(L=(10.0, 1.0, 1.0), n=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_test=1.0,
-                fp32=False, seed=0, skip=False, kappa=0.0):
+                fp32=False, seed=0, skip=False, kappa=0.0, mass=0.0, mu=0.0):
     p = Params()
     for a in range(3):
         p.L[a] = float(L[a])
@@ -131,6 +136,8 @@ def make_params(L=(10.0, 1.0, 1.0), n=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_tes
     p.key[1] = (int(seed) >> 32) & 0xFFFFFFFF
     p.skip = 1 if skip else 0
     p.kappa = float(kappa)
+    p.mass = float(mass)
+    p.mu = float(mu)
     return p
 
 
@@ -257,6 +264,16 @@ def skip_gap(Q, U, M):
     return int(lib().orc_skip_gap(_ptr(Q, C.c_uint64), int(U), int(M)))
 
 
+def kinematics_ex(key, mass, mu, step, cell, i, j, pi, pj):
+    """Kinematics of an executed pair for any mass and angular distribution."""
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    a = np.array(pi, dtype=np.float64)
+    b = np.array(pj, dtype=np.float64)
+    ok = lib().orc_kinematics_ex(_ptr(k, C.c_uint32), float(mass), float(mu), step, cell, i, j,
+                                 _ptr(a, C.c_double), _ptr(b, C.c_double))
+    return bool(ok), a, b
+
+
 def cell_accept(p, step, cell, mom):
     """Accepted (i, j) pairs of one cell; mom has shape (3, nc) in sorted order."""
     mom = np.ascontiguousarray(mom, dtype=np.float64)
@@ -363,10 +380,10 @@ def observables(p, st, cell_start):
     return T00, T0x, cnt
 
 
-def totals(st):
+def totals(st, mass=0.0):
     st = np.ascontiguousarray(st, dtype=np.float64)
     out = np.zeros(4)
-    lib().orc_totals(st.shape[1], _ptr(st, C.c_double), _ptr(out, C.c_double))
+    lib().orc_totals(st.shape[1], _ptr(st, C.c_double), float(mass), _ptr(out, C.c_double))
     return out
 
 
