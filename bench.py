@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--acceptance", default="all-pairs", choices=["all-pairs", "skip"],
                     help="pair test of the paper (every pair draws its uniform) or skip-ahead sampling")
+    ap.add_argument("--mass", type=float, default=0.0, help="particle mass, GeV (0: massless gluons)")
+    ap.add_argument("--mu", type=float, default=0.0, help="> 0: screened forward-peaked scattering, GeV")
     ap.add_argument("--kappa", type=float, default=0.0,
                     help="> 0: adaptive time step (kappa collisions per particle of the fullest cell per "
                          "step, dt as its cap)")
@@ -490,7 +492,7 @@ def main():
     p = cuba.make_params(L=cfg["L"], n_cells=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
                          n_test=cfg["n_test"], precision=prec, seed=replica_seed(args.seed, rank),
                          acceptance=cuba.CUBA_ACCEPT_SKIP if args.acceptance == "skip" else cuba.CUBA_ACCEPT_ALL_PAIRS,
-                         kappa=args.kappa)
+                         kappa=args.kappa, mass=args.mass, mu=args.mu)
     sim = cuba.Sim(p, args.n)
     stream = torch.cuda.Stream()
     if args.workload == "hotspot3d":
@@ -610,7 +612,7 @@ def main():
             "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "n_particles": args.n, "n_cells": args.cells, "dt": args.dt,
                        "sigma_mb": args.sigma_mb, "precision": args.precision, "n_test": cfg["n_test"],
-                       "acceptance": args.acceptance, "kappa": args.kappa,
+                       "acceptance": args.acceptance, "kappa": args.kappa, "mass": args.mass, "mu": args.mu,
                        "simulated_fm_per_step": sim_fm_per_step,
                        "l2": "state %.0f MB > L2, no flush" % (args.n * 24 / 1e6 * (2 if prec else 1)),
                        "parallelism": "replicas" if world > 1 else "single",

@@ -94,6 +94,17 @@ typedef struct cuba_params {
                              collisions; capped by dt (the field above), which
                              is used as is without collisions.  0: fixed dt.
                              At most 1/2 (keeps 2 C <= 1). */
+    double mass;          /* particle mass m, GeV (0: the paper's massless
+                             gluons).  E = sqrt(|p|^2 + m^2) everywhere; v_rel
+                             is the Moller velocity sqrt((p_i.p_j)^2 - m^4) /
+                             (E_i E_j); thermal sampling follows the Juttner
+                             spectrum.  No counterpart in the paper. */
+    double mu;            /* > 0: screened forward-peaked scattering,
+                             dsigma/dt ~ 1/(t - mu^2)^2 in the CM frame (mu in
+                             GeV); 0: isotropic (the paper's case).  The total
+                             cross section, and so P22, is sigma either way.
+                             With CUBA_FP32 these collisions run in FP64 (the
+                             incoming CM direction cancels in FP32). */
 } cuba_params;
 
 #define CUBA_ACCEPT_ALL_PAIRS 0

@@ -68,6 +68,12 @@ int make_desc(const cuba_params* p, SimDesc* S)
     if (p->acceptance != CUBA_ACCEPT_ALL_PAIRS && p->acceptance != CUBA_ACCEPT_SKIP)
         return fail(CUBA_ERR_INVALID, "acceptance must be CUBA_ACCEPT_ALL_PAIRS or CUBA_ACCEPT_SKIP");
     if (!(p->kappa >= 0.0) || p->kappa > 0.5) return fail(CUBA_ERR_INVALID, "kappa must lie in [0, 1/2]");
+    if (!(p->mass >= 0.0) || !std::isfinite(p->mass)) return fail(CUBA_ERR_INVALID, "mass must be >= 0");
+    if (!(p->mu >= 0.0) || !std::isfinite(p->mu)) return fail(CUBA_ERR_INVALID, "mu must be >= 0");
+    S->mass = p->mass;
+    S->m2 = p->mass * p->mass;
+    S->m2f = (float)S->m2;
+    S->mu = p->mu;
     S->skip = p->acceptance == CUBA_ACCEPT_SKIP ? 1u : 0u;
     S->V = (S->dx[0] * S->dx[1]) * S->dx[2];
     S->sigma = p->sigma_fm2;

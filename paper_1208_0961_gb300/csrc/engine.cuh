@@ -50,6 +50,10 @@ struct SimDesc {
     double dt_max;
     double sigma, n_test, V;
     double time;
+    // particle mass (m2 = m^2, m2f its FP32 copy) and the screening mass of
+    // the forward-peaked angular distribution (0: isotropic)
+    double mass, m2, mu;
+    float m2f;
 };
 
 // C, its FP32 copy, the byte thresholds and the skip-ahead tables of a

@@ -26,6 +26,9 @@ template <> __device__ __forceinline__ float sim_dt<float>(const SimDesc& S) { r
 template <typename T> __device__ __forceinline__ T sim_L(const SimDesc& S, int a);
 template <> __device__ __forceinline__ double sim_L<double>(const SimDesc& S, int a) { return S.L[a]; }
 template <> __device__ __forceinline__ float sim_L<float>(const SimDesc& S, int a) { return S.Lf[a]; }
+template <typename T> __device__ __forceinline__ T sim_m2(const SimDesc& S);
+template <> __device__ __forceinline__ double sim_m2<double>(const SimDesc& S) { return S.m2; }
+template <> __device__ __forceinline__ float sim_m2<float>(const SimDesc& S) { return S.m2f; }
 template <typename T> __device__ __forceinline__ T sim_dx(const SimDesc& S, int a);
 template <> __device__ __forceinline__ double sim_dx<double>(const SimDesc& S, int a) { return S.dx[a]; }
 template <> __device__ __forceinline__ float sim_dx<float>(const SimDesc& S, int a) { return S.dxf[a]; }

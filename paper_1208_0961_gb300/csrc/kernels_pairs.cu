@@ -58,9 +58,39 @@ __device__ __forceinline__ T p22_of_units(T C, const T ui[3], const T uj[3])
     return mul_rn(C, v);
 }
 
+// Massive particles (m2 = m^2 > 0): v_rel is the Moller velocity
+// sqrt((p_i.p_j)^2 - m^4) / (E_i E_j), p_i.p_j = E_i E_j - p_i.p_j (3-vectors),
+// written sqrt((F - m^2)(F + m^2)) / (E_i E_j), 0 where rounding gives F < m^2.
 template <typename T>
-__device__ __forceinline__ T pair_p22(T C, const T* __restrict__ st, uint32_t pcap, uint32_t gi, uint32_t gj)
+__device__ __forceinline__ T p22_massive(T C, T m2, const T mi[3], const T mj[3])
 {
+    const T Ei = sqrt_rn(add_rn(add_rn(add_rn(mul_rn(mi[0], mi[0]), mul_rn(mi[1], mi[1])), mul_rn(mi[2], mi[2])), m2));
+    const T Ej = sqrt_rn(add_rn(add_rn(add_rn(mul_rn(mj[0], mj[0]), mul_rn(mj[1], mj[1])), mul_rn(mj[2], mj[2])), m2));
+    const T dot = add_rn(add_rn(mul_rn(mi[0], mj[0]), mul_rn(mi[1], mj[1])), mul_rn(mi[2], mj[2]));
+    const T EE = mul_rn(Ei, Ej);
+    const T F = sub_rn(EE, dot);
+    const T a = sub_rn(F, m2);
+    if (!(a > T(0))) return T(0);
+    return mul_rn(C, div_rn(sqrt_rn(mul_rn(a, add_rn(F, m2))), EE));
+}
+
+template <typename T>
+__device__ __forceinline__ void load_mom(const T* __restrict__ st, uint32_t pcap, uint32_t g, T m[3])
+{
+    m[0] = st[3 * (size_t)pcap + g];
+    m[1] = st[4 * (size_t)pcap + g];
+    m[2] = st[5 * (size_t)pcap + g];
+}
+
+template <typename T>
+__device__ __forceinline__ T pair_p22(T C, T m2, const T* __restrict__ st, uint32_t pcap, uint32_t gi, uint32_t gj)
+{
+    if (m2 > T(0)) {
+        T mi[3], mj[3];
+        load_mom<T>(st, pcap, gi, mi);
+        load_mom<T>(st, pcap, gj, mj);
+        return p22_massive<T>(C, m2, mi, mj);
+    }
     T ui[3], uj[3];
     unit_dir<T>(st, pcap, gi, ui);
     unit_dir<T>(st, pcap, gj, uj);
@@ -159,7 +189,7 @@ __device__ __forceinline__ void append_accepted(const CellCtx& cc, uint32_t i, u
 // to the cell's list.
 template <typename T, bool kMark>
 __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
-                                               uint32_t thr16, T C, const T* __restrict__ st, uint32_t pcap,
+                                               uint32_t thr16, T C, T m2, const T* __restrict__ st, uint32_t pcap,
                                                const uint4* qw, const uint2* qig, uint32_t e0,
                                                uint32_t e1, uint32_t* __restrict__ acc_count,
                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
@@ -183,7 +213,7 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
             const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
             const uint32_t rw = (r16 << 16) | (fine >> 16);
             const T u = unit_u<T>(rw);
-            const T P = pair_p22<T>(C, st, pcap, cc.cbase + i, cc.cbase + j);
+            const T P = pair_p22<T>(C, m2, st, pcap, cc.cbase + i, cc.cbase + j);
             if (u < P) append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
         }
     }
@@ -196,7 +226,7 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
 // it to the active-cell list (the small-cell path finds its cells by scanning).
 template <typename T, bool kMark, int NB>
 __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32_t step, uint32_t thr8, uint32_t thr16,
-                                          T C, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap, uint4* qw,
+                                          T C, T m2, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap, uint4* qw,
                                           uint2* qig, uint32_t* __restrict__ acc_count,
                                           unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                           uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
@@ -233,7 +263,7 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
         // up to 32 NB blocks are pushed below: drain to at most 32 first
         while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
             __syncwarp();
-            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qig, qn - 32, qn, acc_count, acc,
+            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, qn - 32, qn, acc_count, acc,
                                      acc_cap, counters, active, stats);
             __syncwarp();
             qn -= 32;
@@ -249,7 +279,7 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
     }
     if (qn) {
         __syncwarp();
-        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, st, pcap, qw, qig, 0, qn, acc_count, acc, acc_cap,
+        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, 0, qn, acc_count, acc, acc_cap,
                                  counters, active, stats);
         __syncwarp();
     }
@@ -300,8 +330,10 @@ __device__ __forceinline__ uint32_t skip_rows(const CellCtx& cc, uint32_t rb, co
     const uint32_t i = rb * kPairRows + lane;
     uint32_t cand = 0;
     if (i + 1 < cc.n) {
-        T ui[3];
-        unit_dir<T>(st, pcap, cc.cbase + i, ui);  // row particle, loaded once (coalesced over the lanes)
+        const T m2 = sim_m2<T>(S);
+        T ui[3], mi[3];
+        if (m2 > T(0)) load_mom<T>(st, pcap, cc.cbase + i, mi);
+        else unit_dir<T>(st, pcap, cc.cbase + i, ui);  // row particle, loaded once (coalesced over the lanes)
         PhiloxRow R;
         R.init(S.step, cc.lc, i, K);
         const T pm = skip_pmax<T>(S);
@@ -315,10 +347,17 @@ __device__ __forceinline__ uint32_t skip_rows(const CellCtx& cc, uint32_t rb, co
             const uint32_t j = pos + 1u + (uint32_t)G;
             ++cand;
             const T u = mul_rn(unit_u<T>(w.z), pm);
-            T uj[3];
-            unit_dir<T>(st, pcap, cc.cbase + j, uj);
-            if (u < p22_of_units<T>(C, ui, uj))
-                append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
+            T P;
+            if (m2 > T(0)) {
+                T mj[3];
+                load_mom<T>(st, pcap, cc.cbase + j, mj);
+                P = p22_massive<T>(C, m2, mi, mj);
+            } else {
+                T uj[3];
+                unit_dir<T>(st, pcap, cc.cbase + j, uj);
+                P = p22_of_units<T>(C, ui, uj);
+            }
+            if (u < P) append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
             pos = j;
         }
     }
@@ -453,7 +492,7 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
         const uint32_t rb = item - w0.x;
         const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
         const PhiloxKey& K = kOneKey ? Kp : Kl;
-        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_ig[w],
+        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_w[w], q_ig[w],
                            acc_count, acc, acc_cap, counters, active, stats);
     }
 }
@@ -513,7 +552,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
             const PhiloxKey& K = kOneKey ? Kp : Kl;
             const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
             for (uint32_t rb = 0; rb < nrb; ++rb)
-                pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), K, st, pcap, q_w[w], q_ig[w],
+                pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_w[w], q_ig[w],
                                         acc_count, acc, acc_cap, counters, active, stats);
         }
     }
@@ -560,50 +599,95 @@ template <> __device__ __forceinline__ float word_unit<float>(uint32_t w) { retu
 __device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
 
-// Lorentz factor of the pair's centre-of-mass frame, gamma = E_t / sqrt(s).
+// Invariant mass squared s of a pair of particles of mass m (m2 = m^2):
+// massless 2 E_i E_j v_rel with v_rel in the unit-vector form, massive
+// 2 m^2 + 2 (E_i E_j - p_i.p_j).  Ei, Ej receive the energies.
 template <typename R>
-__device__ __forceinline__ R pair_gamma(const R mi[3], const R mj[3])
+__device__ __forceinline__ R pair_s(R m2, const R mi[3], const R mj[3], R& Ei, R& Ej)
 {
-    const R Ei = sqrt((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]);
-    const R Ej = sqrt((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]);
-    if (!(Ei > R(0)) || !(Ej > R(0))) return R(0);
-    R d[3];
-    for (int a = 0; a < 3; ++a) d[a] = mi[a] / Ei - mj[a] / Ej;
-    const R s = ((R(2) * Ei) * Ej) * (R(0.5) * ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]));
-    return (s > R(0)) ? (Ei + Ej) / sqrt(s) : R(0);
-}
-
-// Executed pair (Sec. 2): boost to the CM frame, isotropic direction from the
-// Philox block (step, cell, i, TAG_ANGLE | j), boost back.
-// p' = p* + beta (gamma^2 / (gamma + 1) (beta . p*) + gamma E*), p2* = -p*.
-template <typename R>
-__device__ __forceinline__ bool collide_pair(const PhiloxKey& K, uint32_t step, uint32_t lc, uint32_t i, uint32_t j,
-                                             R mi[3], R mj[3])
-{
-    const R Ei = sqrt((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]);
-    const R Ej = sqrt((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]);
+    Ei = sqrt(((mi[0] * mi[0] + mi[1] * mi[1]) + mi[2] * mi[2]) + m2);
+    Ej = sqrt(((mj[0] * mj[0] + mj[1] * mj[1]) + mj[2] * mj[2]) + m2);
+    if (m2 > R(0)) {
+        const R F = Ei * Ej - ((mi[0] * mj[0] + mi[1] * mj[1]) + mi[2] * mj[2]);
+        return R(2) * m2 + R(2) * F;
+    }
     R ui[3], uj[3];
     for (int a = 0; a < 3; ++a) {
         ui[a] = (Ei > R(0)) ? mi[a] / Ei : R(0);
         uj[a] = (Ej > R(0)) ? mj[a] / Ej : R(0);
     }
     const R d0 = ui[0] - uj[0], d1 = ui[1] - uj[1], d2 = ui[2] - uj[2];
-    const R s = ((R(2) * Ei) * Ej) * (R(0.5) * ((d0 * d0 + d1 * d1) + d2 * d2));
-    if (!(s > R(0))) return false;
+    return ((R(2) * Ei) * Ej) * (R(0.5) * ((d0 * d0 + d1 * d1) + d2 * d2));
+}
+
+// Lorentz factor of the pair's centre-of-mass frame, gamma = E_t / sqrt(s).
+template <typename R>
+__device__ __forceinline__ R pair_gamma(R m2, const R mi[3], const R mj[3])
+{
+    R Ei, Ej;
+    const R s = pair_s<R>(m2, mi, mj, Ei, Ej);
+    if (!(Ei > R(0)) || !(Ej > R(0))) return R(0);
+    return (s > R(4) * m2) ? (Ei + Ej) / sqrt(s) : R(0);
+}
+
+// Executed pair (Sec. 2): boost to the CM frame, direction from the Philox
+// block (step, cell, i, TAG_ANGLE | j), boost back.  In the CM frame both
+// particles carry E* = sqrt(s)/2 and momenta +-p*, |p*| = sqrt(E*^2 - m^2);
+// p' = p* + beta (gamma^2 / (gamma + 1) (beta . p*) + gamma E*).  Isotropic
+// (mu = 0): cos t = 2 u1 - 1 about the z axis.  Screened (mu > 0):
+// dsigma/dt ~ 1/(t - mu^2)^2, t = -2 |p*|^2 (1 - cos t), x = 1 - cos t from
+// the closed-form inverse CDF with a = 2 |p*|^2, A = 1/mu^2, B = 1/(2a + mu^2):
+// x = (1/(A - u1 (A - B)) - mu^2) / a, measured from particle i's incoming
+// CM direction, azimuth about it in the basis e1 = unit(h x e), e2 = e x e1
+// (h = x^ if |e_x| < 0.9, else y^).
+template <typename R>
+__device__ __forceinline__ bool collide_pair(const PhiloxKey& K, uint32_t step, uint32_t lc, uint32_t i, uint32_t j,
+                                             R m, R mu, R mi[3], R mj[3])
+{
+    const R m2 = m * m;
+    R Ei, Ej;
+    const R s = pair_s<R>(m2, mi, mj, Ei, Ej);
+    if (!(s > R(4) * m2)) return false;
     const R rs = sqrt(s);
     const R Es = R(0.5) * rs;
+    const R pm = m2 > R(0) ? sqrt((Es - m) * (Es + m)) : Es;
     const R Et = Ei + Ej;
     const R beta[3] = {(mi[0] + mj[0]) / Et, (mi[1] + mj[1]) / Et, (mi[2] + mj[2]) / Et};
     const R gamma = Et / rs;
+    const R a = (gamma * gamma) / (gamma + R(1));
     const uint4 w = philox4x32_10(make_uint4(step, lc, i, kTagAngle | j), K);
     const R u1 = word_unit<R>(w.x), u2 = word_unit<R>(w.y);
-    const R ct = R(2) * u1 - R(1);
-    const R stt = sqrt((R(1) - ct) * (R(1) + ct));
     R sp, cp;
     sincos_t(R(2) * R(3.141592653589793) * u2, &sp, &cp);
-    const R ps[3] = {Es * (stt * cp), Es * (stt * sp), Es * ct};
+    R ps[3];
+    if (!(mu > R(0))) {
+        const R ct = R(2) * u1 - R(1);
+        const R stt = sqrt((R(1) - ct) * (R(1) + ct));
+        ps[0] = pm * (stt * cp);
+        ps[1] = pm * (stt * sp);
+        ps[2] = pm * ct;
+    } else {
+        const R bpi = (beta[0] * mi[0] + beta[1] * mi[1]) + beta[2] * mi[2];
+        const R fin = a * bpi - gamma * Ei;
+        R e[3] = {mi[0] + beta[0] * fin, mi[1] + beta[1] * fin, mi[2] + beta[2] * fin};
+        const R en = sqrt((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2]);
+        for (int q = 0; q < 3; ++q) e[q] = e[q] / en;
+        R h[3] = {R(0), R(0), R(0)};
+        if (fabs(e[0]) < R(0.9)) h[0] = R(1); else h[1] = R(1);
+        R e1[3] = {h[1] * e[2] - h[2] * e[1], h[2] * e[0] - h[0] * e[2], h[0] * e[1] - h[1] * e[0]};
+        const R n1 = sqrt((e1[0] * e1[0] + e1[1] * e1[1]) + e1[2] * e1[2]);
+        for (int q = 0; q < 3; ++q) e1[q] = e1[q] / n1;
+        const R e2[3] = {e[1] * e1[2] - e[2] * e1[1], e[2] * e1[0] - e[0] * e1[2], e[0] * e1[1] - e[1] * e1[0]};
+        const R aa = R(2) * (pm * pm);
+        const R mu2 = mu * mu;
+        const R A = R(1) / mu2, B = R(1) / (R(2) * aa + mu2);
+        R x = (R(1) / (A - u1 * (A - B)) - mu2) / aa;
+        x = x < R(0) ? R(0) : (x > R(2) ? R(2) : x);
+        const R ct = R(1) - x;
+        const R stt = sqrt(x * (R(2) - x));
+        for (int q = 0; q < 3; ++q) ps[q] = pm * (ct * e[q] + stt * (cp * e1[q] + sp * e2[q]));
+    }
     const R bp = (beta[0] * ps[0] + beta[1] * ps[1]) + beta[2] * ps[2];
-    const R a = (gamma * gamma) / (gamma + R(1));
     const R fi = a * bp + gamma * Es;
     const R fj = -a * bp + gamma * Es;
     for (int q = 0; q < 3; ++q) {
@@ -627,7 +711,7 @@ __device__ __forceinline__ int collide_state<double>(const SimDesc& S, const Phi
         mi[a] = st[(size_t)(3 + a) * pcap + gi];
         mj[a] = st[(size_t)(3 + a) * pcap + gj];
     }
-    if (collide_pair<double>(K, S.step, lc, i, j, mi, mj)) {
+    if (collide_pair<double>(K, S.step, lc, i, j, S.mass, S.mu, mi, mj)) {
         for (int a = 0; a < 3; ++a) {
             st[(size_t)(3 + a) * pcap + gi] = mi[a];
             st[(size_t)(3 + a) * pcap + gj] = mj[a];
@@ -637,7 +721,8 @@ __device__ __forceinline__ int collide_state<double>(const SimDesc& S, const Phi
 }
 
 // FP32 state: FP32 kinematics unless the CM Lorentz factor exceeds the
-// simulation's threshold, where the boost cancels badly and FP64 is used.
+// simulation's threshold, where the boost cancels badly and FP64 is used
+// (always FP64 with the screened angular distribution).
 template <>
 __device__ __forceinline__ int collide_state<float>(const SimDesc& S, const PhiloxKey& K, uint32_t lc, uint32_t i,
                                                     uint32_t j, float* __restrict__ st, uint32_t pcap, uint32_t gi,
@@ -648,17 +733,19 @@ __device__ __forceinline__ int collide_state<float>(const SimDesc& S, const Phil
         mi[a] = st[(size_t)(3 + a) * pcap + gi];
         mj[a] = st[(size_t)(3 + a) * pcap + gj];
     }
-    const float gam = pair_gamma<float>(mi, mj);
+    const float gam = pair_gamma<float>(S.m2f, mi, mj);
     int used64 = 0;
     bool ok;
-    if (gam > S.gamma_fp64 || !(gam > 0.0f)) {
+    // the screened direction is taken from the incoming CM momentum, whose
+    // boost cancels at every gamma: FP64 for every such collision
+    if (gam > S.gamma_fp64 || !(gam > 0.0f) || S.mu > 0.0) {
         double di[3], dj[3];
         for (int a = 0; a < 3; ++a) { di[a] = mi[a]; dj[a] = mj[a]; }
-        ok = collide_pair<double>(K, S.step, lc, i, j, di, dj);
+        ok = collide_pair<double>(K, S.step, lc, i, j, S.mass, S.mu, di, dj);
         for (int a = 0; a < 3; ++a) { mi[a] = (float)di[a]; mj[a] = (float)dj[a]; }
         used64 = 1;
     } else {
-        ok = collide_pair<float>(K, S.step, lc, i, j, mi, mj);
+        ok = collide_pair<float>(K, S.step, lc, i, j, (float)S.mass, (float)S.mu, mi, mj);
     }
     if (ok) {
         for (int a = 0; a < 3; ++a) {

@@ -37,6 +37,26 @@ __global__ void __launch_bounds__(256) k_keys_only(const SimDesc* __restrict__ s
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double open01(uint32_t r) { return ((double)r + 0.5) * 0x1p-32; }
 
+// Momentum magnitude of a thermal particle at temperature T.  Massless: the
+// Gamma(3, T) variate p0.  Massive (m > 0): the Juttner density
+// p^2 exp(-sqrt(p^2 + m^2)/T) by rejection from the massless one: try k draws
+// the block (STEP_INIT, g, 0, TAG_MASS | k), proposes q = -T ln(u0 u1 u2) and
+// keeps it iff u3 < exp(-(m^2 / (sqrt(q^2 + m^2) + q)) / T); after 64
+// rejected tries the last proposal is kept.
+__device__ __forceinline__ double sample_pmag(const SimDesc& S, const PhiloxKey& K, double T, uint32_t g, double p0)
+{
+    if (!(S.mass > 0.0)) return p0;
+    const double m2 = S.m2;
+    double q = p0;
+    for (uint32_t k = 0; k < 64; ++k) {
+        const uint4 w = philox4x32_10(make_uint4(kStepInit, g, 0u, kTagMass | k), K);
+        q = -T * log(open01(w.x) * open01(w.y) * open01(w.z));
+        const double acc = exp(-(m2 / (sqrt(q * q + m2) + q)) / T);
+        if (open01(w.w) < acc) break;
+    }
+    return q;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_thermal(SimDesc S, T* __restrict__ st, uint32_t pcap,
                                                       const double* __restrict__ regions, int nreg,
@@ -55,7 +75,7 @@ __global__ void __launch_bounds__(256) k_init_thermal(SimDesc S, T* __restrict__
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax)
             pos[ax] = __dadd_rn(R[ax], __dmul_rn(open01(aw[ax]), __dsub_rn(R[3 + ax], R[ax])));
-        const double E = -R[6] * log(open01(a.w) * open01(b.x) * open01(b.y));
+        const double E = sample_pmag(S, K, R[6], g, -R[6] * log(open01(a.w) * open01(b.x) * open01(b.y)));
         const double ct = 2.0 * open01(b.z) - 1.0;
         const double stt = sqrt((1.0 - ct) * (1.0 + ct));
         const double phi = 2.0 * 3.141592653589793 * open01(b.w);
@@ -102,7 +122,7 @@ __global__ void __launch_bounds__(256) k_init_hotspot(SimDesc S, T* __restrict__
         }
         const uint4 a = philox4x32_10(make_uint4(kStepInit, g, 0u, 0u), K);
         const uint4 b = philox4x32_10(make_uint4(kStepInit, g, 0u, 1u), K);
-        const double E = -Tl * log(open01(a.w) * open01(b.x) * open01(b.y));
+        const double E = sample_pmag(S, K, Tl, g, -Tl * log(open01(a.w) * open01(b.x) * open01(b.y)));
         const double ct = 2.0 * open01(b.z) - 1.0;
         const double stt = sqrt((1.0 - ct) * (1.0 + ct));
         const double phi = 2.0 * 3.141592653589793 * open01(b.w);
@@ -462,7 +482,7 @@ __global__ void __launch_bounds__(256) k_observables(SimDesc S, const T* __restr
         double se = 0.0, sx = 0.0;
         for (uint32_t k = b + threadIdx.x; k < e; k += blockDim.x) {
             const double qx = st[3 * (size_t)pcap + k], qy = st[4 * (size_t)pcap + k], qz = st[5 * (size_t)pcap + k];
-            se += sqrt((qx * qx + qy * qy) + qz * qz);
+            se += sqrt(((qx * qx + qy * qy) + qz * qz) + S.m2);
             sx += qx;
         }
         const double te = block_sum_fixed(se, red);
@@ -485,7 +505,7 @@ __global__ void __launch_bounds__(256) k_totals_partial(SimDesc S, const T* __re
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < S.np; k += stride) {
         const uint32_t g = S.p_off + k;
         const double qx = st[3 * (size_t)pcap + g], qy = st[4 * (size_t)pcap + g], qz = st[5 * (size_t)pcap + g];
-        a[0] += sqrt((qx * qx + qy * qy) + qz * qz);
+        a[0] += sqrt(((qx * qx + qy * qy) + qz * qz) + S.m2);
         a[1] += qx;
         a[2] += qy;
         a[3] += qz;

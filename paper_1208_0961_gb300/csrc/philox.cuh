@@ -94,6 +94,7 @@ constexpr uint32_t kTagMid = 0x20000000u;    // bits 23..16 of a pair's uniform
 constexpr uint32_t kTagFine = 0x40000000u;   // low 16 bits of a pair's uniform
 constexpr uint32_t kTagAngle = 0x80000000u;  // centre-of-mass direction
 constexpr uint32_t kTagSkip = 0xC0000000u;   // skip-ahead: k-th candidate draw of a row
+constexpr uint32_t kTagMass = 0x40000000u;   // sampling (first word kStepInit): massive momentum, try k
 constexpr uint32_t kStepInit = 0xFFFFFFFFu;  // first word reserved for sampling
 
 }  // namespace cuba

@@ -27,13 +27,14 @@ __device__ __forceinline__ uint32_t cell_key(const SimDesc& S, const T pos[3])
     return id[0] + (uint32_t)S.n[0] * (id[1] + (uint32_t)S.n[1] * id[2]);
 }
 
-// Free streaming x <- x + (p/E) dt (Eq. 2, c = 1, E = |p|) and elastic
+// Free streaming x <- x + (p/E) dt (Eq. 2, c = 1, E = sqrt(|p|^2 + m^2)) and elastic
 // reflection: beyond a wall the position is mirrored and that momentum
 // component flips.  Returns the number of reflections.
 template <typename T>
 __device__ __forceinline__ int stream_one(const SimDesc& S, T pos[3], T mom[3])
 {
-    const T E = sqrt_rn(add_rn(add_rn(mul_rn(mom[0], mom[0]), mul_rn(mom[1], mom[1])), mul_rn(mom[2], mom[2])));
+    const T E = sqrt_rn(
+        add_rn(add_rn(add_rn(mul_rn(mom[0], mom[0]), mul_rn(mom[1], mom[1])), mul_rn(mom[2], mom[2])), sim_m2<T>(S)));
     const T dt = sim_dt<T>(S);
     int nref = 0;
 #pragma unroll

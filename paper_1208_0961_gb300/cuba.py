@@ -39,6 +39,8 @@ class cuba_params(C.Structure):
         ("gamma_fp64", C.c_double),
         ("acceptance", C.c_int32),
         ("kappa", C.c_double),
+        ("mass", C.c_double),
+        ("mu", C.c_double),
     ]
 
 
@@ -174,7 +176,7 @@ def _ptr(x):
 
 
 def make_params(L=(10.0, 1.0, 1.0), n_cells=(100, 1, 1), dt=0.05, sigma_fm2=1.0, n_test=1.0,
-                precision=CUBA_FP64, seed=0, gamma_fp64=0.0, acceptance=0, kappa=0.0):
+                precision=CUBA_FP64, seed=0, gamma_fp64=0.0, acceptance=0, kappa=0.0, mass=0.0, mu=0.0):
     p = cuba_params()
     for a in range(3):
         p.L[a] = float(L[a])
@@ -187,6 +189,8 @@ def make_params(L=(10.0, 1.0, 1.0), n_cells=(100, 1, 1), dt=0.05, sigma_fm2=1.0,
     p.gamma_fp64 = float(gamma_fp64)
     p.acceptance = int(acceptance)
     p.kappa = float(kappa)
+    p.mass = float(mass)
+    p.mu = float(mu)
     return p
 
 

@@ -22,18 +22,19 @@ from paper_1208_0961_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0, skip=False, kappa=0.0):
+def _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, gamma_fp64=0.0, skip=False, kappa=0.0, mass=0.0, mu=0.0):
     p = cuba.make_params(L=L, n_cells=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test,
                          precision=cuba.CUBA_FP32 if fp32 else cuba.CUBA_FP64, seed=seed, gamma_fp64=gamma_fp64,
-                         acceptance=cuba.CUBA_ACCEPT_SKIP if skip else cuba.CUBA_ACCEPT_ALL_PAIRS, kappa=kappa)
+                         acceptance=cuba.CUBA_ACCEPT_SKIP if skip else cuba.CUBA_ACCEPT_ALL_PAIRS, kappa=kappa,
+                         mass=mass, mu=mu)
     op = O.make_params(L=L, n=n_cells, dt=dt, sigma_fm2=sigma_fm2, n_test=n_test, fp32=fp32, seed=seed, skip=skip,
-                       kappa=kappa)
+                       kappa=kappa, mass=mass, mu=mu)
     return p, op
 
 
 def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_index=3, small_max=None,
-                      skip=False, kappa=0.0):
-    p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, skip=skip, kappa=kappa)
+                      skip=False, kappa=0.0, mass=0.0, mu=0.0):
+    p, op = _pair(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, skip=skip, kappa=kappa, mass=mass, mu=mu)
     dtype = np.float32 if fp32 else np.float64
     st0 = st0.astype(dtype)
     n = st0.shape[1]
@@ -69,7 +70,7 @@ def _one_step_compare(L, n_cells, dt, sigma_fm2, n_test, fp32, seed, st0, step_i
     exe_g = set(tuple(x) for x in pairs[exe].tolist())
     assert exe_g == exe_o, "executed pairs differ"
     # momenta
-    E = np.sqrt((o_out[3:] ** 2).sum(axis=0))
+    E = np.sqrt((o_out[3:] ** 2).sum(axis=0) + mass * mass)
     tol = np.zeros(n)
     for c, i, j in res.executed.tolist():
         b = res.cell_start[c]
