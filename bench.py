@@ -208,13 +208,13 @@ def launches_per_step(ncells, small_max, skip=False, adaptive=False):
     """Kernels of one step: streaming histogram; per radix pass the digit
     histogram (passes after the first), 3 scan kernels and the ranking
     kernel, then (two passes or more) the gather; cell preparation + 3 scan
-    kernels; small-cell and tiled pair kernels (skip-ahead: 3 scan kernels of
-    its row blocks and its pair kernel); small-cell and per-cell resolve
-    kernels; the step counter."""
+    kernels; small-cell and tiled pair kernels and the survivor kernel
+    (skip-ahead: 3 scan kernels of its row blocks and its pair kernel);
+    small-cell and per-cell resolve kernels; the step counter."""
     p = bin_passes(ncells)
     sort = 1 + 4 * p + (p - 1) + (1 if p > 1 else 0)
     small = 1 if small_max else 0
-    pairs = 3 + 1 if skip else 1 + small
+    pairs = 3 + 1 if skip else 1 + small + 1
     return (1 if adaptive else 0) + sort + 4 + pairs + (1 + small) + 1
 
 

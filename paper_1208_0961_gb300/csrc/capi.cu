@@ -96,7 +96,7 @@ int make_desc(const cuba_params* p, SimDesc* S)
 
 void arena_free(Arena& A)
 {
-    void* ptrs[] = {A.st[0], A.st[1], A.key[0], A.key[1], A.idx[0], A.idx[1], A.cell_start, A.cell_work, A.skip_work,
+    void* ptrs[] = {A.st[0], A.st[1], A.key[0], A.key[1], A.idx[0], A.idx[1], A.cell_start, A.cell_work, A.skip_work, A.surv,
                     A.acc_count, A.acc, A.radix_hist, A.scan_tmp, A.counters, A.active, A.used_bits, A.stats,
                     A.d_sims, A.trace_keys};
     for (void* p : ptrs)
@@ -139,6 +139,10 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
     A.scan_tmp_bytes = scan_tmp_needed(pcap, ccap);
     if (!rc) rc = dalloc(&A.scan_tmp, A.scan_tmp_bytes, "scan_tmp");
     if (!rc) rc = dalloc(&A.counters, 16 * 4, "counters");
+    // survivors of the random-byte filters: about one pair in 2^16, or
+    // 2.0001 C of them (larger batches spill to in-place evaluation)
+    A.surv_cap = std::max<uint32_t>(1u << 21, (uint32_t)(pc / 2));
+    if (!rc) rc = dalloc(&A.surv, (size_t)A.surv_cap * sizeof(uint4), "survivors");
     if (!rc) rc = dalloc(&A.used_bits, (pc / 32 + 2) * 4, "used_bits");
     if (!rc) rc = dalloc(&A.stats, (size_t)simcap * kStatCount * 8, "stats");
     if (!rc) rc = dalloc(&A.d_sims, (size_t)simcap * sizeof(SimDesc), "sims");

@@ -187,11 +187,13 @@ struct Arena {
     uint32_t* acc_count = nullptr;      // ccap
     unsigned long long* acc = nullptr;  // accepted (i << 32 | j), per-cell segments
     uint64_t acc_capacity = 0;
+    uint4* surv = nullptr;              // survivors of both random-byte filters, counters[3] of them
+    uint32_t surv_cap = 0;
     uint32_t* radix_hist = nullptr;     // digit histograms and their scan, 2 kBinBins * tiles
     uint32_t radix_hist_cap = 0;
     void* scan_tmp = nullptr;           // scan partial sums
     size_t scan_tmp_bytes = 0;
-    uint32_t* counters = nullptr;       // [0] pair work counter, [1] error bits, [2] active cells
+    uint32_t* counters = nullptr;       // [0] pair work counter, [1] error bits, [2] active cells, [3] survivors
     uint32_t* active = nullptr;         // ccap: cells with at least one accepted pair
     uint32_t* used_bits = nullptr;      // pcap / 32 + 1: greedy bitmap for cells too big for smem
     unsigned long long* stats = nullptr;  // simcap * kStatCount

@@ -180,6 +180,119 @@ __device__ __forceinline__ void append_accepted(const CellCtx& cc, uint32_t i, u
     }
 }
 
+// Survivors of both random-byte filters (r16 <= thr16, about one pair in
+// 2^16) need their low 16 random bits and the momenta: they are collected
+// per warp in shared memory and written in bulk to a global list, which
+// k_pair_finish evaluates with one thread per survivor, so that no warp of
+// the pair tile waits on their momentum loads.  A record is (cell, i, j,
+// r16 | kMark << 31).  Where a buffer is full the survivor is evaluated in
+// place: the decisions are the same either way.
+constexpr uint32_t kSurvBuf = 64;     // per-warp shared-memory survivors
+constexpr uint32_t kSurvFlush = 32;   // flushed to the global list from this many
+
+template <typename T, bool kMark>
+__device__ __forceinline__ void eval_survivor(const CellCtx& cc, const PhiloxKey& K, uint32_t step, T C, T m2,
+                                              const T* __restrict__ st, uint32_t pcap, uint32_t i, uint32_t j,
+                                              uint32_t r16, uint32_t* __restrict__ acc_count,
+                                              unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                              uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                              unsigned long long* __restrict__ stats)
+{
+    const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
+    const uint32_t rw = (r16 << 16) | (fine >> 16);
+    const T u = unit_u<T>(rw);
+    const T P = pair_p22<T>(C, m2, st, pcap, cc.cbase + i, cc.cbase + j);
+    if (u < P) append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
+}
+
+// A survivor record evaluated on its own (its cell's context reloaded).
+template <typename T, bool kOneKey>
+__device__ __forceinline__ void finish_survivor(uint4 e, const SimDesc* __restrict__ sims, int nsims,
+                                                const T* __restrict__ st, uint32_t pcap,
+                                                const uint32_t* __restrict__ cell_start,
+                                                const uint2* __restrict__ work, uint32_t* __restrict__ acc_count,
+                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                unsigned long long* __restrict__ stats, const PhiloxKey& Kp)
+{
+    CellCtx cc;
+    cc.c = e.x;
+    cc.s = sim_of_cell(sims, nsims, e.x);
+    const SimDesc& S = sims[cc.s];
+    cc.slot = S.stat_slot;
+    cc.lc = e.x - S.cell_off;
+    cc.cbase = cell_start[e.x];
+    cc.n = cell_start[e.x + 1] - cc.cbase;
+    const uint2 w0 = work[e.x], w1 = work[e.x + 1];
+    cc.list0 = w0.y;
+    cc.room = w1.y - w0.y;
+    const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
+    const PhiloxKey& K = kOneKey ? Kp : Kl;
+    if (e.w >> 31)
+        eval_survivor<T, true>(cc, K, S.step, sim_C<T>(S), sim_m2<T>(S), st, pcap, e.y, e.z, e.w & 0xFFFFu, acc_count,
+                               acc, acc_cap, counters, active, stats);
+    else
+        eval_survivor<T, false>(cc, K, S.step, sim_C<T>(S), sim_m2<T>(S), st, pcap, e.y, e.z, e.w & 0xFFFFu,
+                                acc_count, acc, acc_cap, counters, active, stats);
+}
+
+// The warp's buffer count gets this bit once the global list is full: every
+// later push then finds pos >= kSurvBuf and evaluates in place, and the
+// records left in the buffer are evaluated when the warp finishes.
+constexpr uint32_t kSurvFull = 0x80000000u;
+
+// Warp-collective: move the warp's buffered survivors to the global list
+// (counters[3] counts them).  Records past its capacity stay at the front of
+// the buffer, *left of them, and the buffer is marked full.
+__device__ __forceinline__ void flush_survivors(uint4* sv, uint32_t* svn, uint32_t* left, uint4* __restrict__ surv,
+                                                uint32_t surv_cap, uint32_t* __restrict__ counters)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    __syncwarp();
+    const uint32_t v = *svn;
+    if (v == 0 || (v & kSurvFull)) return;
+    const uint32_t n = min(v, kSurvBuf);
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&counters[3], n);
+    base = __shfl_sync(kFull, base, 0);
+    const uint32_t fit = base >= surv_cap ? 0u : min(n, surv_cap - base);
+    uint4 e0 = make_uint4(0, 0, 0, 0), e1 = e0;
+    if (lane < n) e0 = sv[lane];
+    if (lane + 32 < n) e1 = sv[lane + 32];
+    __syncwarp();
+    if (lane < n) {
+        if (lane < fit) surv[base + lane] = e0; else sv[lane - fit] = e0;
+    }
+    if (lane + 32 < n) {
+        if (lane + 32 < fit) surv[base + lane + 32] = e1; else sv[lane + 32 - fit] = e1;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        *svn = fit < n ? kSurvFull : 0u;
+        *left = n - fit;
+    }
+    __syncwarp();
+}
+
+// Warp-collective, when the warp has no more work: flush, then evaluate in
+// place whatever the full global list could not take.
+template <typename T, bool kOneKey>
+__device__ __forceinline__ void drain_survivors(uint4* sv, uint32_t* svn, uint32_t* left, uint4* __restrict__ surv,
+                                                uint32_t surv_cap, const SimDesc* __restrict__ sims, int nsims,
+                                                const T* __restrict__ st, uint32_t pcap,
+                                                const uint32_t* __restrict__ cell_start,
+                                                const uint2* __restrict__ work, uint32_t* __restrict__ acc_count,
+                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                unsigned long long* __restrict__ stats, const PhiloxKey& Kp)
+{
+    flush_survivors(sv, svn, left, surv, surv_cap, counters);
+    const uint32_t n = *left;
+    for (uint32_t k = threadIdx.x & 31; k < n; k += 32)
+        finish_survivor<T, kOneKey>(sv[k], sims, nsims, st, pcap, cell_start, work, acc_count, acc, acc_cap, counters,
+                                    active, stats, Kp);
+}
+
 // Resolve queued blocks [e0, e1) of the warp, one block per lane.  The bytes
 // <= thr8 at real pairs j (i < j < n) are first refined by the pair's middle
 // byte, drawn from the block (step, cell, i, TAG_MID | g) shared by the 16
@@ -191,7 +304,8 @@ template <typename T, bool kMark>
 __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
                                                uint32_t thr16, T C, T m2, const T* __restrict__ st, uint32_t pcap,
                                                const uint4* qw, const uint2* qig, uint32_t e0,
-                                               uint32_t e1, uint32_t* __restrict__ acc_count,
+                                               uint32_t e1, uint4* sv, uint32_t* svn,
+                                               uint32_t* __restrict__ acc_count,
                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                                uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
                                                unsigned long long* __restrict__ stats)
@@ -210,11 +324,12 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
             const uint32_t r16 = (block_byte(r, bit) << 8) | block_byte(mb, bit);
             if (r16 > thr16) continue;
             const uint32_t j = 16u * g + bit;
-            const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
-            const uint32_t rw = (r16 << 16) | (fine >> 16);
-            const T u = unit_u<T>(rw);
-            const T P = pair_p22<T>(C, m2, st, pcap, cc.cbase + i, cc.cbase + j);
-            if (u < P) append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
+            const uint32_t pos = atomicAdd(svn, 1u);
+            if (pos < kSurvBuf)
+                sv[pos] = make_uint4(cc.c, i, j, r16 | (kMark ? 0x80000000u : 0u));
+            else
+                eval_survivor<T, kMark>(cc, K, step, C, m2, st, pcap, i, j, r16, acc_count, acc, acc_cap, counters,
+                                        active, stats);
         }
     }
 }
@@ -227,7 +342,8 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
 template <typename T, bool kMark, int NB>
 __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32_t step, uint32_t thr8, uint32_t thr16,
                                           T C, T m2, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap, uint4* qw,
-                                          uint2* qig, uint32_t* __restrict__ acc_count,
+                                          uint2* qig, uint4* sv, uint32_t* svn,
+                                          uint32_t* __restrict__ acc_count,
                                           unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                           uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
                                           unsigned long long* __restrict__ stats)
@@ -263,7 +379,7 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
         // up to 32 NB blocks are pushed below: drain to at most 32 first
         while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
             __syncwarp();
-            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, qn - 32, qn, acc_count, acc,
+            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, qn - 32, qn, sv, svn, acc_count, acc,
                                      acc_cap, counters, active, stats);
             __syncwarp();
             qn -= 32;
@@ -279,7 +395,7 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
     }
     if (qn) {
         __syncwarp();
-        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, 0, qn, acc_count, acc, acc_cap,
+        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, 0, qn, sv, svn, acc_count, acc, acc_cap,
                                  counters, active, stats);
         __syncwarp();
     }
@@ -442,13 +558,17 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
                 const uint32_t* __restrict__ cell_start, const uint2* __restrict__ work, uint32_t ncells,
                 uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc, uint64_t acc_cap,
                 uint32_t* __restrict__ counters, uint32_t* __restrict__ active, unsigned long long* __restrict__ stats,
-                const PhiloxKey Kp)
+                uint4* __restrict__ surv, uint32_t surv_cap, const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
     __shared__ uint4 q_w[kWarps][queue_cap(NB)];
     __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
+    __shared__ uint4 s_v[kWarps][kSurvBuf];
+    __shared__ uint32_t s_vn[kWarps], s_left[kWarps];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = threadIdx.x & 31;
+    if (lane == 0) s_vn[w] = s_left[w] = 0;
+    __syncwarp();
     const uint32_t total = work[ncells].x;
     if ((uint64_t)work[ncells].y > acc_cap) {
         // the lists of this step do not fit the allocation: report, do nothing
@@ -492,9 +612,14 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
         const uint32_t rb = item - w0.x;
         const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
         const PhiloxKey& K = kOneKey ? Kp : Kl;
-        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_w[w], q_ig[w],
-                           acc_count, acc, acc_cap, counters, active, stats);
+        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_w[w],
+                               q_ig[w], s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active, stats);
+        __syncwarp();
+        if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
+            flush_survivors(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, counters);
     }
+    drain_survivors<T, kOneKey>(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, sims, nsims, st, pcap, cell_start, work,
+                                acc_count, acc, acc_cap, counters, active, stats, Kp);
 }
 
 // Small cells (2 <= n <= small_max): one warp per cell, all its rows, found
@@ -511,12 +636,17 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
                                                              uint32_t* __restrict__ counters,
                                                              uint32_t* __restrict__ active,
                                                              unsigned long long* __restrict__ stats,
+                                                             uint4* __restrict__ surv, uint32_t surv_cap,
                                                              const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
     __shared__ uint4 q_w[kWarps][queue_cap(NB)];
     __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
+    __shared__ uint4 s_v[kWarps][kSurvBuf];
+    __shared__ uint32_t s_vn[kWarps], s_left[kWarps];
     const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) s_vn[w] = s_left[w] = 0;
+    __syncwarp();
     if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kWarps;
@@ -552,10 +682,36 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
             const PhiloxKey& K = kOneKey ? Kp : Kl;
             const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
             for (uint32_t rb = 0; rb < nrb; ++rb)
-                pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_w[w], q_ig[w],
-                                        acc_count, acc, acc_cap, counters, active, stats);
+                pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap,
+                                        q_w[w], q_ig[w], s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active,
+                                        stats);
+            __syncwarp();
+            if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
+                flush_survivors(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, counters);
         }
     }
+    drain_survivors<T, kOneKey>(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, sims, nsims, st, pcap, cell_start, work,
+                                acc_count, acc, acc_cap, counters, active, stats, Kp);
+}
+
+// The survivors the pair kernels collected: one thread per record.
+template <typename T, bool kOneKey>
+__global__ void __launch_bounds__(256) k_pair_finish(const SimDesc* __restrict__ sims, int nsims,
+                                                     const T* __restrict__ st, uint32_t pcap,
+                                                     const uint32_t* __restrict__ cell_start,
+                                                     const uint2* __restrict__ work, uint32_t ncells,
+                                                     uint32_t* __restrict__ acc_count,
+                                                     unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                     uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                     unsigned long long* __restrict__ stats,
+                                                     const uint4* __restrict__ surv, uint32_t surv_cap,
+                                                     const PhiloxKey Kp)
+{
+    if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
+    const uint32_t n = min(counters[3], surv_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        finish_survivor<T, kOneKey>(surv[k], sims, nsims, st, pcap, cell_start, work, acc_count, acc, acc_cap,
+                                    counters, active, stats, Kp);
 }
 
 // ---------------------------------------------------------------------------
@@ -1051,7 +1207,7 @@ static void launch_small(const Arena& A, cudaStream_t st)
 {
     k_pair_small<T, kOneKey, NB><<<small_grid<T, kOneKey, NB>(), kPairThreads, 0, st>>>(
         A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.small_max,
-        A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
+        A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.surv, A.surv_cap, A.key_sched);
 }
 
 template <typename T, bool kOneKey, int NB>
@@ -1059,7 +1215,15 @@ static void launch_tile(const Arena& A, cudaStream_t st)
 {
     k_pair_tile<T, kOneKey, NB><<<pair_grid<T, kOneKey, NB>(), kPairThreads, 0, st>>>(
         A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count, A.acc,
-        A.acc_capacity, A.counters, A.active, A.stats, A.key_sched);
+        A.acc_capacity, A.counters, A.active, A.stats, A.surv, A.surv_cap, A.key_sched);
+}
+
+template <typename T, bool kOneKey>
+static void launch_finish(const Arena& A, cudaStream_t st)
+{
+    k_pair_finish<T, kOneKey><<<(unsigned)(sm_count() * 4), 256, 0, st>>>(
+        A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count, A.acc,
+        A.acc_capacity, A.counters, A.active, A.stats, A.surv, A.surv_cap, A.key_sched);
 }
 
 template <typename T, bool kOneKey>
@@ -1080,6 +1244,7 @@ static void launch_pairs(const Arena& A, cudaStream_t st)
         launch_tile<T, kOneKey, 2>(A, st);
     else
         launch_tile<T, kOneKey, 4>(A, st);
+    launch_finish<T, kOneKey>(A, st);
 }
 
 int launch_pair_tile(const Arena& A, cudaStream_t st)

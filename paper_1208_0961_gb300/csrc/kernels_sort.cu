@@ -415,6 +415,7 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
     if (t0 == 0) {
         counters[0] = 0;  // pair work counter
         counters[2] = 0;  // active cells
+        counters[3] = 0;  // survivors of the random-byte filters
         work[ncells] = make_uint2(0, 0);
         if (skip_work) skip_work[ncells] = 0;
     }

@@ -80,9 +80,9 @@ def test_launch_count():
     # one 11-bit pass up to 2048 cells, two up to 2^22
     assert bench.bin_passes(1) == 1 and bench.bin_passes(2000) == 1 and bench.bin_passes(2048) == 1
     assert bench.bin_passes(2049) == 2 and bench.bin_passes(128 ** 3) == 2 and bench.bin_passes(1 << 23) == 3
-    # counted against the ncu launch lists of one step: 12 (16 M, 2000 cells,
-    # no small-cell kernels) and 20 (64 M, 128^3 cells, small-cell kernels)
-    assert bench.launches_per_step(2000, 0) == 12
-    assert bench.launches_per_step(128 ** 3, 64) == 20
+    # counted against the ncu launch lists of one step: 13 (16 M, 2000 cells,
+    # no small-cell kernels) and 21 (64 M, 128^3 cells, small-cell kernels)
+    assert bench.launches_per_step(2000, 0) == 13
+    assert bench.launches_per_step(128 ** 3, 64) == 21
     # skip-ahead (15 per step of the 16 M workload in its ncu launch list)
     assert bench.launches_per_step(2000, 0, skip=True) == 15
