@@ -129,8 +129,9 @@ constexpr int kPairThreads = 256;
 // Launch shape of the pair kernels: Philox blocks a lane draws per loop
 // iteration (tile: 4 or 2, warp-per-small-cell: 2 or 1; chosen at run time,
 // by the autotuner) and the register budget.  With one simulation the round
-// keys are kernel parameters (constant-bank operands) and four blocks run
-// uncapped (about 126 registers, two blocks of 256 per SM); with several
+// keys are kernel parameters (constant-bank operands) and the kernel runs
+// uncapped (94 registers in FP32, two blocks of 256 per SM: measured faster
+// than 80 registers and three blocks, or 64 and four); with several
 // simulations each warp holds its cell's round keys in registers, capped at
 // 128 (four blocks) or 80 (two).
 template <bool kOneKey, int NB>

@@ -13,8 +13,9 @@
 // evaluate P22.  The decision is the same as testing every pair in full.
 // Work unit: one warp takes 32 rows of one cell (lane = row) and walks the
 // row's column blocks; blocks with a small byte are queued per warp in shared
-// memory and resolved together, one block per lane.  Accepted pairs go to the
-// cell's segment of the list.
+// memory and resolved together, one block per lane.  Survivors of both bytes
+// are collected per warp and evaluated by k_pair_finish, one per thread.
+// Accepted pairs go to the cell's segment of the list.
 //
 // k_resolve (A6, A7): per cell with accepted pairs — sort the list
 // lexicographically (bitonic network in shared memory), take the greedy
@@ -146,19 +147,32 @@ struct CellCtx {
     uint32_t slot;    // its counters row
 };
 
-// Store a queue entry (block r, row and group ig) iff p, without a branch.
-__device__ __forceinline__ void st_shared_if(bool p, uint4* w, uint4 r, uint2 ig, uint2* wig)
+// Push a block onto the warp's queue iff its test word x has a bit of
+// 0x80808080 set: one predicate feeds the ballot and the two predicated
+// shared-memory stores (block r at qw_s + 16 slot, (i, g) at qig_s + 8 slot).
+// Returns the warp's new queue length.
+__device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t qn, uint32_t qw_s, uint32_t qig_s,
+                                               uint4 r, uint32_t i, uint32_t g)
 {
-    const uint32_t aw = (uint32_t)__cvta_generic_to_shared(w);
-    const uint32_t ai = (uint32_t)__cvta_generic_to_shared(wig);
+    uint32_t qn_out;
     asm volatile(
-        "{\n\t.reg .pred q;\n\t"
-        "setp.ne.u32 q, %0, 0;\n\t"
-        "@q st.shared.v4.u32 [%1], {%2, %3, %4, %5};\n\t"
-        "@q st.shared.v2.u32 [%6], {%7, %8};\n\t}"
-        :
-        : "r"((uint32_t)p), "r"(aw), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(ai), "r"(ig.x), "r"(ig.y)
+        "{\n\t.reg .pred p;\n\t.reg .b32 t, b, s, a;\n\t"
+        "and.b32 t, %1, 0x80808080;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "vote.sync.ballot.b32 b, p, 0xffffffff;\n\t"
+        "and.b32 t, b, %2;\n\t"
+        "popc.b32 t, t;\n\t"
+        "add.u32 s, %3, t;\n\t"
+        "popc.b32 t, b;\n\t"
+        "add.u32 %0, %3, t;\n\t"
+        "mad.lo.u32 a, s, 16, %4;\n\t"
+        "@p st.shared.v4.u32 [a], {%6, %7, %8, %9};\n\t"
+        "mad.lo.u32 a, s, 8, %5;\n\t"
+        "@p st.shared.v2.u32 [a], {%10, %11};\n\t}"
+        : "=r"(qn_out)
+        : "r"(x), "r"(lt), "r"(qn), "r"(qw_s), "r"(qig_s), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g)
         : "memory");
+    return qn_out;
 }
 
 // Append accepted pair (i, j) to its cell's list; kMark: the cell's first
@@ -357,40 +371,32 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
     R.init(step, cc.lc, i, K);
     const uint32_t gfirst = (rb * kPairRows + 1) >> 4;
     const uint32_t glast = (cc.n - 1) >> 4;
-    // Some byte of a word x is below m = thr8 + 1 iff (x - m 0x01010101) & ~x
-    // has a bit 7 set (a borrow only adds flags above a true one, so the
-    // "any" answer is exact); thr8 >= 128 queues every block.
-    const bool all_hit = thr8 >= 128u;
-    const uint32_t t8 = 0x01010101u * (thr8 + 1u);
+    // Some byte of a word x is below m = thr8 + 1 <= 128 iff (x - m 0x01010101)
+    // & ~x has a bit 7 set (a borrow only adds flags above a true one, so the
+    // "any" answer is exact).  Rows without partners test against m = 0,
+    // which flags nothing; thr8 >= 128 flags every block of a row with
+    // partners.  Blocks of pairs outside i < j < n (before the row's diagonal
+    // or past the cell's end) may be queued: the resolve drops their columns.
+    const uint32_t t8 = row_ok ? 0x01010101u * (thr8 + 1u) : 0u;
+    const uint32_t x0 = (row_ok && thr8 >= 128u) ? 0x80000000u : 0u;
+    const uint32_t qw_s = (uint32_t)__cvta_generic_to_shared(qw);
+    const uint32_t qig_s = (uint32_t)__cvta_generic_to_shared(qig);
     uint32_t qn = 0;  // warp-uniform number of queued blocks
     for (uint32_t g = gfirst; g <= glast; g += NB) {
-        uint4 r[NB];
-        bool h[NB];
-        unsigned bal[NB];
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            // a group past the row's end is drawn but never queued
-            r[q] = R.block(g + q, K);
-            const uint32_t x = ((r[q].x - t8) & ~r[q].x) | ((r[q].y - t8) & ~r[q].y) | ((r[q].z - t8) & ~r[q].z) |
-                               ((r[q].w - t8) & ~r[q].w);
-            h[q] = row_ok & (g + q <= glast) & (all_hit | ((x & 0x80808080u) != 0u));
-            bal[q] = __ballot_sync(kFull, h[q]);
-        }
         // up to 32 NB blocks are pushed below: drain to at most 32 first
         while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
             __syncwarp();
-            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, qn - 32, qn, sv, svn, acc_count, acc,
-                                     acc_cap, counters, active, stats);
+            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, qn - 32, qn, sv, svn,
+                                     acc_count, acc, acc_cap, counters, active, stats);
             __syncwarp();
             qn -= 32;
         }
-        // branch-free push: predicated shared-memory stores of the lanes
-        // with a candidate block
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const uint32_t slot = qn + (uint32_t)__popc(bal[q] & lt);
-            st_shared_if(h[q], &qw[slot], r[q], make_uint2(i, g + q), &qig[slot]);
-            qn += (uint32_t)__popc(bal[q]);
+            const uint4 r = R.block(g + q, K);
+            const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
+                               ((r.w - t8) & ~r.w) | x0;
+            qn = queue_push(x, lt, qn, qw_s, qig_s, r, i, g + q);
         }
     }
     if (qn) {

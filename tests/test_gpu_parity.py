@@ -117,6 +117,21 @@ def test_large_accepted_list_uses_global_sort_path():
     assert na > 4096
 
 
+def test_survivors_beyond_the_global_list():
+    # one cell, C = 0.45: the byte filters pass about 90 % of the 2.9 M pairs,
+    # more survivors than the 2^21-record list holds, so the pair kernel also
+    # evaluates the overflow in place (shared-memory and global)
+    L = (0.5, 0.5, 0.5)
+    regs = [((0.0, 0.0, 0.0), L, 0.4)]
+    st0 = W.thermal_state(2400, regs, seed=13)
+    C = 0.45
+    dt, n_test = 0.1, 1.0
+    sigma = C * n_test * (0.5 ** 3) / dt
+    for fp32 in (False, True):
+        na, ne = _one_step_compare(L, (1, 1, 1), dt, sigma, n_test, fp32, 21, st0)
+        assert na > 2 ** 20 and ne > 1000
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 33, 4097])
 def test_tiny_and_ragged_sizes(n):
     L = (1.0, 1.0, 1.0)
