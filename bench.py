@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=int, default=1, help="pick the collision launch shape before timing")
+    ap.add_argument("--shape", default=None,
+                    help="small_max,small_blocks,tile_blocks: set the collision launch shape (no autotuning)")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     return ap.parse_args()
@@ -504,10 +506,12 @@ def main():
     cuba.cuba_step(sim.h, args.warmup, stream)
     torch.cuda.synchronize()
     tuned = None
-    if args.autotune:
+    tune_ms = None
+    if args.shape:
+        sm, sb, tb = (int(v) for v in args.shape.split(","))
+        cuba.cuba_set_launch_shape(sim.h, sm, sb, tb)
+    elif args.autotune:
         tuned, tune_ms = cuba.cuba_autotune_shape(sim.h, 2, stream)
-    else:
-        tune_ms = None
 
     t_sim0 = cuba.cuba_get_time(sim.h)[0]
     clocks = ClockSampler(torch.cuda.current_device())

@@ -241,7 +241,7 @@ int cuba_autotune(cuba_sim* sim, int n_steps, int32_t* chosen, double* ms_per_ca
  * The whole launch shape of the collision step: small_max as above, and the
  * Philox blocks a lane draws per loop iteration in the warp-per-cell pair
  * kernel (small_blocks: 1 or 2, default 2) and in the 32-row item kernel
- * (tile_blocks: 2 or 4, default 4).  Results do not depend on it.
+ * (tile_blocks: 2, 4 or 8, default 4).  Results do not depend on it.
  */
 typedef struct cuba_launch_shape {
     int32_t small_max;
@@ -255,12 +255,12 @@ int cuba_get_launch_shape(const cuba_sim* sim, cuba_launch_shape* shape);
 /*
  * Autotuner of the whole shape, by coordinates: small_max over the eight
  * candidates of cuba_autotune, then small_blocks in {1, 2}, then tile_blocks
- * in {2, 4}, each candidate timed over n_steps steps from the same saved
+ * in {2, 4, 8}, each candidate timed over n_steps steps from the same saved
  * state (the simulation does not advance); the fastest value of each
  * coordinate is kept before the next.  *chosen (optional) receives the shape,
- * ms_per_candidate (optional, host, 12 doubles) the device time per step of
+ * ms_per_candidate (optional, host, 13 doubles) the device time per step of
  * the eight small_max candidates, then small_blocks 1, 2, then tile_blocks
- * 2, 4.  Synchronous; allocates a temporary copy of the state.
+ * 2, 4, 8.  Synchronous; allocates a temporary copy of the state.
  */
 int cuba_autotune_shape(cuba_sim* sim, int n_steps, cuba_launch_shape* chosen, double* ms_per_candidate,
                         void* stream);

@@ -370,7 +370,7 @@ static const int kTuneCount = (int)(sizeof(kTuneCandidates) / sizeof(kTuneCandid
 // restore that state and keep the fastest threshold; with shape_too, then the
 // blocks per iteration of the small-cell and the item pair kernel, in that
 // order.  The simulations do not advance.  ms (optional) receives the
-// timings in candidate order (kTuneCount, then 2 + 2 with shape_too).
+// timings in candidate order (kTuneCount, then 2 + 3 with shape_too).
 static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms, bool shape_too)
 {
     if (n_steps < 1) return fail(CUBA_ERR_INVALID, "n_steps must be >= 1");
@@ -433,7 +433,7 @@ static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, d
     A.small_max = rc ? keep : (uint32_t)best_v;
     // coordinates 2 and 3: blocks per iteration of the two pair kernels
     if (shape_too && !rc) {
-        const uint32_t small_c[2] = {1u, 2u}, tile_c[2] = {2u, 4u};
+        const uint32_t small_c[2] = {1u, 2u}, tile_c[3] = {2u, 4u, 8u};
         const uint32_t keep_s = A.small_nb, keep_t = A.tile_nb;
         double bs = 1e300, bt = 1e300;
         uint32_t vs = keep_s, vt = keep_t;
@@ -445,7 +445,7 @@ static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, d
             if (!rc && t < bs) { bs = t; vs = small_c[k]; }
         }
         A.small_nb = rc ? keep_s : vs;
-        for (int k = 0; k < 2 && !rc; ++k) {
+        for (int k = 0; k < 3 && !rc; ++k) {
             A.tile_nb = tile_c[k];
             double t = 0.0;
             rc = time_shape(&t);
@@ -481,8 +481,8 @@ int set_launch_shape(Arena& A, const cuba_launch_shape* shape)
     if (!shape) return fail(CUBA_ERR_INVALID, "shape is NULL");
     if (shape->small_blocks != 1 && shape->small_blocks != 2)
         return fail(CUBA_ERR_INVALID, "small_blocks must be 1 or 2");
-    if (shape->tile_blocks != 2 && shape->tile_blocks != 4)
-        return fail(CUBA_ERR_INVALID, "tile_blocks must be 2 or 4");
+    if (shape->tile_blocks != 2 && shape->tile_blocks != 4 && shape->tile_blocks != 8)
+        return fail(CUBA_ERR_INVALID, "tile_blocks must be 2, 4 or 8");
     int rc = set_small_max(A, shape->small_max);
     if (rc) return rc;
     A.small_nb = (uint32_t)shape->small_blocks;

@@ -127,16 +127,17 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kPairRows = 32;
 constexpr int kPairThreads = 256;
 // Launch shape of the pair kernels: Philox blocks a lane draws per loop
-// iteration (tile: 4 or 2, warp-per-small-cell: 2 or 1; chosen at run time,
-// by the autotuner) and the register budget.  With one simulation the round
-// keys are kernel parameters (constant-bank operands) and the kernel runs
+// iteration (tile: 8, 4 or 2, warp-per-small-cell: 2 or 1; chosen at run
+// time, by the autotuner) and the register budget.  With one simulation the
+// round keys are kernel parameters (constant-bank operands): four blocks run
 // uncapped (94 registers in FP32, two blocks of 256 per SM: measured faster
-// than 80 registers and three blocks, or 64 and four); with several
-// simulations each warp holds its cell's round keys in registers, capped at
-// 128 (four blocks) or 80 (two).
+// than 80 registers and three blocks, or 64 and four), eight capped at two
+// blocks of 256 per SM (124 registers in FP32).  With several simulations
+// each warp holds its cell's round keys in registers, capped at 128 (four or
+// eight blocks) or 80 (two).
 template <bool kOneKey, int NB>
 struct PairShape {
-    static constexpr int min_blocks = kOneKey ? 1 : (NB >= 4 ? 2 : 3);  // resident blocks per SM targeted
+    static constexpr int min_blocks = kOneKey ? (NB >= 8 ? 2 : 1) : (NB >= 4 ? 2 : 3);  // resident blocks per SM
 };
 // Queued Philox blocks per warp for nb blocks per iteration.
 __host__ __device__ constexpr int queue_cap(int nb) { return 32 + 32 * nb; }

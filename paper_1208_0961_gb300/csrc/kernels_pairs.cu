@@ -1248,8 +1248,10 @@ static void launch_pairs(const Arena& A, cudaStream_t st)
     }
     if (A.tile_nb == 2)
         launch_tile<T, kOneKey, 2>(A, st);
-    else
+    else if (A.tile_nb == 4)
         launch_tile<T, kOneKey, 4>(A, st);
+    else
+        launch_tile<T, kOneKey, 8>(A, st);
     launch_finish<T, kOneKey>(A, st);
 }
 
@@ -1278,6 +1280,10 @@ int kernels_init()
             cudaSuccess)
         return -1;
     if (bin_kernels_init()) return -1;
+    pair_grid<double, false, 8>();
+    pair_grid<float, false, 8>();
+    pair_grid<double, true, 8>();
+    pair_grid<float, true, 8>();
     pair_grid<double, false, 4>();
     pair_grid<float, false, 4>();
     pair_grid<double, true, 4>();

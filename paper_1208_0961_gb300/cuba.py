@@ -332,7 +332,7 @@ def cuba_get_small_max(sim):
 
 
 SHAPE_CANDIDATES = tuple("small_max=%d" % v for v in TUNE_CANDIDATES) + (
-    "small_blocks=1", "small_blocks=2", "tile_blocks=2", "tile_blocks=4")
+    "small_blocks=1", "small_blocks=2", "tile_blocks=2", "tile_blocks=4", "tile_blocks=8")
 
 
 def _shape_dict(sh):

@@ -45,7 +45,7 @@ def test_autotune_leaves_state_and_results_unchanged():
         b.close()
 
 
-@pytest.mark.parametrize("small_blocks,tile_blocks", [(1, 2), (1, 4), (2, 2)])
+@pytest.mark.parametrize("small_blocks,tile_blocks", [(1, 2), (1, 4), (2, 2), (2, 8)])
 def test_launch_shapes_give_identical_steps(small_blocks, tile_blocks):
     """Every blocks-per-iteration shape of the two pair kernels steps a
     mixed-occupancy state (small cells and 32-row items) to the same bits."""
@@ -74,8 +74,8 @@ def test_autotune_shape_leaves_state_unchanged():
         before = a.get_state()
         shape, ms = cuba.cuba_autotune_shape(a.h, 2)
         assert shape["small_max"] in cuba.TUNE_CANDIDATES
-        assert shape["small_blocks"] in (1, 2) and shape["tile_blocks"] in (2, 4)
-        assert len(ms) == 12 and all(v > 0 for v in ms.values())
+        assert shape["small_blocks"] in (1, 2) and shape["tile_blocks"] in (2, 4, 8)
+        assert len(ms) == 13 and all(v > 0 for v in ms.values())
         assert cuba.cuba_get_launch_shape(a.h) == shape
         assert np.array_equal(a.get_state(), before)
         assert cuba.cuba_get_step(a.h) == 1
@@ -86,6 +86,6 @@ def test_autotune_shape_leaves_state_unchanged():
         with pytest.raises(cuba.CubaError):
             cuba.cuba_set_launch_shape(c.h, 32, 3, 4)
         with pytest.raises(cuba.CubaError):
-            cuba.cuba_set_launch_shape(c.h, 32, 2, 8)
+            cuba.cuba_set_launch_shape(c.h, 32, 2, 6)
     finally:
         c.close()
