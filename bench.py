@@ -542,21 +542,25 @@ def main():
     pair_ms = phase[3] / max(1, args.profile_steps)
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    # pair tile: integer-issue bound.  Algorithmic work per 16-pair Philox
-    # block: 16 wide multiplies + 18 xors (rounds after the row-invariant
-    # part) + 9 ops of the byte test = 43 lane-ops, i.e. 43/16 per pair test.
+    # pair tile: bound by the integer multiply pipe.  Every pair test costs
+    # one 32x32->64 multiply (16 per 16-pair Philox block once the
+    # row-invariant part of rounds 1-3 is hoisted); the FMA-heavy pipe issues
+    # them at 32 lanes per clock per SM, so the ceiling is n_SM x 32 x f_SM
+    # pair tests/s.  The issue-slot view (43 algorithmic lane-ops per block:
+    # 16 multiplies, 18 xors, 9 for the byte test, against 128 lanes per clock
+    # per SM) and the FP32 view are reported beside it.
     ops_per_pair = 43.0 / 16.0
     pair_s = pair_ms / 1000.0
     peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12
     achieved_tops = pairs_per_step * ops_per_pair / pair_s / 1e12
-    pipe_peak = n_sm * 32 * sm_mhz * 1e6  # one 32x32->64 multiply per pair at 32 lanes/clk/SM
-    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32 lane-ops)",
-                "frac": achieved_tops / peak_tops, "traffic": pair_tile_traffic(),
-                "kernel": "k_pair_tile", "pair_tests_per_s": pairs_per_step / pair_s,
-                "ops_per_pair": ops_per_pair,
-                "peak_basis": "%d SMs x 128 lanes x %.0f MHz (sampled median)" % (n_sm, sm_mhz),
-                "multiply_pipe_peak_pair_tests_per_s": pipe_peak,
-                "multiply_pipe_frac": pairs_per_step / pair_s / pipe_peak,
+    pipe_peak = n_sm * 32 * sm_mhz * 1e6
+    roofline = {"bound": "alu", "achieved": pairs_per_step / pair_s / 1e12, "peak": pipe_peak / 1e12,
+                "unit": "T pair tests/s (one 32x32->64 integer multiply each)",
+                "frac": pairs_per_step / pair_s / pipe_peak, "traffic": pair_tile_traffic(),
+                "kernel": "k_pair_tile (+ k_pair_finish)",
+                "peak_basis": "%d SMs x 32 multiplies/clk x %.0f MHz (sampled median)" % (n_sm, sm_mhz),
+                "issue_lane_ops": {"ops_per_pair": ops_per_pair, "achieved_tops": achieved_tops,
+                                   "peak_tops": peak_tops, "frac": achieved_tops / peak_tops},
                 # the pair-test rate against the FP32 peak, at the 9 flops per
                 # pair an FP32 all-pairs tile would spend (dot product, P22,
                 # uniform conversion, compare)
