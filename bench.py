@@ -251,15 +251,14 @@ def pair_tile_traffic():
     return None
 
 
-def cpu_sample(args, cfg, steps):
-    """Time the oracle on a strip of cells with the workload's occupancy.
-
-    The strip keeps dx, dt, sigma, N_test and the per-cell particle numbers of
-    the left and right halves: m cells, half of them at the left occupancy and
-    half at the right one, so per-update cost matches the full workload's mix.
-    """
+def strip_sample(args, cfg):
+    """A strip of cells with the workload's occupancy: it keeps dx, dt, sigma,
+    N_test and the per-cell particle numbers of the left and right halves (m
+    cells, half of them at the left occupancy and half at the right one), so
+    per-update cost matches the full workload's mix.  Returns the box, the
+    cell count, the seeded state (FP32-representable for an FP32 run) and the
+    two particle numbers."""
     import numpy as np
-    from oracle import oracle as O
     from paper_1208_0961_gb300 import workloads as W
     m = max(2, args.cpu_sample_cells - args.cpu_sample_cells % 2)
     dx = cfg["L"][0] / cfg["n_cells"][0]
@@ -269,13 +268,20 @@ def cpu_sample(args, cfg, steps):
     Ls = (m * dx, cfg["L"][1], cfg["L"][2])
     n_l = int(round(per_l * m / 2))
     n_r = int(round(per_r * m / 2))
-    rng = np.random.default_rng(args.seed)
     regs = [((0.0, 0.0, 0.0), (Ls[0] / 2, Ls[1], Ls[2]), cfg["T_left"]),
             ((Ls[0] / 2, 0.0, 0.0), Ls, cfg["T_right"])]
     st = np.concatenate([W.thermal_state(n_l, regs[:1], seed=args.seed),
                          W.thermal_state(n_r, regs[1:], seed=args.seed + 1)], axis=1)
     if args.precision == "fp32":
         st = st.astype(np.float32).astype(np.float64)
+    return Ls, m, st, n_l, n_r
+
+
+def cpu_sample(args, cfg, steps):
+    """Time the oracle on a strip of cells with the workload's occupancy
+    (strip_sample)."""
+    from oracle import oracle as O
+    Ls, m, st, n_l, n_r = strip_sample(args, cfg)
     op = O.make_params(L=Ls, n=(m, 1, 1), dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"], n_test=cfg["n_test"],
                        fp32=args.precision == "fp32", seed=args.seed)
     st, _, _, _ = O.sort(op, st)
@@ -287,6 +293,66 @@ def cpu_sample(args, cfg, steps):
     sample = ("%d-cell strip of the same box (%d + %d particles at the workload's left/right cell "
               "occupancy, same dx, dt, sigma, N_test), %d oracle steps" % (m, n_l, n_r, steps))
     return n * steps / dt, O.threads(), sample, dt
+
+
+def fp32_vs_fp64_oracle(args, cfg):
+    """The FP32 path against the FP64 oracle on the strip of cpu_sample: one
+    step on the GPU in FP32 and one oracle step in FP64 from the same
+    FP32-representable state.  Keys may differ only by rounding near a cell
+    face; accepted pairs are compared in the cells whose sorted order agrees,
+    each pair accepted on one side only measured by |u - P22_FP64| / C (the
+    band where FP32 rounding of v_rel can flip a decision); momenta of the
+    pairs executed on both sides against the pair energy."""
+    import numpy as np
+    from oracle import oracle as O
+    Ls, m, st, _, _ = strip_sample(args, cfg)
+    op = O.make_params(L=Ls, n=(m, 1, 1), dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"], n_test=cfg["n_test"],
+                       seed=args.seed)
+    o_in, _, _, _ = O.sort(op, st)
+    o_out, res = O.step(op, 0, o_in)
+    n = o_in.shape[1]
+    p = cuba.make_params(L=Ls, n_cells=(m, 1, 1), dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"], n_test=cfg["n_test"],
+                         precision=cuba.CUBA_FP32, seed=args.seed)
+    sim = cuba.Sim(p, n)
+    try:
+        sim.set_state(o_in.astype(np.float32))
+        cuba.cuba_trace_enable(sim.h, True)
+        cuba.cuba_set_step(sim.h, 0)
+        sim.step(1)
+        g = sim.get_state().astype(np.float64)
+        keys, perm, cs, pairs, exe = sim.trace()
+    finally:
+        sim.close()
+    keys_differ = int(np.count_nonzero(keys != res.keys))
+    same = np.array([np.array_equal(perm[cs[c]:cs[c + 1]], res.perm[res.cell_start[c]:res.cell_start[c + 1]])
+                     for c in range(m)])
+    cells = np.nonzero(same)[0]
+    acc_g = set(map(tuple, pairs[np.isin(pairs[:, 0], cells)].tolist()))
+    acc_o = set(map(tuple, res.accepted[np.isin(res.accepted[:, 0], cells)].tolist()))
+    flips = acc_g ^ acc_o
+    band = 0.0
+    if flips:
+        C = O.p22_scale(op)
+        free = O.make_params(L=Ls, n=(m, 1, 1), dt=cfg["dt"], sigma_fm2=0.0, n_test=cfg["n_test"], seed=args.seed)
+        mid, _ = O.step(free, 0, o_in)
+        key = [args.seed & 0xFFFFFFFF, (args.seed >> 32) & 0xFFFFFFFF]
+        for c, i, j in flips:
+            b = res.cell_start[c]
+            ni = mid[3:, b + i] / np.linalg.norm(mid[3:, b + i])
+            nj = mid[3:, b + j] / np.linalg.norm(mid[3:, b + j])
+            u = O.pair_word(key, 0, c, i, j) * 2.0 ** -32
+            band = max(band, abs(u - C * 0.5 * float(np.sum((ni - nj) ** 2))) / C)
+    ex_g = set(map(tuple, pairs[exe].tolist()))
+    both = [e for e in map(tuple, res.executed.tolist()) if e in ex_g and same[e[0]]]
+    worst = 0.0
+    for c, i, j in both:
+        bo, bg = res.cell_start[c], cs[c]
+        s = np.linalg.norm(o_out[3:, bo + i]) + np.linalg.norm(o_out[3:, bo + j])
+        worst = max(worst, np.abs(g[3:, bg + i] - o_out[3:, bo + i]).max() / s,
+                    np.abs(g[3:, bg + j] - o_out[3:, bo + j]).max() / s)
+    return {"particles": n, "keys_differ": keys_differ, "cells_compared": int(same.sum()), "cells": m,
+            "accepted": int(len(acc_o)), "accepted_differ": len(flips), "max_abs_u_minus_p22_over_C": band,
+            "pairs_compared": len(both), "max_dp_over_pair_energy": worst}
 
 
 def run_reference(args):
@@ -611,6 +677,10 @@ def main():
         r, cores, sample, dt = cpu_sample(args, cfg, args.cpu_sample_steps)
         cpu = {"value": r, "unit": "particle-updates/s", "cores": cores, "kind": "oracle", "sample": sample,
                "seconds": dt}
+        if (prec == cuba.CUBA_FP32 and args.workload == "riemann1d" and args.acceptance == "all-pairs"
+                and args.mass == 0.0 and args.mu == 0.0 and args.kappa == 0.0):
+            # the FP32-vs-FP64-oracle error of this result, on the same strip
+            cpu["fp32_vs_fp64_oracle"] = fp32_vs_fp64_oracle(args, cfg)
 
     if rank == 0:
         line = {
