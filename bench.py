@@ -305,6 +305,7 @@ def fp32_vs_fp64_oracle(args, cfg):
     pairs executed on both sides against the pair energy."""
     import numpy as np
     from oracle import oracle as O
+    from paper_1208_0961_gb300 import cuba
     Ls, m, st, _, _ = strip_sample(args, cfg)
     op = O.make_params(L=Ls, n=(m, 1, 1), dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"], n_test=cfg["n_test"],
                        seed=args.seed)
