@@ -147,32 +147,36 @@ struct CellCtx {
     uint32_t slot;    // its counters row
 };
 
+// One entry of a warp's block queue: the Philox block and its row and
+// group (32 bytes, so an entry's address is one shift-add of its slot).
+struct __align__(16) QEntry {
+    uint4 r;
+    uint32_t i, g, pad0, pad1;
+};
+
 // Push a block onto the warp's queue iff its test word x has a bit of
 // 0x80808080 set: one predicate feeds the ballot and the two predicated
-// shared-memory stores (block r at qw_s + 16 slot, (i, g) at qig_s + 8 slot).
-// Returns the warp's new queue length.
-__device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t qn, uint32_t qw_s, uint32_t qig_s,
-                                               uint4 r, uint32_t i, uint32_t g)
+// shared-memory stores.  qa is the shared address of the next free entry;
+// returns it after the warp's pushes.
+__device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t qa, uint4 r, uint32_t i, uint32_t g)
 {
-    uint32_t qn_out;
+    uint32_t qa_out;
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b32 t, b, s, a;\n\t"
+        "{\n\t.reg .pred p;\n\t.reg .b32 t, b, a;\n\t"
         "and.b32 t, %1, 0x80808080;\n\t"
         "setp.ne.u32 p, t, 0;\n\t"
         "vote.sync.ballot.b32 b, p, 0xffffffff;\n\t"
         "and.b32 t, b, %2;\n\t"
         "popc.b32 t, t;\n\t"
-        "add.u32 s, %3, t;\n\t"
+        "mad.lo.u32 a, t, 32, %3;\n\t"
+        "@p st.shared.v4.u32 [a], {%4, %5, %6, %7};\n\t"
+        "@p st.shared.v2.u32 [a+16], {%8, %9};\n\t"
         "popc.b32 t, b;\n\t"
-        "add.u32 %0, %3, t;\n\t"
-        "mad.lo.u32 a, s, 16, %4;\n\t"
-        "@p st.shared.v4.u32 [a], {%6, %7, %8, %9};\n\t"
-        "mad.lo.u32 a, s, 8, %5;\n\t"
-        "@p st.shared.v2.u32 [a], {%10, %11};\n\t}"
-        : "=r"(qn_out)
-        : "r"(x), "r"(lt), "r"(qn), "r"(qw_s), "r"(qig_s), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g)
+        "mad.lo.u32 %0, t, 32, %3;\n\t}"
+        : "=r"(qa_out)
+        : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g)
         : "memory");
-    return qn_out;
+    return qa_out;
 }
 
 // Append accepted pair (i, j) to its cell's list; kMark: the cell's first
@@ -317,7 +321,7 @@ __device__ __forceinline__ void drain_survivors(uint4* sv, uint32_t* svn, uint32
 template <typename T, bool kMark>
 __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
                                                uint32_t thr16, T C, T m2, const T* __restrict__ st, uint32_t pcap,
-                                               const uint4* qw, const uint2* qig, uint32_t e0,
+                                               const QEntry* q, uint32_t e0,
                                                uint32_t e1, uint4* sv, uint32_t* svn,
                                                uint32_t* __restrict__ acc_count,
                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
@@ -326,9 +330,8 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
 {
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t e = e0 + lane; e < e1; e += 32) {
-        const uint4 r = qw[e];
-        const uint2 ig = qig[e];
-        const uint32_t i = ig.x, g = ig.y;
+        const uint4 r = q[e].r;
+        const uint32_t i = q[e].i, g = q[e].g;
         uint32_t m = block_le_mask(r, thr8) & valid_cols(g, i, cc.n);
         if (!m) continue;
         const uint4 mb = philox4x32_10(make_uint4(step, cc.lc, i, kTagMid | g), K);
@@ -355,8 +358,8 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
 // it to the active-cell list (the small-cell path finds its cells by scanning).
 template <typename T, bool kMark, int NB>
 __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32_t step, uint32_t thr8, uint32_t thr16,
-                                          T C, T m2, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap, uint4* qw,
-                                          uint2* qig, uint4* sv, uint32_t* svn,
+                                          T C, T m2, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap,
+                                          QEntry* q, uint4* sv, uint32_t* svn,
                                           uint32_t* __restrict__ acc_count,
                                           unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                           uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
@@ -379,30 +382,32 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
     // or past the cell's end) may be queued: the resolve drops their columns.
     const uint32_t t8 = row_ok ? 0x01010101u * (thr8 + 1u) : 0u;
     const uint32_t x0 = (row_ok && thr8 >= 128u) ? 0x80000000u : 0u;
-    const uint32_t qw_s = (uint32_t)__cvta_generic_to_shared(qw);
-    const uint32_t qig_s = (uint32_t)__cvta_generic_to_shared(qig);
-    uint32_t qn = 0;  // warp-uniform number of queued blocks
+    // qa: shared address of the next free queue entry; past qa_drain a
+    // warp could not push 32 NB more blocks, so it drains 32 first
+    const uint32_t q_s = (uint32_t)__cvta_generic_to_shared(q);
+    const uint32_t qa_drain = q_s + 32u * (uint32_t)(kQueueCap - 32 * NB);
+    uint32_t qa = q_s;  // warp-uniform
     for (uint32_t g = gfirst; g <= glast; g += NB) {
-        // up to 32 NB blocks are pushed below: drain to at most 32 first
-        while (qn > (uint32_t)(kQueueCap - 32 * NB)) {
+        while (qa > qa_drain) {
+            const uint32_t qn = (qa - q_s) >> 5;
             __syncwarp();
-            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, qn - 32, qn, sv, svn,
-                                     acc_count, acc, acc_cap, counters, active, stats);
+            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, q, qn - 32, qn, sv, svn, acc_count,
+                                     acc, acc_cap, counters, active, stats);
             __syncwarp();
-            qn -= 32;
+            qa -= 32u * 32u;
         }
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const uint4 r = R.block(g + q, K);
+        for (int b = 0; b < NB; ++b) {
+            const uint4 r = R.block(g + b, K);
             const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
                                ((r.w - t8) & ~r.w) | x0;
-            qn = queue_push(x, lt, qn, qw_s, qig_s, r, i, g + q);
+            qa = queue_push(x, lt, qa, r, i, g + b);
         }
     }
-    if (qn) {
+    if (qa != q_s) {
         __syncwarp();
-        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, qw, qig, 0, qn, sv, svn, acc_count, acc, acc_cap,
-                                 counters, active, stats);
+        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, q, 0, (qa - q_s) >> 5, sv, svn, acc_count,
+                                 acc, acc_cap, counters, active, stats);
         __syncwarp();
     }
 }
@@ -567,8 +572,7 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
                 uint4* __restrict__ surv, uint32_t surv_cap, const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    __shared__ uint4 q_w[kWarps][queue_cap(NB)];
-    __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
+    __shared__ QEntry q_e[kWarps][queue_cap(NB)];
     __shared__ uint4 s_v[kWarps][kSurvBuf];
     __shared__ uint32_t s_vn[kWarps], s_left[kWarps];
     const int w = threadIdx.x >> 5;
@@ -618,8 +622,8 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
         const uint32_t rb = item - w0.x;
         const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
         const PhiloxKey& K = kOneKey ? Kp : Kl;
-        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_w[w],
-                               q_ig[w], s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active, stats);
+        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_e[w],
+                               s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active, stats);
         __syncwarp();
         if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
             flush_survivors(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, counters);
@@ -646,8 +650,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
                                                              const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    __shared__ uint4 q_w[kWarps][queue_cap(NB)];
-    __shared__ uint2 q_ig[kWarps][queue_cap(NB)];
+    __shared__ QEntry q_e[kWarps][queue_cap(NB)];
     __shared__ uint4 s_v[kWarps][kSurvBuf];
     __shared__ uint32_t s_vn[kWarps], s_left[kWarps];
     const int w = threadIdx.x >> 5;
@@ -689,7 +692,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
             const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
             for (uint32_t rb = 0; rb < nrb; ++rb)
                 pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap,
-                                        q_w[w], q_ig[w], s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active,
+                                        q_e[w], s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active,
                                         stats);
             __syncwarp();
             if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
