@@ -324,8 +324,8 @@ int cuba_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, voi
  * resolve).  Results of a simulation do not depend on the other residents:
  * its random numbers are keyed by its own seed, step counter and local cell
  * and particle indices, and every per-cell operation is order independent.
- * This is the execution layer for ensembles and for serving (north star; the
- * paper runs one simulation at a time).
+ * This is the execution layer for ensembles and for serving (the paper runs
+ * one simulation at a time).
  */
 typedef struct cuba_batch cuba_batch;
 

@@ -75,7 +75,8 @@ def thermal_state(n, regions, seed, dtype=np.float64):
 
 
 # Workloads of the benchmark and of the parity tests.  Sizes follow the
-# paper's 1D Riemann problem (Sec. 5), scaled as described in the design doc.
+# paper's 1D Riemann problem (Sec. 5): the 20 k-particle, 100-cell box and
+# its 16 M-particle, 2000-cell scale-up at the same temperatures.
 def riemann_1d(n_particles, n_cells, dt, sigma_mb, T_left=0.4, T_right=0.32, L=(10.0, 1.0, 1.0)):
     regs = riemann_regions(L, T_left, T_right)
     return dict(L=L, n_cells=(n_cells, 1, 1), dt=dt, sigma_fm2=sigma_mb * FM2_PER_MB,
@@ -98,6 +99,35 @@ def hotspot_3d(n_particles, cells_per_axis, dt, sigma_mb, L=12.8, T0=0.4, dT=0.2
     n_phys = GLUON_DOF * Z / (math.pi ** 2 * HBARC_GEV_FM ** 3)
     return dict(L=(L, L, L), n_cells=(cells_per_axis,) * 3, dt=dt, sigma_fm2=sigma_mb * FM2_PER_MB,
                 n_test=n_particles / n_phys, n=n_particles, T0=T0, dT=dT, width=width)
+
+
+def hotspot_state(n, cfg, seed, dtype=np.float64, chunk=1 << 24):
+    """(6, n) state of the hot-spot box: positions uniform in the box, kept
+    with probability (T(r) / T_max)^3 (density ∝ T^3), then a massless
+    Boltzmann energy E ~ Gamma(3, T(r)) and an isotropic direction."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(cfg["L"], dtype=np.float64)
+    T0, dT, w = cfg["T0"], cfg["dT"], cfg["width"]
+    tmax = T0 + dT
+    st = np.empty((6, n), dtype=np.float64)
+    k = 0
+    while k < n:
+        x = rng.uniform(0.0, 1.0, (3, chunk)) * L[:, None]
+        r2 = ((x - 0.5 * L[:, None]) ** 2).sum(axis=0)
+        T = T0 + dT * np.exp(-r2 / (2.0 * w * w))
+        keep = rng.uniform(0.0, 1.0, chunk) < (T / tmax) ** 3
+        m = min(int(keep.sum()), n - k)
+        st[:3, k:k + m] = x[:, keep][:, :m]
+        Tk = T[keep][:m]
+        E = rng.gamma(3.0, Tk)
+        ct = rng.uniform(-1.0, 1.0, m)
+        phi = rng.uniform(0.0, 2.0 * math.pi, m)
+        s = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+        st[3, k:k + m] = E * s * np.cos(phi)
+        st[4, k:k + m] = E * s * np.sin(phi)
+        st[5, k:k + m] = E * ct
+        k += m
+    return st.astype(dtype)
 
 
 HOTSPOT_64M = dict(name="hotspot-3d-64M", n=64_000_000, cells=128, dt=0.01, sigma_mb=5.0, steps=200)

@@ -101,3 +101,55 @@ def test_batch_capacity_is_enforced():
         b.step(2)
     finally:
         b.close()
+
+
+def test_full_size_ensemble_sampled_members():
+    """The batched ensemble at full size (256 Riemann runs, 2.4e8 particles,
+    FP32), one step of the whole batch: the members the oracle can step in
+    seconds (the fewest pair tests) start from host-sampled states and must
+    match the oracle's single-precision mirror — positions bit-exact (hence
+    the same sort), the same accepted and executed counts, momenta of
+    colliding particles within 1e-5 of the pair energy and untouched ones
+    exact; the other members are sampled on the device."""
+    import bench
+    members = bench.ensemble(256, 0)
+    cost = [m["n"] ** 2 / m["n_cells"][0] for m in members]
+    sampled = set(np.argsort(cost)[:3].tolist())
+    N = sum(m["n"] for m in members)
+    C = sum(m["n_cells"][0] for m in members)
+    b = cuba.Batch(cuba.make_batch_config(cuba.CUBA_FP32, max_sims=256, max_particles=N, max_cells=C))
+    want = {}
+    try:
+        ids = {}
+        for k, m in enumerate(members):
+            p = cuba.make_params(L=m["L"], n_cells=m["n_cells"], dt=m["dt"], sigma_fm2=m["sigma_fm2"],
+                                 n_test=m["n_test"], precision=cuba.CUBA_FP32, seed=m["seed"])
+            if k in sampled:
+                st = W.thermal_state(m["n"], m["regions"], seed=100 + k).astype(np.float32)
+                ids[k] = b.add_state(p, st)
+                want[k] = st
+            else:
+                b.add(p, m["n"], m["regions"])
+        b.step(1)
+        got = {k: (b.get_state(ids[k]), b.stats(ids[k])) for k in sampled}
+    finally:
+        b.close()
+    for k in sorted(sampled):
+        m = members[k]
+        op = O.make_params(L=m["L"], n=m["n_cells"], dt=m["dt"], sigma_fm2=m["sigma_fm2"], n_test=m["n_test"],
+                           fp32=True, seed=m["seed"])
+        o, _, _, _ = O.sort(op, want[k].astype(np.float64))
+        o, res = O.step(op, 0, o)
+        g, s = got[k]
+        assert np.array_equal(g[:3].astype(np.float64), o[:3]), k
+        assert s["accepted"] == res.n_acc and s["executed"] == res.n_exe, k
+        E = np.sqrt((o[3:] ** 2).sum(axis=0))
+        tol = np.zeros(o.shape[1])
+        for c, i, j in res.executed.tolist():
+            bb = res.cell_start[c]
+            tol[bb + i] = tol[bb + j] = E[bb + i] + E[bb + j]
+        d = np.abs(g[3:].astype(np.float64) - o[3:]).max(axis=0)
+        moved = tol > 0
+        assert np.all(d[~moved] == 0), k
+        assert np.all(d[moved] <= 1e-5 * tol[moved]), k
+        assert res.n_exe > 0, k

@@ -1,4 +1,4 @@
-"""Ensemble parity (the benchmark spec): multi-step energy-density profiles of the
+"""Ensemble parity: multi-step energy-density profiles of the
 GPU (FP32 state, one batch of R independent runs) and of the FP64 oracle (R
 other independent runs) agree cell by cell within 3 standard errors: at most
 1 % of the (cell, time) points may exceed 3 sigma and the chi^2 of every

@@ -1,4 +1,4 @@
-"""FP32 state against the FP64 oracle (spec: the FP32-vs-FP64 error is
+"""FP32 state against the FP64 oracle (the FP32-vs-FP64 error is
 stated for every result).  One step from the same FP32-representable state:
   * cell keys: the FP32 positions differ from the FP64 ones by rounding, so a
     key may differ only for a particle within 1e-5 of a cell face (in units of

@@ -1,4 +1,4 @@
-"""The FP64 threshold of the FP32 kinematics (spec: FP64 only for CM
+"""The FP64 threshold of the FP32 kinematics (FP64 only for CM
 boosts above a stated Lorentz factor).  Pairs with a chosen CM gamma are
 boosted by the device's FP32 path with no FP64 fallback and compared with the
 oracle's FP64 kinematics on the same (float-rounded) momenta.  Relative to

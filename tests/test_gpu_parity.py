@@ -242,6 +242,9 @@ def test_full_size_riemann_16M_sampled():
     sim = cuba.Sim(p, 16_000_000)
     try:
         sim.set_state(st0)
+        # the shape the autotuner picks for this workload: 32-row items only,
+        # eight Philox blocks per lane and iteration
+        cuba.cuba_set_launch_shape(sim.h, 0, 2, 8)
         cuba.cuba_trace_enable(sim.h, True)
         sim.step(1)
         g = sim.get_state()
@@ -286,6 +289,69 @@ def test_full_size_riemann_16M_sampled():
             assert np.max(np.abs(g[3:, b + i] - pi)) <= 1e-5 * s
             assert np.max(np.abs(g[3:, b + j] - pj)) <= 1e-5 * s
     assert len(used) > 0
+
+
+def _check_cell(op, c, mom, pairs, exe, g, b):
+    """All accepted pairs of cell c, its greedy matching and the momenta of
+    its executed pairs (1e-5 of the pair energy) against the oracle."""
+    acc = O.cell_accept(op, 0, c, mom)
+    sel = pairs[:, 0] == c
+    assert np.array_equal(pairs[sel][:, 1:], acc), c
+    used = set()
+    for (i, j), x in zip(acc.tolist(), exe[sel].tolist()):
+        want = i not in used and j not in used
+        assert x == want
+        if want:
+            used.update((i, j))
+            ok, pi, pj = O.kinematics([0, 0], 0, c, i, j, mom[:, i], mom[:, j])
+            s = np.linalg.norm(mom[:, i]) + np.linalg.norm(mom[:, j])
+            assert np.max(np.abs(g[3:, b + i] - pi)) <= 1e-5 * s
+            assert np.max(np.abs(g[3:, b + j] - pj)) <= 1e-5 * s
+    return len(acc), len(used) // 2
+
+
+def test_full_size_hotspot_64M_sampled():
+    """The 3D hot spot at full size (64 M particles, 128^3 cells, sigma = 5 mb,
+    dt = 0.01, FP32), one step in the launch shape the autotuner picks for it
+    (warp-per-cell kernels for cells up to 256 particles, two Philox blocks per
+    iteration of the 32-row item kernel): keys, permutation, cell_start and
+    positions of every particle against the oracle's single-precision mirror;
+    accepted pairs, greedy matching and momenta of the fullest cells and of
+    random ones."""
+    n = 64_000_000
+    cfg = W.hotspot_3d(n, 128, 0.01, 5.0)
+    st0 = W.hotspot_state(n, cfg, seed=23).astype(np.float32)
+    p, op = _pair(cfg["L"], cfg["n_cells"], cfg["dt"], cfg["sigma_fm2"], cfg["n_test"], True, 0)
+    sim = cuba.Sim(p, n)
+    try:
+        sim.set_state(st0)
+        cuba.cuba_set_launch_shape(sim.h, 256, 1, 2)
+        cuba.cuba_trace_enable(sim.h, True)
+        sim.step(1)
+        g = sim.get_state()
+        keys, perm, cs, pairs, exe = sim.trace()
+    finally:
+        sim.close()
+    op0 = O.make_params(L=cfg["L"], n=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=0.0, n_test=cfg["n_test"],
+                        fp32=True, seed=0)
+    o_in, _, _, _ = O.sort(op0, st0.astype(np.float64))
+    del st0
+    mid, r0 = O.step(op0, 0, o_in)
+    del o_in
+    assert np.array_equal(keys, r0.keys.astype(np.uint32))
+    assert np.array_equal(perm.astype(np.int64), r0.perm)
+    assert np.array_equal(cs.astype(np.int64), r0.cell_start)
+    assert np.array_equal(g[:3].astype(np.float64), mid[:3])
+    occ = np.diff(r0.cell_start)
+    rng = np.random.default_rng(7)
+    cells = np.concatenate([np.argsort(occ)[-3:], rng.integers(0, len(occ), 40)])
+    na = ne = 0
+    for c in cells.tolist():
+        b, e = int(cs[c]), int(cs[c + 1])
+        a, x = _check_cell(op, c, mid[3:, b:e], pairs, exe, g, b)
+        na += a
+        ne += x
+    assert na > 20 and ne > 10
 
 
 @pytest.mark.parametrize("small_max", [0, 32, 1024])
