@@ -206,15 +206,26 @@ def bin_passes(ncells):
     return max(1, (bits + 10) // 11)
 
 
-def launches_per_step(ncells, small_max, skip=False, adaptive=False):
-    """Kernels of one step: streaming histogram; per radix pass the digit
-    histogram (passes after the first), 3 scan kernels and the ranking
-    kernel, then (two passes or more) the gather; cell preparation + 3 scan
-    kernels; small-cell and tiled pair kernels and the survivor kernel
-    (skip-ahead: 3 scan kernels of its row blocks and its pair kernel);
-    small-cell and per-cell resolve kernels; the step counter."""
+def neighbour_sort(n, cfg):
+    """Whether a step of this single-simulation workload sorts by neighbour
+    moves (the library's rule: more than 2048 cells, at most 64 particles per
+    cell on average, dt at most 0.98 of the cell edge on every axis with more
+    than one cell)."""
+    cells = cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2]
+    edges_ok = all(cfg["n_cells"][a] == 1 or cfg["dt"] <= 0.98 * cfg["L"][a] / cfg["n_cells"][a] for a in range(3))
+    return cells > 2048 and n <= 64 * cells and edges_ok
+
+
+def launches_per_step(ncells, small_max, skip=False, adaptive=False, neighbour=False):
+    """Kernels of one step: the stream/sort kernels — radix: streaming
+    histogram; per radix pass the digit histogram (passes after the first), 3
+    scan kernels and the ranking kernel, then (two passes or more) the gather;
+    neighbour-move sort: count pass, offsets, 3 scan kernels, scatter pass —;
+    cell preparation + 3 scan kernels; small-cell and tiled pair kernels and
+    the survivor kernel (skip-ahead: 3 scan kernels of its row blocks and its
+    pair kernel); small-cell and per-cell resolve kernels; the step counter."""
     p = bin_passes(ncells)
-    sort = 1 + 4 * p + (p - 1) + (1 if p > 1 else 0)
+    sort = 6 if neighbour else 1 + 4 * p + (p - 1) + (1 if p > 1 else 0)
     small = 1 if small_max else 0
     pairs = 3 + 1 if skip else 1 + small + 1
     return (1 if adaptive else 0) + sort + 4 + pairs + (1 + small) + 1
@@ -699,7 +710,7 @@ def main():
             "clocks": clk,
             "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2],
                                               cuba.cuba_get_small_max(sim.h), args.acceptance == "skip",
-                                              args.kappa > 0) * args.steps,
+                                              args.kappa > 0, neighbour_sort(args.n, cfg)) * args.steps,
             "roofline": roofline,
             "hbm_phases": hbm,
             "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in zip(phase_names, phase)},

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcuba.so")
-SOURCES = ["kernels_sort.cu", "kernels_bin.cu", "kernels_pairs.cu", "capi.cu", "capi_batch.cu"]
+SOURCES = ["kernels_sort.cu", "kernels_bin.cu", "kernels_nbr.cu", "kernels_pairs.cu", "capi.cu", "capi_batch.cu"]
 HEADERS = ["engine.cuh", "fp.cuh", "philox.cuh", "stream.cuh", "host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

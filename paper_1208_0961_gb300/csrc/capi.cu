@@ -97,6 +97,7 @@ int make_desc(const cuba_params* p, SimDesc* S)
 void arena_free(Arena& A)
 {
     void* ptrs[] = {A.st[0], A.st[1], A.key[0], A.key[1], A.idx[0], A.idx[1], A.cell_start, A.cell_work, A.skip_work, A.surv,
+                    A.nbr_rel, A.nbr_cs,
                     A.acc_count, A.acc, A.radix_hist, A.scan_tmp, A.counters, A.active, A.used_bits, A.stats,
                     A.d_sims, A.trace_keys};
     for (void* p : ptrs)
@@ -144,6 +145,11 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
     A.surv_cap = std::max<uint32_t>(1u << 21, (uint32_t)(pc / 2));
     if (!rc) rc = dalloc(&A.surv, (size_t)A.surv_cap * sizeof(uint4), "survivors");
     if (!rc) rc = dalloc(&A.used_bits, (pc / 32 + 2) * 4, "used_bits");
+    if (!rc && ccap > (uint32_t)kBinBins && (size_t)27 * ccap <= ((size_t)1 << 29)) {
+        A.nbr_cap = ccap;
+        rc = dalloc(&A.nbr_rel, (size_t)27 * ccap * 4, "neighbour offsets");
+        if (!rc) rc = dalloc(&A.nbr_cs, ((size_t)ccap + 1) * 4, "neighbour cell_start");
+    }
     if (!rc) rc = dalloc(&A.stats, (size_t)simcap * kStatCount * 8, "stats");
     if (!rc) rc = dalloc(&A.d_sims, (size_t)simcap * sizeof(SimDesc), "sims");
     if (rc) {
@@ -162,7 +168,8 @@ int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simca
 int enqueue_step(Arena& A, cudaStream_t st)
 {
     if (A.any_adapt && launch_adapt_dt(A, st)) return fail(CUBA_ERR_CUDA, "adaptive dt launch failed");
-    if (launch_step_bin(A, st, nullptr)) return fail(CUBA_ERR_CUDA, "stream/sort launch failed");
+    if ((nbr_path(A) ? launch_step_nbr(A, st, nullptr) : launch_step_bin(A, st, nullptr)))
+        return fail(CUBA_ERR_CUDA, "stream/sort launch failed");
     if (launch_cell_prep(A, st)) return fail(CUBA_ERR_CUDA, "cell preparation launch failed");
     if (launch_pair_tile(A, st)) return fail(CUBA_ERR_CUDA, "pair tile launch failed");
     if (launch_resolve(A, st)) return fail(CUBA_ERR_CUDA, "resolve launch failed");
@@ -277,6 +284,8 @@ int read_kernel_errors(Arena& A)
     CUDA_TRY(cudaMemcpy(&err, A.counters + 1, 4, cudaMemcpyDeviceToHost), "read error flags");
     if (err) {
         cudaMemset(A.counters + 1, 0, 4);
+        if (err & kErrMove)
+            return fail(CUBA_ERR_INVALID, "a particle moved more than one cell along an axis in a step");
         if (err & kErrCapacity)
             return fail(CUBA_ERR_OVERFLOW, "accepted-pair lists of a step exceeded the allocated list; "
                                            "that step skipped its collisions");
@@ -300,7 +309,7 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
 {
     if (np != A.np || acc != A.acc || trace != A.trace || nsims != A.nsims || ncells != A.ncells ||
         small_max != A.small_max || one_key != A.one_key || key0 != A.key_sched.k0[0] || key1 != A.key_sched.k1[0] ||
-        modes != A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs || tile_nb != A.tile_nb ||
+        modes != A.nbr_ok * 8 + A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs || tile_nb != A.tile_nb ||
         small_nb != A.small_nb)
         drop();
     for (int k = 0; k < n; ++k) {
@@ -331,7 +340,7 @@ int StepGraphs::run(Arena& A, int n, cudaStream_t st)
             one_key = A.one_key;
             key0 = A.key_sched.k0[0];
             key1 = A.key_sched.k1[0];
-            modes = A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs;
+            modes = A.nbr_ok * 8 + A.any_adapt * 4 + A.any_skip * 2 + A.any_all_pairs;
             tile_nb = A.tile_nb;
             small_nb = A.small_nb;
         }
@@ -348,9 +357,13 @@ void set_key_param(Arena& A, const SimDesc* table, int n)
     A.any_skip = 0;
     A.any_all_pairs = 0;
     A.any_adapt = 0;
+    A.nbr_ok = 1;
     for (int k = 0; k < n; ++k) {
         if (table[k].skip) A.any_skip = 1; else A.any_all_pairs = 1;
         if (table[k].kappa > 0.0) A.any_adapt = 1;
+        const double dt = std::max(table[k].dt, table[k].dt_max);
+        for (int a = 0; a < 3; ++a)
+            if (table[k].n[a] > 1 && !(dt <= 0.98 * table[k].dx[a])) A.nbr_ok = 0;
     }
 }
 
@@ -385,6 +398,7 @@ static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, d
     if (rc) return rc;
     std::vector<SimDesc> table(A.nsims);
     std::vector<unsigned long long> stats((size_t)A.simcap * kStatCount);
+    std::vector<uint32_t> cells((size_t)A.ncells + 1);
     CUDA_TRY(cudaDeviceSynchronize(), "sync");
     const int cur0 = A.cur;
     const uint32_t keep = A.small_max;
@@ -392,12 +406,14 @@ static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, d
         cudaMemcpy((char*)saved + c * col, (char*)A.st[cur0] + (size_t)c * A.pcap * es, col, cudaMemcpyDeviceToDevice);
     cudaMemcpy(table.data(), A.d_sims, table.size() * sizeof(SimDesc), cudaMemcpyDeviceToHost);
     cudaMemcpy(stats.data(), A.stats, stats.size() * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(cells.data(), A.cell_start, cells.size() * 4, cudaMemcpyDeviceToHost);
     auto restore = [&]() {
         A.cur = cur0;
         for (int c = 0; c < 6; ++c)
             cudaMemcpy((char*)A.st[cur0] + (size_t)c * A.pcap * es, (char*)saved + c * col, col, cudaMemcpyDeviceToDevice);
         cudaMemcpy(A.d_sims, table.data(), table.size() * sizeof(SimDesc), cudaMemcpyHostToDevice);
         cudaMemcpy(A.stats, stats.data(), stats.size() * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(A.cell_start, cells.data(), cells.size() * 4, cudaMemcpyHostToDevice);
         cudaDeviceSynchronize();
     };
     cudaEvent_t e0, e1;
@@ -734,7 +750,8 @@ int cuba_step_profiled(cuba_sim* s, int n_steps, double* phase_ms, void* stream)
     for (int it = 0; it < n_steps && !rc; ++it) {
         cudaEventRecord(ev[0], st);
         if (A.any_adapt && launch_adapt_dt(A, st)) rc = fail(CUBA_ERR_CUDA, "adaptive dt launch failed");
-        if (!rc && launch_step_bin(A, st, ev[1])) rc = fail(CUBA_ERR_CUDA, "stream/sort launch failed");
+        if (!rc && (nbr_path(A) ? launch_step_nbr(A, st, ev[1]) : launch_step_bin(A, st, ev[1])))
+            rc = fail(CUBA_ERR_CUDA, "stream/sort launch failed");
         cudaEventRecord(ev[2], st);
         if (!rc && launch_cell_prep(A, st)) rc = fail(CUBA_ERR_CUDA, "cell preparation launch failed");
         cudaEventRecord(ev[3], st);

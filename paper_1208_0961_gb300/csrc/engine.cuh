@@ -105,6 +105,7 @@ enum StatIdx {
 // Error bits set by kernels.
 constexpr uint32_t kErrAccOverflow = 1u;   // accepted list ran out of room
 constexpr uint32_t kErrCapacity = 2u;      // list capacity of a step exceeds the allocation
+constexpr uint32_t kErrMove = 4u;          // a particle moved more than one cell along an axis
 
 // Radix sort geometry: 256 threads x 16 keys per tile; 8-bit digits for the
 // sort of a settled state, 11-bit digits for the sort inside a step (one pass
@@ -189,6 +190,14 @@ struct Arena {
     uint32_t* acc_count = nullptr;      // ccap
     unsigned long long* acc = nullptr;  // accepted (i << 32 | j), per-cell segments
     uint64_t acc_capacity = 0;
+    // neighbour-move sort: per-direction counts / in-cell offsets (27 rows of
+    // nbr_cap cells), the new cell_start; allocated for arenas of more than
+    // 2048 cells; nbr_ok: every simulation's dt (or its cap) lies below 0.98
+    // of the cell edge on each axis with more than one cell
+    uint32_t* nbr_rel = nullptr;
+    uint32_t* nbr_cs = nullptr;
+    uint32_t nbr_cap = 0;
+    int nbr_ok = 0;
     uint4* surv = nullptr;              // survivors of both random-byte filters, counters[3] of them
     uint32_t surv_cap = 0;
     uint32_t* radix_hist = nullptr;     // digit histograms and their scan, 2 kBinBins * tiles
@@ -231,6 +240,10 @@ int scan_u32(uint32_t* data, size_t n, void* tmp, size_t tmp_bytes, cudaStream_t
 // cell_start and, when tracing, the keys and the permutation.  after_stream
 // (may be null) is recorded once the streaming pass is done.
 int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream);
+// A1-A4 as a neighbour-move sort (many small cells, dt below the cell edge):
+// used instead of launch_step_bin when nbr_path(A)
+bool nbr_path(const Arena& A);
+int launch_step_nbr(Arena& A, cudaStream_t st, cudaEvent_t after_stream);
 int bin_kernels_init();
 size_t bin_scan_bytes();   // scratch the histogram scan needs in scan_tmp
 int launch_cell_prep(const Arena& A, cudaStream_t st, int count_pairs = 1);

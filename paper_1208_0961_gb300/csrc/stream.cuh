@@ -10,11 +10,10 @@
 
 namespace cuba {
 
-// Cell key: i_a = clamp(floor(x_a / dx_a), 0, n_a - 1); key = ix + nx (iy + ny iz).
+// Cell coordinates: i_a = clamp(floor(x_a / dx_a), 0, n_a - 1).
 template <typename T>
-__device__ __forceinline__ uint32_t cell_key(const SimDesc& S, const T pos[3])
+__device__ __forceinline__ void cell_coords(const SimDesc& S, const T pos[3], uint32_t id[3])
 {
-    uint32_t id[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const T c = floor_t(div_rn(pos[a], sim_dx<T>(S, a)));
@@ -24,6 +23,14 @@ __device__ __forceinline__ uint32_t cell_key(const SimDesc& S, const T pos[3])
         else ic = (uint32_t)c;
         id[a] = ic;
     }
+}
+
+// Cell key: key = ix + nx (iy + ny iz).
+template <typename T>
+__device__ __forceinline__ uint32_t cell_key(const SimDesc& S, const T pos[3])
+{
+    uint32_t id[3];
+    cell_coords<T>(S, pos, id);
     return id[0] + (uint32_t)S.n[0] * (id[1] + (uint32_t)S.n[1] * id[2]);
 }
 

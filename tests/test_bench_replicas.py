@@ -84,5 +84,11 @@ def test_launch_count():
     # no small-cell kernels) and 21 (64 M, 128^3 cells, small-cell kernels)
     assert bench.launches_per_step(2000, 0) == 13
     assert bench.launches_per_step(128 ** 3, 64) == 21
+    # the neighbour-move sort of the 64 M hot spot: 16 per step
+    assert bench.launches_per_step(128 ** 3, 256, neighbour=True) == 16
+    hs = {"n_cells": (128, 128, 128), "L": (12.8, 12.8, 12.8), "dt": 0.01}
+    assert bench.neighbour_sort(64_000_000, hs) and not bench.neighbour_sort(300_000_000, hs)
+    rm = {"n_cells": (2000, 1, 1), "L": (10.0, 1.0, 1.0), "dt": 0.0025}
+    assert not bench.neighbour_sort(16_000_000, rm)
     # skip-ahead (15 per step of the 16 M workload in its ncu launch list)
     assert bench.launches_per_step(2000, 0, skip=True) == 15

@@ -108,6 +108,52 @@ def test_single_step_3d_ragged(fp32):
     assert na > 100
 
 
+@pytest.mark.parametrize("dt", [0.05, 0.0985])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_single_step_3d_many_small_cells(fp32, dt):
+    # 16 x 12 x 12 = 2304 cells (more than one 11-bit digit), about 17
+    # particles per cell: dt = 0.05 takes the neighbour-move sort (dt below
+    # 0.98 of the 0.1 fm cell edge), dt = 0.0985 the two-pass radix sort
+    L = (1.6, 1.2, 1.2)
+    regs = [((0.0, 0.0, 0.0), (0.8, 1.2, 1.2), 0.45), ((0.8, 0.0, 0.0), L, 0.35)]
+    st0 = W.thermal_state(40000, regs, seed=17)
+    na, ne = _one_step_compare(L, (16, 12, 12), dt, 0.002, 5.0, fp32, 19, st0, step_index=5)
+    assert na > 200 and ne > 100
+
+
+def test_neighbour_sort_several_steps():
+    """Four steps in FP64 on 3072 small cells (every step after the first
+    sorts from the previous step's order and cell_start): keys, permutation
+    and cell_start of the last step equal the oracle's, positions agree to
+    1e-12 fm and momenta to 1e-10 of the particle energy."""
+    L = (1.6, 1.6, 1.2)
+    regs = [((0.0, 0.0, 0.0), L, 0.4)]
+    st0 = W.thermal_state(50000, regs, seed=29)
+    p, op = _pair(L, (16, 16, 12), 0.06, 0.002, 5.0, False, 31)
+    sim = cuba.Sim(p, 50000)
+    try:
+        sim.set_state(st0)
+        sim.step(3)
+        cuba.cuba_trace_enable(sim.h, True)
+        sim.step(1)
+        g = sim.get_state()
+        keys, perm, cs, pairs, exe = sim.trace()
+        stats = sim.stats()
+    finally:
+        sim.close()
+    o, _, _, _ = O.sort(op, st0)
+    for k in range(3):
+        o, _ = O.step(op, k, o)
+    o, res = O.step(op, 3, o)
+    assert np.array_equal(keys, res.keys.astype(np.uint32))
+    assert np.array_equal(perm.astype(np.int64), res.perm)
+    assert np.array_equal(cs.astype(np.int64), res.cell_start)
+    assert np.max(np.abs(g[:3] - o[:3])) <= 1e-12
+    E = np.sqrt((o[3:] ** 2).sum(axis=0))
+    assert np.max(np.abs(g[3:] - o[3:]).max(axis=0) / E) <= 1e-10
+    assert stats["reflections"] > 0 and stats["executed"] > 0
+
+
 def test_large_accepted_list_uses_global_sort_path():
     # one cell, ~10^4 accepted pairs: beyond the shared-memory list size
     L = (0.5, 0.5, 0.5)
