@@ -147,18 +147,19 @@ struct CellCtx {
     uint32_t slot;    // its counters row
 };
 
-// One entry of a warp's block queue: the Philox block and its row and
-// group (32 bytes, so an entry's address is one shift-add of its slot).
+// One entry of a warp's block queue: the Philox block, its row and group and
+// its cell (32 bytes, so an entry's address is one shift-add of its slot).
 struct __align__(16) QEntry {
     uint4 r;
-    uint32_t i, g, pad0, pad1;
+    uint32_t i, g, c, pad;
 };
 
 // Push a block onto the warp's queue iff its test word x has a bit of
 // 0x80808080 set: one predicate feeds the ballot and the two predicated
 // shared-memory stores.  qa is the shared address of the next free entry;
 // returns it after the warp's pushes.
-__device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t qa, uint4 r, uint32_t i, uint32_t g)
+__device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t qa, uint4 r, uint32_t i, uint32_t g,
+                                               uint32_t c)
 {
     uint32_t qa_out;
     asm volatile(
@@ -170,11 +171,11 @@ __device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t
         "popc.b32 t, t;\n\t"
         "mad.lo.u32 a, t, 32, %3;\n\t"
         "@p st.shared.v4.u32 [a], {%4, %5, %6, %7};\n\t"
-        "@p st.shared.v2.u32 [a+16], {%8, %9};\n\t"
+        "@p st.shared.v4.u32 [a+16], {%8, %9, %10, %10};\n\t"
         "popc.b32 t, b;\n\t"
         "mad.lo.u32 %0, t, 32, %3;\n\t}"
         : "=r"(qa_out)
-        : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g)
+        : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g), "r"(c)
         : "memory");
     return qa_out;
 }
@@ -401,7 +402,7 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
             const uint4 r = R.block(g + b, K);
             const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
                                ((r.w - t8) & ~r.w) | x0;
-            qa = queue_push(x, lt, qa, r, i, g + b);
+            qa = queue_push(x, lt, qa, r, i, g + b, cc.c);
         }
     }
     if (qa != q_s) {
@@ -410,6 +411,112 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
                                  acc, acc_cap, counters, active, stats);
         __syncwarp();
     }
+}
+
+// The warp-per-cell path keeps its block queue across cells: queued blocks
+// are resolved 32 at a time, each lane rebuilding its entry's cell context
+// (simulation, cell bounds, list segment), instead of a mostly idle resolve
+// at the end of every small cell.
+template <typename T, bool kOneKey>
+__device__ __forceinline__ void resolve_entries(const QEntry* q, uint32_t e0, uint32_t e1,
+                                                const SimDesc* __restrict__ sims, int nsims,
+                                                const T* __restrict__ st, uint32_t pcap,
+                                                const uint32_t* __restrict__ cell_start,
+                                                const uint2* __restrict__ work, uint4* sv, uint32_t* svn,
+                                                uint32_t* __restrict__ acc_count,
+                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                unsigned long long* __restrict__ stats, const PhiloxKey& Kp)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t e = e0 + lane; e < e1; e += 32) {
+        const uint4 r = q[e].r;
+        const uint32_t i = q[e].i, g = q[e].g, c = q[e].c;
+        const int s = sim_of_cell(sims, nsims, c);
+        const SimDesc& S = sims[s];
+        const uint32_t cbase = cell_start[c];
+        const uint32_t n = cell_start[c + 1] - cbase;
+        uint32_t m = block_le_mask(r, S.thr8) & valid_cols(g, i, n);
+        if (!m) continue;
+        const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
+        const PhiloxKey& K = kOneKey ? Kp : Kl;
+        const uint32_t lc = c - S.cell_off;
+        const uint4 mb = philox4x32_10(make_uint4(S.step, lc, i, kTagMid | g), K);
+        while (m) {
+            const uint32_t bit = (uint32_t)__ffs(m) - 1u;
+            m &= m - 1u;
+            const uint32_t r16 = (block_byte(r, bit) << 8) | block_byte(mb, bit);
+            if (r16 > S.thr16) continue;
+            const uint32_t j = 16u * g + bit;
+            const uint32_t pos = atomicAdd(svn, 1u);
+            if (pos < kSurvBuf) {
+                sv[pos] = make_uint4(c, i, j, r16);
+            } else {
+                CellCtx cc;
+                cc.c = c;
+                cc.s = s;
+                cc.slot = S.stat_slot;
+                cc.lc = lc;
+                cc.cbase = cbase;
+                cc.n = n;
+                const uint2 w0 = work[c], w1 = work[c + 1];
+                cc.list0 = w0.y;
+                cc.room = w1.y - w0.y;
+                eval_survivor<T, false>(cc, K, S.step, sim_C<T>(S), sim_m2<T>(S), st, pcap, i, j, r16, acc_count, acc,
+                                        acc_cap, counters, active, stats);
+            }
+        }
+    }
+}
+
+// All pairs of one small cell (n <= small_max) on the warp, pushing onto the
+// warp's persistent queue at shared address qa (returned); full queues are
+// drained with resolve_entries.
+template <typename T, bool kOneKey, int NB>
+__device__ __forceinline__ uint32_t pair_cell_small(uint32_t c, uint32_t lc, uint32_t n, uint32_t step, uint32_t thr8,
+                                                    const PhiloxKey& K, QEntry* q, uint32_t qa,
+                                                    const SimDesc* __restrict__ sims, int nsims,
+                                                    const T* __restrict__ st, uint32_t pcap,
+                                                    const uint32_t* __restrict__ cell_start,
+                                                    const uint2* __restrict__ work, uint4* sv, uint32_t* svn,
+                                                    uint32_t* __restrict__ acc_count,
+                                                    unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                                    uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                                    unsigned long long* __restrict__ stats, const PhiloxKey& Kp)
+{
+    constexpr int kQueueCap = queue_cap(NB);
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t q_s = (uint32_t)__cvta_generic_to_shared(q);
+    const uint32_t qa_drain = q_s + 32u * (uint32_t)(kQueueCap - 32 * NB);
+    const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
+    const uint32_t glast = (n - 1) >> 4;
+    for (uint32_t rb = 0; rb < nrb; ++rb) {
+        const uint32_t i = rb * kPairRows + lane;
+        const bool row_ok = i + 1 < n;
+        PhiloxRow R;
+        R.init(step, lc, i, K);
+        const uint32_t t8 = row_ok ? 0x01010101u * (thr8 + 1u) : 0u;
+        const uint32_t x0 = (row_ok && thr8 >= 128u) ? 0x80000000u : 0u;
+        for (uint32_t g = (rb * kPairRows + 1) >> 4; g <= glast; g += NB) {
+            while (qa > qa_drain) {
+                const uint32_t qn = (qa - q_s) >> 5;
+                __syncwarp();
+                resolve_entries<T, kOneKey>(q, qn - 32, qn, sims, nsims, st, pcap, cell_start, work, sv, svn,
+                                            acc_count, acc, acc_cap, counters, active, stats, Kp);
+                __syncwarp();
+                qa -= 32u * 32u;
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const uint4 r = R.block(g + b, K);
+                const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
+                                   ((r.w - t8) & ~r.w) | x0;
+                qa = queue_push(x, lt, qa, r, i, g + b, c);
+            }
+        }
+    }
+    return qa;
 }
 
 // ---------------------------------------------------------------------------
@@ -659,16 +766,11 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
     if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kWarps;
+    const uint32_t q_s = (uint32_t)__cvta_generic_to_shared(q_e[w]);
+    uint32_t qa = q_s;  // the warp's queue, kept across cells
     for (uint32_t c0 = (blockIdx.x * kWarps + w) * 32u; c0 < ncells; c0 += nwarps * 32u) {
         const uint32_t cl = c0 + lane;
-        uint32_t my_base = 0, my_n = 0, my_list0 = 0, my_room = 0;
-        if (cl < ncells) {
-            my_base = cell_start[cl];
-            my_n = cell_start[cl + 1] - my_base;
-            const uint2 w0 = work[cl], w1 = work[cl + 1];
-            my_list0 = w0.y;
-            my_room = w1.y - w0.y;
-        }
+        const uint32_t my_n = cl < ncells ? cell_start[cl + 1] - cell_start[cl] : 0u;
         unsigned todo = __ballot_sync(kFull, cl < ncells && my_n >= 2 && my_n <= small_max);
         while (todo) {
             const int k = __ffs(todo) - 1;
@@ -678,26 +780,21 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
             const int s = sim_of_cell(sims, nsims, c);
             const SimDesc& S = sims[s];
             if (!(S.C > 0.0) || S.skip) continue;  // skip-ahead cells: k_pair_skip
-            CellCtx cc;
-            cc.c = c;
-            cc.s = s;
-            cc.slot = S.stat_slot;
-            cc.lc = c - S.cell_off;
-            cc.cbase = __shfl_sync(kFull, my_base, k);
-            cc.n = n;
-            cc.list0 = __shfl_sync(kFull, my_list0, k);
-            cc.room = __shfl_sync(kFull, my_room, k);
             const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
             const PhiloxKey& K = kOneKey ? Kp : Kl;
-            const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
-            for (uint32_t rb = 0; rb < nrb; ++rb)
-                pair_rows<T, false, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap,
-                                        q_e[w], s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active,
-                                        stats);
+            qa = pair_cell_small<T, kOneKey, NB>(c, c - S.cell_off, n, S.step, S.thr8, K, q_e[w], qa, sims, nsims, st,
+                                                 pcap, cell_start, work, s_v[w], &s_vn[w], acc_count, acc, acc_cap,
+                                                 counters, active, stats, Kp);
             __syncwarp();
             if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
                 flush_survivors(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, counters);
         }
+    }
+    if (qa != q_s) {
+        __syncwarp();
+        resolve_entries<T, kOneKey>(q_e[w], 0, (qa - q_s) >> 5, sims, nsims, st, pcap, cell_start, work, s_v[w],
+                                    &s_vn[w], acc_count, acc, acc_cap, counters, active, stats, Kp);
+        __syncwarp();
     }
     drain_survivors<T, kOneKey>(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, sims, nsims, st, pcap, cell_start, work,
                                 acc_count, acc, acc_cap, counters, active, stats, Kp);
