@@ -156,27 +156,46 @@ struct __align__(16) QEntry {
 
 // Push a block onto the warp's queue iff its test word x has a bit of
 // 0x80808080 set: one predicate feeds the ballot and the two predicated
-// shared-memory stores.  qa is the shared address of the next free entry;
-// returns it after the warp's pushes.
+// shared-memory stores (kCell: the entry's cell too, for a queue that spans
+// cells).  qa is the shared address of the next free entry; returns it after
+// the warp's pushes.
+template <bool kCell>
 __device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t qa, uint4 r, uint32_t i, uint32_t g,
                                                uint32_t c)
 {
     uint32_t qa_out;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b32 t, b, a;\n\t"
-        "and.b32 t, %1, 0x80808080;\n\t"
-        "setp.ne.u32 p, t, 0;\n\t"
-        "vote.sync.ballot.b32 b, p, 0xffffffff;\n\t"
-        "and.b32 t, b, %2;\n\t"
-        "popc.b32 t, t;\n\t"
-        "mad.lo.u32 a, t, 32, %3;\n\t"
-        "@p st.shared.v4.u32 [a], {%4, %5, %6, %7};\n\t"
-        "@p st.shared.v4.u32 [a+16], {%8, %9, %10, %10};\n\t"
-        "popc.b32 t, b;\n\t"
-        "mad.lo.u32 %0, t, 32, %3;\n\t}"
-        : "=r"(qa_out)
-        : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g), "r"(c)
-        : "memory");
+    if (kCell)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b32 t, b, a;\n\t"
+            "and.b32 t, %1, 0x80808080;\n\t"
+            "setp.ne.u32 p, t, 0;\n\t"
+            "vote.sync.ballot.b32 b, p, 0xffffffff;\n\t"
+            "and.b32 t, b, %2;\n\t"
+            "popc.b32 t, t;\n\t"
+            "mad.lo.u32 a, t, 32, %3;\n\t"
+            "@p st.shared.v4.u32 [a], {%4, %5, %6, %7};\n\t"
+            "@p st.shared.v4.u32 [a+16], {%8, %9, %10, %10};\n\t"
+            "popc.b32 t, b;\n\t"
+            "mad.lo.u32 %0, t, 32, %3;\n\t}"
+            : "=r"(qa_out)
+            : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g), "r"(c)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b32 t, b, a;\n\t"
+            "and.b32 t, %1, 0x80808080;\n\t"
+            "setp.ne.u32 p, t, 0;\n\t"
+            "vote.sync.ballot.b32 b, p, 0xffffffff;\n\t"
+            "and.b32 t, b, %2;\n\t"
+            "popc.b32 t, t;\n\t"
+            "mad.lo.u32 a, t, 32, %3;\n\t"
+            "@p st.shared.v4.u32 [a], {%4, %5, %6, %7};\n\t"
+            "@p st.shared.v2.u32 [a+16], {%8, %9};\n\t"
+            "popc.b32 t, b;\n\t"
+            "mad.lo.u32 %0, t, 32, %3;\n\t}"
+            : "=r"(qa_out)
+            : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g)
+            : "memory");
     return qa_out;
 }
 
@@ -402,7 +421,7 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
             const uint4 r = R.block(g + b, K);
             const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
                                ((r.w - t8) & ~r.w) | x0;
-            qa = queue_push(x, lt, qa, r, i, g + b, cc.c);
+            qa = queue_push<false>(x, lt, qa, r, i, g + b, cc.c);
         }
     }
     if (qa != q_s) {
@@ -512,7 +531,7 @@ __device__ __forceinline__ uint32_t pair_cell_small(uint32_t c, uint32_t lc, uin
                 const uint4 r = R.block(g + b, K);
                 const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
                                    ((r.w - t8) & ~r.w) | x0;
-                qa = queue_push(x, lt, qa, r, i, g + b, c);
+                qa = queue_push<true>(x, lt, qa, r, i, g + b, c);
             }
         }
     }
