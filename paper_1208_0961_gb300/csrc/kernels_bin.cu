@@ -4,10 +4,11 @@
 //
 // The state is sorted by cell at the start of a step.  The first kernel
 // streams every particle in registers (A1, A2), computes its new cell key
-// (A3) and the tile histogram of the key's first digit, writing only the key;
-// the streamed state is never stored there.  It is recomputed, from the
-// unmodified old state with the same IEEE operations and so to the same bits,
-// by the kernel that writes each particle into its sorted slot (A4):
+// (A3) and the tile histogram of the key's first digit, writing only the key
+// (FP32) or the key and the streamed state in place (FP64).  In FP32 the
+// streamed state is recomputed, from the unmodified old state with the same
+// IEEE operations and so to the same bits, by the kernel that writes each
+// particle into its sorted slot (A4):
 //   one pass:  the ranking kernel itself (it reads the old state in order and
 //              writes runs of sorted slots, since particles move little);
 //              cell_start is the scanned digit histogram;
@@ -34,6 +35,11 @@
 namespace cuba {
 
 constexpr int kWarpsPerTile = kSortThreads / 32;
+// FP64 streaming is bound by the FP64 divisions and square root (a small
+// fraction of the FP32 rate on this GPU), so in FP64 the first kernel writes
+// the streamed state back in place and the sorted write copies it instead of
+// streaming again; in FP32 re-streaming is cheaper than that extra write.
+template <typename T> struct StreamInPlace { static constexpr bool value = sizeof(T) == 8; };
 constexpr int kDigitsPerThread = kBinBins / kSortThreads;
 #ifndef CUBA_BIN_MIN_BLOCKS
 #define CUBA_BIN_MIN_BLOCKS 4   // resident ranking blocks per SM the register budget targets
@@ -72,7 +78,7 @@ __device__ __forceinline__ void store_tile_hist(const uint32_t* h, uint32_t* __r
 // are taken four rounds at a time so that their loads overlap.
 template <typename T>
 __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __restrict__ sims, int nsims,
-                                                              const T* __restrict__ st, uint32_t pcap, uint32_t n,
+                                                              T* __restrict__ st, uint32_t pcap, uint32_t n,
                                                               uint32_t* __restrict__ keys_out, int shift,
                                                               uint32_t* __restrict__ hist,
                                                               unsigned long long* __restrict__ stats)
@@ -95,6 +101,7 @@ __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __r
             T pos[3], mom[3];
             load_particle<T>(st, pcap, i, pos, mom);
             const int nr = stream_one<T>(S, pos, mom);
+            if (StreamInPlace<T>::value) store_particle<T>(st, pcap, i, pos, mom);
             if (nr) {
                 if (S.stat_slot != cur_slot) {
                     if (nref) atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)nref);
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
             const int s = sim_of_particle(sims, nsims, i);
             T x[3], m[3];
             load_particle<T>(st_old, pcap, i, x, m);
-            stream_one<T>(sims[s], x, m);
+            if (!StreamInPlace<T>::value) stream_one<T>(sims[s], x, m);
             store_particle<T>(st_new, pcap, p, x, m);
             if (perm) perm[p] = i;
         }
@@ -392,7 +399,7 @@ __global__ void __launch_bounds__(256) k_bin_gather(const SimDesc* __restrict__ 
         const int s = sim_of_particle(sims, nsims, g);
         T x[3], p[3];
         load_particle<T>(st_old, pcap, g, x, p);
-        stream_one<T>(sims[s], x, p);
+        if (!StreamInPlace<T>::value) stream_one<T>(sims[s], x, p);
         store_particle<T>(st_new, pcap, k, x, p);
         const uint32_t kk = skey[k];
         const int64_t prev = (k == 0) ? -1 : (int64_t)skey[k - 1];
@@ -459,10 +466,10 @@ int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
     uint32_t* off = A.radix_hist + (size_t)kBinBins * ntiles;
     const bool fp64 = A.precision == 1;
     if (fp64)
-        k_stream_hist<double><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, n,
+        k_stream_hist<double><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, n,
                                                                A.key[0], 0, hist, A.stats);
     else
-        k_stream_hist<float><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, n,
+        k_stream_hist<float><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap, n,
                                                               A.key[0], 0, hist, A.stats);
     if (after_stream) cudaEventRecord(after_stream, st);
     if (A.trace) cudaMemcpyAsync(A.trace_keys, A.key[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
