@@ -453,6 +453,12 @@ def run_batch_mode(args):
     torch.cuda.synchronize()
     b.step(args.warmup, stream)
     torch.cuda.synchronize()
+    # the launch shape for the whole batch (timed on its live state, which is
+    # restored); the one-at-a-time loop below keeps the library's default
+    # shape, which is faster for it than the batch's
+    shape, tune_ms = (cuba.cuba_batch_autotune_shape(b.h, 1, stream) if args.autotune
+                      else (None, None))
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier(world)
@@ -491,6 +497,7 @@ def run_batch_mode(args):
                 "particles": int(tot), "cells": int(sum_over_ranks(C, world)) if world > 1 else C,
                 "pair_tests_per_step": pair_tests,
                 "alone": {"value": tot * args.steps / (alone_ms / 1000.0), "ms_per_step": alone_ms / args.steps},
+                "launch_shape": shape, "autotune_ms": tune_ms,
                 "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
         line["speedup_vs_alone"] = line["value"] / line["alone"]["value"]
         print(json.dumps(line), flush=True)
