@@ -37,6 +37,7 @@ constexpr int kNbrDirs = 27;
 constexpr int kNbrThreads = 256;
 constexpr int kNbrWarps = kNbrThreads / 32;
 constexpr unsigned kNbrFull = 0xffffffffu;
+constexpr int kNbrGroup = 2;   // scatter rounds whose loads are issued together
 
 // Key offset of the source cell of direction d (new key = old key + delta).
 __device__ __forceinline__ int32_t nbr_delta(const SimDesc& S, int d)
@@ -171,47 +172,66 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
         if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1) run[w][d] += (uint32_t)__popc(peers);
         __syncwarp();
     }
-    for (int r = 0; r < kSortItems; ++r) {
-        const uint32_t i = base + r * 32 + lane;
-        if (base + r * 32 >= n) break;
-        uint32_t key = 0xFFFFFFFFu, c = 0xFFFFFFFFu, dest = 0;
-        int d = 0;
-        T pos[3], mom[3];
-        if (i < n) {
-            const SimDesc& S = sims[sim_of_particle(sims, nsims, i)];
-            nbr_load<T>(st_old, pcap, i, pos, mom);
-            uint32_t nr = 0;
-            if (nbr_move<T>(S, pos, mom, c, d, dest, nr))
-                key = (c << 5) | (uint32_t)d;
-            else
-                atomicOr(&counters[1], kErrMove);
-        }
-        const unsigned peers = __match_any_sync(kNbrFull, key);
-        if (key != 0xFFFFFFFFu) {
-            const uint32_t slot = cs_new[dest] + rel[(size_t)d * rel_stride + c] + (c == carry ? run[w][d] : 0u) +
-                                  (uint32_t)__popc(peers & lt);
-            if (slot < n) {
+    // rounds are taken kNbrGroup at a time: their loads and the gathers of
+    // their slot bases are issued together, the rank carry is then applied
+    // round by round
+    for (int r0 = 0; r0 < kSortItems; r0 += kNbrGroup) {
+        if (base + r0 * 32 >= n) break;
+        uint32_t key[kNbrGroup], c[kNbrGroup], dest[kNbrGroup], sb[kNbrGroup];
+        int d[kNbrGroup];
+        T pos[kNbrGroup][3], mom[kNbrGroup][3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    st_new[(size_t)a * pcap + slot] = pos[a];
-                    st_new[(size_t)(3 + a) * pcap + slot] = mom[a];
-                }
-                if (perm) perm[slot] = i;
-            } else {
-                atomicOr(&counters[1], kErrMove);
+        for (int k = 0; k < kNbrGroup; ++k) {
+            const uint32_t i = base + (r0 + k) * 32 + lane;
+            key[k] = 0xFFFFFFFFu;
+            c[k] = 0xFFFFFFFFu;
+            dest[k] = 0;
+            d[k] = 0;
+            if (i < n) {
+                const SimDesc& S = sims[sim_of_particle(sims, nsims, i)];
+                nbr_load<T>(st_old, pcap, i, pos[k], mom[k]);
+                uint32_t nr = 0;
+                if (nbr_move<T>(S, pos[k], mom[k], c[k], d[k], dest[k], nr))
+                    key[k] = (c[k] << 5) | (uint32_t)d[k];
+                else
+                    atomicOr(&counters[1], kErrMove);
             }
         }
-        // the cell of the round's last particle carries into the next round
-        const uint32_t last_lane = min(31u, n - 1 - (base + r * 32));
-        const uint32_t last = __shfl_sync(kNbrFull, c, (int)last_lane);
-        __syncwarp();
-        if (last != carry) {
-            run[w][lane] = 0;
-            carry = last;
+#pragma unroll
+        for (int k = 0; k < kNbrGroup; ++k)
+            sb[k] = key[k] != 0xFFFFFFFFu ? cs_new[dest[k]] + rel[(size_t)d[k] * rel_stride + c[k]] : 0u;
+#pragma unroll
+        for (int k = 0; k < kNbrGroup; ++k) {
+            const uint32_t r_lo = base + (r0 + k) * 32;
+            if (r_lo >= n) break;
+            const uint32_t i = r_lo + lane;
+            const unsigned peers = __match_any_sync(kNbrFull, key[k]);
+            if (key[k] != 0xFFFFFFFFu) {
+                const uint32_t slot = sb[k] + (c[k] == carry ? run[w][d[k]] : 0u) + (uint32_t)__popc(peers & lt);
+                if (slot < n) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        st_new[(size_t)a * pcap + slot] = pos[k][a];
+                        st_new[(size_t)(3 + a) * pcap + slot] = mom[k][a];
+                    }
+                    if (perm) perm[slot] = i;
+                } else {
+                    atomicOr(&counters[1], kErrMove);
+                }
+            }
+            // the cell of the round's last particle carries into the next round
+            const uint32_t last_lane = min(31u, n - 1 - r_lo);
+            const uint32_t last = __shfl_sync(kNbrFull, c[k], (int)last_lane);
+            __syncwarp();
+            if (last != carry) {
+                run[w][lane] = 0;
+                carry = last;
+            }
+            __syncwarp();
+            if (key[k] != 0xFFFFFFFFu && c[k] == carry && lane == __ffs(peers) - 1)
+                run[w][d[k]] += (uint32_t)__popc(peers);
+            __syncwarp();
         }
-        __syncwarp();
-        if (key != 0xFFFFFFFFu && c == carry && lane == __ffs(peers) - 1) run[w][d] += (uint32_t)__popc(peers);
-        __syncwarp();
     }
 }
 
