@@ -1161,7 +1161,7 @@ __device__ __forceinline__ void flush_resolve_stats(uint32_t slot, unsigned long
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_resolve_small(const SimDesc* __restrict__ sims, int nsims, T* __restrict__ st,
+__global__ void __launch_bounds__(256, 4) k_resolve_small(const SimDesc* __restrict__ sims, int nsims, T* __restrict__ st,
                                                        uint32_t pcap, const uint32_t* __restrict__ cell_start,
                                                        const uint2* __restrict__ work, uint32_t ncells,
                                                        uint32_t small_max, const uint32_t* __restrict__ acc_count,
