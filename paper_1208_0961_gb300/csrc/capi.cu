@@ -258,8 +258,7 @@ int sample_regions(Arena& A, int sim_index, const SimDesc& S, int64_t n, const c
 int settle_arena(Arena& A, cudaStream_t st, int* realloc)
 {
     if (realloc) *realloc = 0;
-    if (launch_keys_only(A, st)) return fail(CUBA_ERR_CUDA, "key launch failed");
-    if (launch_sort_and_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
+    if (launch_settle_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
     if (launch_cell_prep(A, st, 0)) return fail(CUBA_ERR_CUDA, "cell preparation failed");
     uint2 tot;
     CUDA_TRY(cudaMemcpyAsync(&tot, A.cell_work + A.ncells, sizeof(uint2), cudaMemcpyDeviceToHost, st), "read list size");

@@ -229,8 +229,7 @@ struct Arena {
 int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double* d_regions, int nreg,
                         const uint64_t* d_region_first, cudaStream_t st);
 int launch_init_hotspot(const Arena& A, const SimDesc& S, double T0, double dT, double width, cudaStream_t st);
-int launch_keys_only(const Arena& A, cudaStream_t st);
-int launch_sort_and_bin(Arena& A, cudaStream_t st);   // keys in key[0] -> sorted state, cell_start
+int launch_settle_bin(Arena& A, cudaStream_t st);   // present positions -> keys, sorted state, cell_start
 int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st);
 int launch_cell_bounds(const uint32_t* skey, uint32_t np, uint32_t* cell_start, uint32_t ncells, cudaStream_t st);
 int scan_u32(uint32_t* data, size_t n, void* tmp, size_t tmp_bytes, cudaStream_t st);

@@ -40,6 +40,8 @@ constexpr int kWarpsPerTile = kSortThreads / 32;
 // the streamed state back in place and the sorted write copies it instead of
 // streaming again; in FP32 re-streaming is cheaper than that extra write.
 template <typename T> struct StreamInPlace { static constexpr bool value = sizeof(T) == 8; };
+// kStream = false: the same kernels bin a state as it is (the settling sort
+// of a new state): no streaming, the sorted write copies.
 constexpr int kDigitsPerThread = kBinBins / kSortThreads;
 #ifndef CUBA_BIN_MIN_BLOCKS
 #define CUBA_BIN_MIN_BLOCKS 4   // resident ranking blocks per SM the register budget targets
@@ -76,7 +78,7 @@ __device__ __forceinline__ void store_tile_hist(const uint32_t* h, uint32_t* __r
 
 // Pass 0: stream, key, digit histogram of the tile.  The particles of a warp
 // are taken four rounds at a time so that their loads overlap.
-template <typename T>
+template <typename T, bool kStream>
 __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __restrict__ sims, int nsims,
                                                               T* __restrict__ st, uint32_t pcap, uint32_t n,
                                                               uint32_t* __restrict__ keys_out, int shift,
@@ -100,8 +102,8 @@ __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __r
             const SimDesc& S = sims[s];
             T pos[3], mom[3];
             load_particle<T>(st, pcap, i, pos, mom);
-            const int nr = stream_one<T>(S, pos, mom);
-            if (StreamInPlace<T>::value) store_particle<T>(st, pcap, i, pos, mom);
+            const int nr = kStream ? stream_one<T>(S, pos, mom) : 0;
+            if (kStream && StreamInPlace<T>::value) store_particle<T>(st, pcap, i, pos, mom);
             if (nr) {
                 if (S.stat_slot != cur_slot) {
                     if (nref) atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)nref);
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
 // One pass: rank by the (only) digit, re-stream each particle from the old
 // state and write it into its sorted slot; perm (tracing only) receives the
 // origin of each slot.
-template <typename T>
+template <typename T, bool kStream>
 __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
     k_bin_final(const SimDesc* __restrict__ sims, int nsims, const uint32_t* __restrict__ key_in,
                 const T* __restrict__ st_old, T* __restrict__ st_new, uint32_t pcap, uint32_t n,
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
             const int s = sim_of_particle(sims, nsims, i);
             T x[3], m[3];
             load_particle<T>(st_old, pcap, i, x, m);
-            if (!StreamInPlace<T>::value) stream_one<T>(sims[s], x, m);
+            if (kStream && !StreamInPlace<T>::value) stream_one<T>(sims[s], x, m);
             store_particle<T>(st_new, pcap, p, x, m);
             if (perm) perm[p] = i;
         }
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
 
 // Two passes: sorted slot k takes particle perm[k], re-streamed from the old
 // state; cell_start[c] = first sorted slot with key >= c.
-template <typename T>
+template <typename T, bool kStream>
 __global__ void __launch_bounds__(256) k_bin_gather(const SimDesc* __restrict__ sims, int nsims,
                                                     const uint32_t* __restrict__ perm,
                                                     const uint32_t* __restrict__ skey, const T* __restrict__ st_old,
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(256) k_bin_gather(const SimDesc* __restrict__ 
         const int s = sim_of_particle(sims, nsims, g);
         T x[3], p[3];
         load_particle<T>(st_old, pcap, g, x, p);
-        if (!StreamInPlace<T>::value) stream_one<T>(sims[s], x, p);
+        if (kStream && !StreamInPlace<T>::value) stream_one<T>(sims[s], x, p);
         store_particle<T>(st_new, pcap, k, x, p);
         const uint32_t kk = skey[k];
         const int64_t prev = (k == 0) ? -1 : (int64_t)skey[k - 1];
@@ -418,10 +420,16 @@ int bin_kernels_init()
 {
     if (cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) != cudaSuccess)
         return -1;
-    if (cudaFuncSetAttribute(k_bin_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
+    if (cudaFuncSetAttribute(k_bin_final<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
         cudaSuccess)
         return -1;
-    if (cudaFuncSetAttribute(k_bin_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
+    if (cudaFuncSetAttribute(k_bin_final<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
+        cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(k_bin_final<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
+        cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(k_bin_final<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
         cudaSuccess)
         return -1;
     return 0;
@@ -451,7 +459,8 @@ static int col_scan(const Arena& A, const uint32_t* hist, uint32_t* off, uint32_
 // st[cur] is left untouched, the new sorted state goes to st[cur ^ 1] (cur
 // flips), cell_start is written; with tracing on, the keys before sorting go
 // to trace_keys and the permutation to idx[sorted_buf].
-int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
+template <bool kStream>
+static int step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
 {
     const uint32_t n = A.np;
     if (n == 0) {
@@ -466,10 +475,10 @@ int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
     uint32_t* off = A.radix_hist + (size_t)kBinBins * ntiles;
     const bool fp64 = A.precision == 1;
     if (fp64)
-        k_stream_hist<double><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, n,
+        k_stream_hist<double, kStream><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, n,
                                                                A.key[0], 0, hist, A.stats);
     else
-        k_stream_hist<float><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap, n,
+        k_stream_hist<float, kStream><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap, n,
                                                               A.key[0], 0, hist, A.stats);
     if (after_stream) cudaEventRecord(after_stream, st);
     if (A.trace) cudaMemcpyAsync(A.trace_keys, A.key[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
@@ -477,12 +486,12 @@ int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
         if (col_scan(A, hist, off, ntiles, A.cell_start, st)) return -1;
         uint32_t* perm = A.trace ? A.idx[1] : nullptr;
         if (fp64)
-            k_bin_final<double><<<ntiles, kSortThreads, kBinSmem, st>>>(A.d_sims, A.nsims, A.key[0],
+            k_bin_final<double, kStream><<<ntiles, kSortThreads, kBinSmem, st>>>(A.d_sims, A.nsims, A.key[0],
                                                                         (const double*)A.st[A.cur],
                                                                         (double*)A.st[A.cur ^ 1], A.pcap, n,
                                                                         off, perm);
         else
-            k_bin_final<float><<<ntiles, kSortThreads, kBinSmem, st>>>(A.d_sims, A.nsims, A.key[0],
+            k_bin_final<float, kStream><<<ntiles, kSortThreads, kBinSmem, st>>>(A.d_sims, A.nsims, A.key[0],
                                                                        (const float*)A.st[A.cur],
                                                                        (float*)A.st[A.cur ^ 1], A.pcap, n,
                                                                        off, perm);
@@ -499,17 +508,29 @@ int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
         }
         const unsigned g = (unsigned)std::min<uint32_t>((n + 255) / 256, (uint32_t)sm_count() * 8);
         if (fp64)
-            k_bin_gather<double><<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.idx[src], A.key[src],
+            k_bin_gather<double, kStream><<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.idx[src], A.key[src],
                                                     (const double*)A.st[A.cur], (double*)A.st[A.cur ^ 1], A.pcap, n,
                                                     A.cell_start, A.ncells);
         else
-            k_bin_gather<float><<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.idx[src], A.key[src],
+            k_bin_gather<float, kStream><<<g, 256, 0, st>>>(A.d_sims, A.nsims, A.idx[src], A.key[src],
                                                    (const float*)A.st[A.cur], (float*)A.st[A.cur ^ 1], A.pcap, n,
                                                    A.cell_start, A.ncells);
         A.sorted_buf = src;
     }
     A.cur ^= 1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
+{
+    return step_bin<true>(A, st, after_stream);
+}
+
+// The settling sort of a state as it is (keys of the present positions,
+// stable sort, cell_start), with the same kernels.
+int launch_settle_bin(Arena& A, cudaStream_t st)
+{
+    return step_bin<false>(A, st, nullptr);
 }
 
 }  // namespace cuba

@@ -1,7 +1,8 @@
-// Particle-parallel kernels of the step: thermal sampling, free streaming with
-// wall reflection and cell keys (A1-A3), the stable counting sort by cell
-// (A4, an LSD radix sort on 8-bit digits), the per-cell work preparation of the
-// pair step, and the FP64 observables (A8).
+// Particle-parallel kernels: thermal sampling, the per-cell work preparation of
+// the pair step, the FP64 observables and totals (A8), the adaptive time step,
+// scans, and the LSD radix sort on 8-bit digits that bins caller buffers
+// without allocation (the step's own stream, key and sort kernels are in
+// kernels_bin.cu and kernels_nbr.cu).
 //
 // Bit-reproducibility: the streaming, the key and the sampling positions use
 // explicitly rounded IEEE operations (__dadd_rn, __fdiv_rn, ...) in the order
@@ -17,20 +18,6 @@
 #include "stream.cuh"
 
 namespace cuba {
-
-// Keys of a state without moving it (after sampling or loading a state).
-template <typename T>
-__global__ void __launch_bounds__(256) k_keys_only(const SimDesc* __restrict__ sims, int nsims, const T* __restrict__ st,
-                                                   uint32_t pcap, uint32_t np, uint32_t* __restrict__ keys)
-{
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < np; g += stride) {
-        const int s = sim_of_particle(sims, nsims, g);
-        const SimDesc& S = sims[s];
-        T pos[3] = {st[g], st[pcap + g], st[2 * (size_t)pcap + g]};
-        keys[g] = S.cell_off + cell_key<T>(S, pos);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Thermal sampling (generation order; sorted afterwards)
@@ -279,7 +266,8 @@ int scan_u32(uint32_t* data, size_t n, void* tmp, size_t tmp_bytes, cudaStream_t
 }
 
 // ---------------------------------------------------------------------------
-// A4: stable LSD radix sort of the cell keys (8-bit digits)
+// Stable LSD radix sort of cell keys on 8-bit digits (binning without
+// allocation)
 // ---------------------------------------------------------------------------
 // Tile t covers keys [t * 4096, (t + 1) * 4096); warp w of a tile owns the
 // contiguous 512 keys starting at w * 512, processed 32 at a time in order.
@@ -354,26 +342,6 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         __syncwarp();
         if (ok && lane == __ffs(peers) - 1) wh[w][d] += (uint32_t)__popc(peers);
         __syncwarp();
-    }
-}
-
-// Gather the payload into sorted order and derive cell_start from the sorted
-// keys: cell_start[c] = first sorted position with key >= c.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
-                                                const T* __restrict__ src, T* __restrict__ dst, uint32_t pcap,
-                                                uint32_t np, uint32_t* __restrict__ cell_start, uint32_t ncells)
-{
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
-        const uint32_t s = perm[k];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) dst[(size_t)c * pcap + k] = src[(size_t)c * pcap + s];
-        const uint32_t kk = skey[k];
-        const int64_t prev = (k == 0) ? -1 : (int64_t)skey[k - 1];
-        for (int64_t c = prev + 1; c <= (int64_t)kk; ++c) cell_start[c] = k;
-        if (k == np - 1)
-            for (int64_t c = (int64_t)kk + 1; c <= (int64_t)ncells; ++c) cell_start[c] = np;
     }
 }
 
@@ -653,17 +621,6 @@ int launch_init_hotspot(const Arena& A, const SimDesc& S, double T0, double dT, 
     return last_err();
 }
 
-int launch_keys_only(const Arena& A, cudaStream_t st)
-{
-    if (A.np == 0) return 0;
-    const unsigned g = grid_for(A.np, 256, 8);
-    if (A.precision == 1)
-        k_keys_only<double><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap, A.np, A.key[0]);
-    else
-        k_keys_only<float><<<g, 256, 0, st>>>(A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap, A.np, A.key[0]);
-    return last_err();
-}
-
 int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st)
 {
     if (n == 0) return 0;
@@ -675,46 +632,6 @@ int launch_cell_bounds(const uint32_t* skey, uint32_t np, uint32_t* cell_start, 
 {
     if (np == 0) return launch_fill_u32(cell_start, ncells + 1, 0u, st);
     k_cell_bounds<<<grid_for(np, 256, 8), 256, 0, st>>>(skey, np, cell_start, ncells);
-    return last_err();
-}
-
-// Keys of the current state are in key[0].  Sorts the state into the other
-// buffer (A.cur flips), leaves the permutation in idx[final] and the sorted
-// keys in key[final], and writes cell_start.
-int launch_sort_and_bin(Arena& A, cudaStream_t st)
-{
-    const uint32_t n = A.np;
-    if (A.trace && n) cudaMemcpyAsync(A.trace_keys, A.key[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-    if (n == 0) {
-        k_fill_u32<<<grid_for(A.ncells + 1, 256, 4), 256, 0, st>>>(A.cell_start, A.ncells + 1, 0u);
-        return last_err();
-    }
-    const int passes = radix_passes(A.ncells);
-    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-    int src = 0;
-    if (passes == 0) {
-        // one cell: the order is unchanged
-        k_iota<<<grid_for(n, 256, 4), 256, 0, st>>>(A.idx[0], n);
-    }
-    for (int p = 0; p < passes; ++p) {
-        const int shift = p * kRadixBits;
-        k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(A.key[src], n, shift, ntiles, A.radix_hist);
-        if (exclusive_scan<uint32_t, U32Add>(A.radix_hist, (size_t)kRadixBins * ntiles, 0u, U32Add(), A.scan_tmp,
-                                             A.scan_tmp_bytes, st))
-            return -1;
-        k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(A.key[src], p == 0 ? nullptr : A.idx[src], A.key[src ^ 1],
-                                                         A.idx[src ^ 1], n, shift, ntiles, A.radix_hist);
-        src ^= 1;
-    }
-    const unsigned g = grid_for(n, 256, 8);
-    if (A.precision == 1)
-        k_gather<double><<<g, 256, 0, st>>>(A.idx[src], A.key[src], (const double*)A.st[A.cur], (double*)A.st[A.cur ^ 1],
-                                            A.pcap, n, A.cell_start, A.ncells);
-    else
-        k_gather<float><<<g, 256, 0, st>>>(A.idx[src], A.key[src], (const float*)A.st[A.cur], (float*)A.st[A.cur ^ 1],
-                                           A.pcap, n, A.cell_start, A.ncells);
-    A.cur ^= 1;
-    A.sorted_buf = src;
     return last_err();
 }
 
