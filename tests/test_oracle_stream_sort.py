@@ -141,3 +141,30 @@ def test_sigma0_riemann_profile_matches_free_streaming(t_end):
         assert stats.chi2.sf(np.sum(z * z), len(z)) > 1e-4
     # the profile is not trivially flat: the analytic solution varies by > 10 sigma
     assert np.ptp(A00) / np.median(s00) > 10
+
+
+def test_threads_do_not_change_results():
+    """The oracle parallelises over particles and cells only: one thread and
+    all threads give identical bits (state, accepted and executed pairs),
+    in FP64, in the FP32 mirror and in the skip-ahead mode."""
+    from paper_1208_0961_gb300 import workloads as W
+    cfg = W.riemann_1d(20000, 100, 0.05, 10.0)
+    st0 = W.thermal_state(20000, cfg["regions"], seed=3)
+    keep = O.threads()
+    try:
+        for fp32, skip in ((False, False), (True, False), (False, True)):
+            op = O.make_params(L=cfg["L"], n=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"],
+                               n_test=cfg["n_test"], fp32=fp32, seed=7, skip=skip)
+            s = st0.astype(np.float32).astype(np.float64) if fp32 else st0
+            out = []
+            for t in (1, max(2, keep)):
+                O.set_threads(t)
+                o, _, _, _ = O.sort(op, s)
+                for k in range(2):
+                    o, res = O.step(op, k, o)
+                out.append((o, res.accepted, res.executed))
+            assert np.array_equal(out[0][0], out[1][0])
+            assert np.array_equal(out[0][1], out[1][1])
+            assert np.array_equal(out[0][2], out[1][2])
+    finally:
+        O.set_threads(keep)
