@@ -440,6 +440,19 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red)
     return t;
 }
 
+// sqrt(e2) to FP64 accuracy for the FP64 sums of A8: one FP64 Newton step
+// from the FP32 square root, e0 + (e2 - e0^2) / (2 e0), with the FP32
+// reciprocal of e0 (FP64 square roots are slow on this GPU).  The FP32 start
+// is within 1e-7 relative, so the step leaves about 1e-14.
+__device__ __forceinline__ double energy_sqrt(double e2)
+{
+    const float s = __fsqrt_rn((float)e2);
+    if (!(s > 1e-30f) || !(s < 1e30f)) return sqrt(e2);
+    const double e0 = (double)s;
+    const double r = fma(-e0, e0, e2);
+    return fma(r, 0.5 * (double)__frcp_rn(s), e0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_observables(SimDesc S, const T* __restrict__ st, uint32_t pcap,
                                                      const uint32_t* __restrict__ cell_start, double* __restrict__ T00,
@@ -451,7 +464,7 @@ __global__ void __launch_bounds__(256) k_observables(SimDesc S, const T* __restr
         double se = 0.0, sx = 0.0;
         for (uint32_t k = b + threadIdx.x; k < e; k += blockDim.x) {
             const double qx = st[3 * (size_t)pcap + k], qy = st[4 * (size_t)pcap + k], qz = st[5 * (size_t)pcap + k];
-            se += sqrt(((qx * qx + qy * qy) + qz * qz) + S.m2);
+            se += energy_sqrt(((qx * qx + qy * qy) + qz * qz) + S.m2);
             sx += qx;
         }
         const double te = block_sum_fixed(se, red);
@@ -474,7 +487,7 @@ __global__ void __launch_bounds__(256) k_totals_partial(SimDesc S, const T* __re
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < S.np; k += stride) {
         const uint32_t g = S.p_off + k;
         const double qx = st[3 * (size_t)pcap + g], qy = st[4 * (size_t)pcap + g], qz = st[5 * (size_t)pcap + g];
-        a[0] += sqrt(((qx * qx + qy * qy) + qz * qz) + S.m2);
+        a[0] += energy_sqrt(((qx * qx + qy * qy) + qz * qz) + S.m2);
         a[1] += qx;
         a[2] += qy;
         a[3] += qz;
