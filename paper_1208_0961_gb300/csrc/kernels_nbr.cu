@@ -39,13 +39,6 @@ constexpr int kNbrWarps = kNbrThreads / 32;
 constexpr unsigned kNbrFull = 0xffffffffu;
 constexpr int kNbrGroup = 2;   // scatter rounds whose loads are issued together
 
-// Key offset of the source cell of direction d (new key = old key + delta).
-__device__ __forceinline__ int32_t nbr_delta(const SimDesc& S, int d)
-{
-    const int32_t dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-    return dx + S.n[0] * (dy + S.n[1] * dz);
-}
-
 template <typename T>
 __device__ __forceinline__ void nbr_load(const T* __restrict__ st, uint32_t pcap, uint32_t g, T pos[3], T mom[3])
 {
