@@ -291,7 +291,12 @@ __device__ __forceinline__ void flush_survivors(uint4* sv, uint32_t* svn, uint32
     if (v == 0 || (v & kSurvFull)) return;
     const uint32_t n = min(v, kSurvBuf);
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&counters[3], n);
+    if (lane == 0) {
+        // once the list is full the counter stops growing (no 32-bit wrap
+        // however many survivors a step has)
+        const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(&counters[3]);
+        base = cur >= surv_cap ? surv_cap : atomicAdd(&counters[3], n);
+    }
     base = __shfl_sync(kFull, base, 0);
     const uint32_t fit = base >= surv_cap ? 0u : min(n, surv_cap - base);
     uint4 e0 = make_uint4(0, 0, 0, 0), e1 = e0;
