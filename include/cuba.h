@@ -285,11 +285,13 @@ int cuba_trace_get(cuba_sim* sim, uint32_t* keys, uint32_t* perm, uint32_t* cell
  * Advance n_steps steps like cuba_step, but launched kernel by kernel (no
  * graph) with CUDA events between the phases; phase_ms (host, 6 doubles)
  * receives the summed device time of each phase over the steps:
- * [0] stream/reflect/key with the first digit histogram, [1] the rest of
- * the sort (scans, radix passes, the final pass that re-streams each particle
- * into its sorted slot, cell_start),
- * [2] per-cell preparation, [3] pair tile, [4] conflicts + kinematics,
- * [5] step counter.  Synchronous.  For measurement.
+ * [0] stream/reflect/key with the first digit histogram (or, for arenas of
+ * many small cells, the neighbour-move sort's counting pass), [1] the rest of
+ * the sort (scans, radix passes or the neighbour offsets, the final pass that
+ * re-streams each particle into its sorted slot, cell_start),
+ * [2] per-cell preparation, [3] pair kernels (including the survivor
+ * kernel), [4] conflicts + kinematics, [5] step counter.  Synchronous.  For
+ * measurement.
  */
 int cuba_step_profiled(cuba_sim* sim, int n_steps, double* phase_ms, void* stream);
 
