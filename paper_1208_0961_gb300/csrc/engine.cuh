@@ -133,7 +133,7 @@ constexpr int kPairThreads = 256;
 // round keys are kernel parameters (constant-bank operands): four blocks run
 // uncapped (94 registers in FP32, two blocks of 256 per SM: measured faster
 // than 80 registers and three blocks, or 64 and four), eight capped at two
-// blocks of 256 per SM (124 registers in FP32).  With several simulations
+// blocks of 256 per SM (122 registers in FP32).  With several simulations
 // each warp holds its cell's round keys in registers, capped at 128 (four or
 // eight blocks) or 80 (two).
 template <bool kOneKey, int NB>

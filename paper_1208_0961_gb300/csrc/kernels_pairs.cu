@@ -377,9 +377,9 @@ __device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKe
 }
 
 // All pairs (i, j), i < j, of the rows [32 rb, 32 rb + 32) of one cell: one
-// lane per row walks the row's 16-pair Philox blocks two at a time; blocks
-// holding a byte <= thr8 are queued in the warp's shared-memory queue and
-// resolved 32 at a time.  kMark: the first accepted pair of the cell appends
+// lane per row walks the row's 16-pair Philox blocks NB at a time (2, 4 or 8,
+// by the launch shape); blocks holding a byte <= thr8 are queued in the
+// warp's shared-memory queue and resolved 32 at a time.  kMark: the first accepted pair of the cell appends
 // it to the active-cell list (the small-cell path finds its cells by scanning).
 template <typename T, bool kMark, int NB>
 __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32_t step, uint32_t thr8, uint32_t thr16,
@@ -765,8 +765,9 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
 
 // Small cells (2 <= n <= small_max): one warp per cell, all its rows, found
 // by a grid-stride scan over groups of 32 cells (no work queue, no per-cell
-// atomic); the bounds and list rooms of a group are read in one coalesced
-// round, one cell per lane, and handed to the cells' turns by shuffles.
+// atomic); the particle counts of a group are read in one coalesced round,
+// one cell per lane, and handed to the cells' turns by shuffles.  The warp's
+// block queue spans cells (pair_cell_small, resolve_entries).
 template <typename T, bool kOneKey, int NB>
 __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* __restrict__ sims, int nsims,
                                                              const T* __restrict__ st, uint32_t pcap,
