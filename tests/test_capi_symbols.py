@@ -5,6 +5,8 @@ import os
 import re
 import subprocess
 
+import pytest
+
 from paper_1208_0961_gb300 import cuba
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -64,3 +66,30 @@ def test_invalid_parameters_are_rejected_without_a_gpu():
     except cuba.CubaError as e:
         raised = e
     assert raised is not None and raised.code == cuba.CUBA_ERR_P22
+
+
+@pytest.mark.parametrize("kw,code,msg", [
+    (dict(dt=-0.01), "CUBA_ERR_INVALID", "dt must be > 0"),
+    (dict(sigma_fm2=-1.0), "CUBA_ERR_INVALID", "sigma"),
+    (dict(sigma_fm2=float("nan")), "CUBA_ERR_INVALID", "sigma"),
+    (dict(n_test=0.0), "CUBA_ERR_INVALID", "n_test"),
+    (dict(kappa=0.6), "CUBA_ERR_INVALID", "kappa"),
+    (dict(mass=-0.1), "CUBA_ERR_INVALID", "mass"),
+    (dict(mu=-0.1), "CUBA_ERR_INVALID", "mu"),
+    (dict(n_cells=(0, 1, 1)), "CUBA_ERR_INVALID", "n_cells"),
+    (dict(L=(0.0, 1.0, 1.0)), "CUBA_ERR_INVALID", "L[0]"),
+    (dict(acceptance=7), "CUBA_ERR_INVALID", "acceptance"),
+    (dict(precision=3), "CUBA_ERR_INVALID", "precision"),
+    # 2C = 1.0 exactly is allowed for the all-pairs test (P22 <= 2C), but
+    # skip-ahead needs 2.0001 C < 1
+    (dict(sigma_fm2=5.0, n_test=1.0, acceptance=1), "CUBA_ERR_P22", "skip-ahead"),
+])
+def test_parameter_validation_without_a_gpu(kw, code, msg):
+    # every check runs in parameter validation, before any CUDA call
+    args = dict(L=(1.0, 1.0, 1.0), n_cells=(10, 1, 1), dt=0.01, sigma_fm2=1.0, n_test=1.0)
+    args.update(kw)
+    p = cuba.make_params(**args)
+    with pytest.raises(cuba.CubaError) as e:
+        cuba.cuba_create(p, 10)
+    assert e.value.code == getattr(cuba, code)
+    assert msg in cuba.cuba_last_error()
