@@ -546,14 +546,7 @@ def run_serve_mode(args):
             "makespan_s": out["makespan_s"], "classes": args.serve_classes,
             "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
     if args.serve_alone:
-        pb = 4 if prec == cuba.CUBA_FP32 else 8
-
-        def factory(r):
-            nc = r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
-            return S.CudaBackend(2 * S.state_bytes(r.n, nc, pb) + (64 << 20), precision=prec, max_sims=1,
-                                 cells_per_particle=max(0.01, nc / max(1, r.n)), stream=stream)
-
-        alone = S.run_alone(factory, reqs)
+        alone = S.run_alone(lambda r: S.CudaBackend.for_request(r, precision=prec, stream=stream), reqs)
         line["alone"] = {"p50_s": alone["p50_s"], "p99_s": alone["p99_s"], "updates_per_s": alone["updates_per_s"],
                          "makespan_s": alone["makespan_s"]}
     print(json.dumps(line), flush=True)

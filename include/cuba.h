@@ -42,6 +42,7 @@
 #ifndef CUBA_H
 #define CUBA_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -140,6 +141,44 @@ typedef struct cuba_sim cuba_sim;
  */
 int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out);
 
+/*
+ * Device memory supplied by the caller.  Every device buffer of a simulation
+ * or batch created with an allocator — state, sort and cell tables, the
+ * accepted-pair list (allocated and grown by the synchronous calls that load
+ * or sample a state), scratch, temporaries of synchronous calls — comes from
+ * alloc and goes back through free; for that object the library calls
+ * neither cudaMalloc nor cudaFree.  This lets a caching allocator (PyTorch's,
+ * a memory pool) own the HBM that a server budgets.
+ *   alloc(bytes, ctx): device memory of the current device, aligned to at
+ *     least 256 bytes, or NULL; NULL fails the calling entry point with
+ *     CUBA_ERR_OOM and a misaligned block with CUBA_ERR_INVALID (after giving
+ *     it back).  Called from creation and from synchronous entry points only.
+ *   free(ptr, bytes, ctx): take back a block alloc returned; bytes is the
+ *     size that was asked for.  The library synchronizes the device before
+ *     it calls free, so no kernel still uses the block.
+ * The struct is copied at creation; ctx must stay valid until the object is
+ * destroyed, and both callbacks must be non-NULL (CUBA_ERR_INVALID).
+ */
+typedef struct cuba_allocator {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* ctx);
+    void* ctx;
+} cuba_allocator;
+
+/* cuba_create with every device buffer taken from `allocator` (above). */
+int cuba_create_with_allocator(const cuba_params* params, int64_t max_particles, const cuba_allocator* allocator,
+                               cuba_sim** out);
+
+/*
+ * Device bytes a simulation with these parameters and max_particles asks
+ * for: everything allocated at creation plus the smallest accepted-pair list
+ * (2^20 entries of 8 bytes, allocated by the first state load).  The list
+ * grows to four times the per-cell room of the loaded state when that is
+ * larger; tracing adds 4 max_particles bytes.  -1 for invalid arguments.
+ * Pure arithmetic: no CUDA call.
+ */
+int64_t cuba_sim_bytes(const cuba_params* params, int64_t max_particles);
+
 /* Free everything a simulation owns (NULL is ignored). */
 void cuba_destroy(cuba_sim* sim);
 
@@ -171,7 +210,6 @@ int cuba_init_riemann(cuba_sim* sim, int64_t n, double T_left, double T_right, v
 int cuba_init_hotspot(cuba_sim* sim, int64_t n, double T0, double dT, double width, void* stream);
 
 /*
- * Load a state of n particles (SoA x, y, z, px, py, pz/*
  * Load a state of n particles (SoA x, y, z, px, py, pz of the simulation's
  * element type, host or device memory, any order); the library sorts it by
  * cell, stably.  Positions must lie in [0, L].  Synchronous.
@@ -307,7 +345,6 @@ int cuba_kinematics_fp32(const float* pin, int64_t npairs, uint64_t key, uint32_
                          float* pout, int32_t* used_fp64, void* stream);
 
 /*
- * Philox4x32-10 of the library's device implementation/*
  * Philox4x32-10 of the library's device implementation for n counters
  * (4 words each) under one key, into out (4 words each).  ctr and out are
  * device pointers.  Async.  For verifying the generator.
@@ -340,6 +377,10 @@ typedef struct cuba_batch_config {
 
 /* Allocate an empty batch on the current device. */
 int cuba_batch_create(const cuba_batch_config* cfg, cuba_batch** out);
+/* The same with every device buffer taken from `allocator` (see
+   cuba_allocator). */
+int cuba_batch_create_with_allocator(const cuba_batch_config* cfg, const cuba_allocator* allocator,
+                                     cuba_batch** out);
 void cuba_batch_destroy(cuba_batch* b);
 
 /*
@@ -382,8 +423,13 @@ int cuba_batch_autotune_shape(cuba_batch* b, int n_steps, cuba_launch_shape* cho
 /* Occupancy: resident simulations, particles and cells in use. */
 int cuba_batch_usage(const cuba_batch* b, int32_t* n_sims, int64_t* n_particles, int64_t* n_cells);
 
-/* Device bytes a batch of this configuration allocates at creation (the
-   accepted-pair list, sized from occupancy, comes on top). */
+/* Device bytes a batch of this configuration asks for: everything allocated
+   at creation plus the smallest accepted-pair list (2^20 entries of 8 bytes,
+   allocated by the first admission).  The list grows, at admissions, to four
+   times the per-cell room of the residents when that is larger (room of a
+   cell of n particles: mu + 8 sqrt(mu) + 16 entries, mu = 2.0001 C n (n - 1)
+   / 2); a server budgets that on top.  -1 for an invalid configuration.
+   Pure arithmetic: no CUDA call. */
 int64_t cuba_batch_bytes(const cuba_batch_config* cfg);
 
 /*

@@ -94,14 +94,54 @@ int make_desc(const cuba_params* p, SimDesc* S)
     return CUBA_OK;
 }
 
+int arena_dalloc_raw(Arena& A, void** ptr, size_t bytes, const char* what)
+{
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (A.mem_alloc) {
+        p = A.mem_alloc(bytes, A.mem_ctx);
+        if (!p) return fail(CUBA_ERR_OOM, "caller allocator returned NULL for %s (%zu bytes)", what, bytes);
+        if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+            A.mem_free(p, bytes, A.mem_ctx);
+            return fail(CUBA_ERR_INVALID, "caller allocator returned %p for %s: not 256-byte aligned", p, what);
+        }
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CUBA_ERR_OOM, "cudaMalloc %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+        }
+    }
+    A.mem_blocks.push_back({p, bytes});
+    *ptr = p;
+    return CUBA_OK;
+}
+
+// A block goes back only once no kernel can still use it: cudaFree waits for
+// the device itself; before a caller's free the device is synchronized here.
+static void give_back(const Arena& A, const Arena::Block& b)
+{
+    if (A.mem_free) A.mem_free(b.ptr, b.bytes, A.mem_ctx);
+    else cudaFree(b.ptr);
+}
+
+void arena_dfree(Arena& A, void* ptr)
+{
+    if (!ptr) return;
+    for (size_t k = 0; k < A.mem_blocks.size(); ++k)
+        if (A.mem_blocks[k].ptr == ptr) {
+            if (A.mem_free) cudaDeviceSynchronize();
+            give_back(A, A.mem_blocks[k]);
+            A.mem_blocks.erase(A.mem_blocks.begin() + k);
+            return;
+        }
+}
+
 void arena_free(Arena& A)
 {
-    void* ptrs[] = {A.st[0], A.st[1], A.key[0], A.key[1], A.idx[0], A.idx[1], A.cell_start, A.cell_work, A.skip_work, A.surv,
-                    A.nbr_rel, A.nbr_cs,
-                    A.acc_count, A.acc, A.radix_hist, A.scan_tmp, A.counters, A.active, A.used_bits, A.stats,
-                    A.d_sims, A.trace_keys};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    if (A.mem_free && !A.mem_blocks.empty()) cudaDeviceSynchronize();
+    for (const Arena::Block& b : A.mem_blocks) give_back(A, b);
     A = Arena();
 }
 
@@ -115,47 +155,81 @@ size_t scan_tmp_needed(uint32_t pcap, uint32_t ccap)
     return std::max<size_t>(need, 256 * 4 * sizeof(double)) + 256;
 }
 
-int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simcap)
+ArenaPlan arena_plan(int precision, uint32_t pcap, uint32_t ccap, int simcap)
 {
+    ArenaPlan P;
+    const size_t es = precision == CUBA_FP64 ? sizeof(double) : sizeof(float);
+    const size_t pc = std::max<uint32_t>(pcap, 1);
+    P.state = 6 * pc * es;
+    P.keys = pc * 4;
+    P.perm = pc * 4;
+    P.cell_start = ((size_t)ccap + 1) * 4;
+    P.cell_work = ((size_t)ccap + 1) * sizeof(uint2);
+    P.skip_work = ((size_t)ccap + 1) * sizeof(uint32_t);
+    P.acc_count = (size_t)ccap * 4;
+    P.active = (size_t)ccap * 4;
+    P.radix_hist_cap = (uint32_t)(2 * kBinBins * ((pc + kSortTile - 1) / kSortTile + 1));
+    P.radix_hist = (size_t)P.radix_hist_cap * 4;
+    P.scan_tmp = scan_tmp_needed(pcap, ccap);
+    P.counters = 16 * 4;
+    // survivors of the random-byte filters: about one pair in 2^16, or
+    // 2.0001 C of them (larger batches spill to in-place evaluation)
+    P.surv_cap = std::max<uint32_t>(1u << 21, (uint32_t)(pc / 2));
+    P.surv = (size_t)P.surv_cap * sizeof(uint4);
+    P.used_bits = (pc / 32 + 2) * 4;
+    if (ccap > (uint32_t)kBinBins && (size_t)27 * ccap <= ((size_t)1 << 29)) {
+        P.nbr_cap = ccap;
+        P.nbr_rel = (size_t)27 * ccap * 4;
+        P.nbr_cs = ((size_t)ccap + 1) * 4;
+    }
+    P.stats = (size_t)simcap * kStatCount * 8;
+    P.sims = (size_t)simcap * sizeof(SimDesc);
+    return P;
+}
+
+int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simcap, const cuba_allocator* mem)
+{
+    if (mem && (!mem->alloc || !mem->free)) return fail(CUBA_ERR_INVALID, "allocator needs both alloc and free");
+    A.mem_alloc = mem ? mem->alloc : nullptr;
+    A.mem_free = mem ? mem->free : nullptr;
+    A.mem_ctx = mem ? mem->ctx : nullptr;
     A.precision = precision;
     A.pcap = pcap;
     A.ccap = ccap;
     A.simcap = simcap;
-    const size_t es = precision == CUBA_FP64 ? sizeof(double) : sizeof(float);
-    const size_t pc = std::max<uint32_t>(pcap, 1);
+    const ArenaPlan P = arena_plan(precision, pcap, ccap, simcap);
     int rc = CUBA_OK;
-    rc |= dalloc(&A.st[0], 6 * pc * es, "state");
-    if (!rc) rc = dalloc(&A.st[1], 6 * pc * es, "state");
-    if (!rc) rc = dalloc(&A.key[0], pc * 4, "keys");
-    if (!rc) rc = dalloc(&A.key[1], pc * 4, "keys");
-    if (!rc) rc = dalloc(&A.idx[0], pc * 4, "perm");
-    if (!rc) rc = dalloc(&A.idx[1], pc * 4, "perm");
-    if (!rc) rc = dalloc(&A.cell_start, ((size_t)ccap + 1) * 4, "cell_start");
-    if (!rc) rc = dalloc(&A.cell_work, ((size_t)ccap + 1) * sizeof(uint2), "cell_work");
-    if (!rc) rc = dalloc(&A.skip_work, ((size_t)ccap + 1) * sizeof(uint32_t), "skip_work");
-    if (!rc) rc = dalloc(&A.acc_count, (size_t)ccap * 4, "acc_count");
-    if (!rc) rc = dalloc(&A.active, (size_t)ccap * 4, "active");
-    A.radix_hist_cap = (uint32_t)(2 * kBinBins * ((pc + kSortTile - 1) / kSortTile + 1));
-    if (!rc) rc = dalloc(&A.radix_hist, (size_t)A.radix_hist_cap * 4, "radix_hist");
-    A.scan_tmp_bytes = scan_tmp_needed(pcap, ccap);
-    if (!rc) rc = dalloc(&A.scan_tmp, A.scan_tmp_bytes, "scan_tmp");
-    if (!rc) rc = dalloc(&A.counters, 16 * 4, "counters");
-    // survivors of the random-byte filters: about one pair in 2^16, or
-    // 2.0001 C of them (larger batches spill to in-place evaluation)
-    A.surv_cap = std::max<uint32_t>(1u << 21, (uint32_t)(pc / 2));
-    if (!rc) rc = dalloc(&A.surv, (size_t)A.surv_cap * sizeof(uint4), "survivors");
-    if (!rc) rc = dalloc(&A.used_bits, (pc / 32 + 2) * 4, "used_bits");
-    if (!rc && ccap > (uint32_t)kBinBins && (size_t)27 * ccap <= ((size_t)1 << 29)) {
-        A.nbr_cap = ccap;
-        rc = dalloc(&A.nbr_rel, (size_t)27 * ccap * 4, "neighbour offsets");
-        if (!rc) rc = dalloc(&A.nbr_cs, ((size_t)ccap + 1) * 4, "neighbour cell_start");
+    rc |= arena_dalloc(A, &A.st[0], P.state, "state");
+    if (!rc) rc = arena_dalloc(A, &A.st[1], P.state, "state");
+    if (!rc) rc = arena_dalloc(A, &A.key[0], P.keys, "keys");
+    if (!rc) rc = arena_dalloc(A, &A.key[1], P.keys, "keys");
+    if (!rc) rc = arena_dalloc(A, &A.idx[0], P.perm, "perm");
+    if (!rc) rc = arena_dalloc(A, &A.idx[1], P.perm, "perm");
+    if (!rc) rc = arena_dalloc(A, &A.cell_start, P.cell_start, "cell_start");
+    if (!rc) rc = arena_dalloc(A, &A.cell_work, P.cell_work, "cell_work");
+    if (!rc) rc = arena_dalloc(A, &A.skip_work, P.skip_work, "skip_work");
+    if (!rc) rc = arena_dalloc(A, &A.acc_count, P.acc_count, "acc_count");
+    if (!rc) rc = arena_dalloc(A, &A.active, P.active, "active");
+    A.radix_hist_cap = P.radix_hist_cap;
+    if (!rc) rc = arena_dalloc(A, &A.radix_hist, P.radix_hist, "radix_hist");
+    A.scan_tmp_bytes = P.scan_tmp;
+    if (!rc) rc = arena_dalloc(A, &A.scan_tmp, P.scan_tmp, "scan_tmp");
+    if (!rc) rc = arena_dalloc(A, &A.counters, P.counters, "counters");
+    A.surv_cap = P.surv_cap;
+    if (!rc) rc = arena_dalloc(A, &A.surv, P.surv, "survivors");
+    if (!rc) rc = arena_dalloc(A, &A.used_bits, P.used_bits, "used_bits");
+    if (!rc && P.nbr_cap) {
+        A.nbr_cap = P.nbr_cap;
+        rc = arena_dalloc(A, &A.nbr_rel, P.nbr_rel, "neighbour offsets");
+        if (!rc) rc = arena_dalloc(A, &A.nbr_cs, P.nbr_cs, "neighbour cell_start");
     }
-    if (!rc) rc = dalloc(&A.stats, (size_t)simcap * kStatCount * 8, "stats");
-    if (!rc) rc = dalloc(&A.d_sims, (size_t)simcap * sizeof(SimDesc), "sims");
+    if (!rc) rc = arena_dalloc(A, &A.stats, P.stats, "stats");
+    if (!rc) rc = arena_dalloc(A, &A.d_sims, P.sims, "sims");
     if (rc) {
         arena_free(A);
         return rc;
     }
+    const size_t pc = std::max<uint32_t>(pcap, 1);
     cudaMemset(A.counters, 0, 16 * 4);
     cudaMemset(A.used_bits, 0, (pc / 32 + 2) * 4);
     cudaMemset(A.stats, 0, (size_t)simcap * kStatCount * 8);
@@ -234,9 +308,9 @@ int sample_regions(Arena& A, int sim_index, const SimDesc& S, int64_t n, const c
     }
     double* d_reg = nullptr;
     uint64_t* d_first = nullptr;
-    if ((rc = dalloc(&d_reg, hreg.size() * sizeof(double), "regions"))) return rc;
-    if ((rc = dalloc(&d_first, first.size() * sizeof(uint64_t), "regions"))) {
-        cudaFree(d_reg);
+    if ((rc = arena_dalloc(A, &d_reg, hreg.size() * sizeof(double), "regions"))) return rc;
+    if ((rc = arena_dalloc(A, &d_first, first.size() * sizeof(uint64_t), "regions"))) {
+        arena_dfree(A, d_reg);
         return rc;
     }
     cudaMemcpy(d_reg, hreg.data(), hreg.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -245,8 +319,8 @@ int sample_regions(Arena& A, int sim_index, const SimDesc& S, int64_t n, const c
     if (launch_init_thermal(A, sim_index, S, d_reg, n_regions, d_first, st))
         rc = fail(CUBA_ERR_CUDA, "thermal sampling launch failed");
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(d_reg);
-    cudaFree(d_first);
+    arena_dfree(A, d_reg);
+    arena_dfree(A, d_first);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "thermal sampling");
     return rc;
 }
@@ -263,12 +337,12 @@ int settle_arena(Arena& A, cudaStream_t st, int* realloc)
     uint2 tot;
     CUDA_TRY(cudaMemcpyAsync(&tot, A.cell_work + A.ncells, sizeof(uint2), cudaMemcpyDeviceToHost, st), "read list size");
     CUDA_TRY(cudaStreamSynchronize(st), "sync");
-    const uint64_t want = 4ull * tot.y + (1ull << 20);
+    const uint64_t want = 4ull * tot.y + kMinAccEntries;
     if (want > A.acc_capacity) {
-        if (A.acc) cudaFree(A.acc);
+        if (A.acc) arena_dfree(A, A.acc);
         A.acc = nullptr;
         A.acc_capacity = 0;
-        int rc = dalloc(&A.acc, want * sizeof(unsigned long long), "accepted list");
+        int rc = arena_dalloc(A, &A.acc, want * sizeof(unsigned long long), "accepted list");
         if (rc) return rc;
         A.acc_capacity = want;
         if (realloc) *realloc = 1;
@@ -393,7 +467,7 @@ static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, d
     const size_t es = A.precision == CUBA_FP64 ? 8 : 4;
     const size_t col = (size_t)A.np * es;
     void* saved = nullptr;
-    int rc = dalloc(&saved, 6 * col, "autotune state");
+    int rc = arena_dalloc(A, &saved, 6 * col, "autotune state");
     if (rc) return rc;
     std::vector<SimDesc> table(A.nsims);
     std::vector<unsigned long long> stats((size_t)A.simcap * kStatCount);
@@ -472,7 +546,7 @@ static int tune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, d
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     restore();
-    cudaFree(saved);
+    arena_dfree(A, saved);
     if (chosen) *chosen = (int32_t)A.small_max;
     if (rc) return rc;
     return read_kernel_errors(A);
@@ -547,7 +621,7 @@ extern "C" {
 
 const char* cuba_last_error(void) { return g_last_error.c_str(); }
 
-int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out)
+static int create_sim(const cuba_params* params, int64_t max_particles, const cuba_allocator* mem, cuba_sim** out)
 {
     if (!out) return fail(CUBA_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -560,7 +634,7 @@ int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out
     cuba_sim* s = new cuba_sim();
     s->params = *params;
     s->desc = S;
-    rc = arena_alloc(s->A, params->precision, (uint32_t)max_particles, S.ncells, 1);
+    rc = arena_alloc(s->A, params->precision, (uint32_t)max_particles, S.ncells, 1, mem);
     if (rc) {
         delete s;
         return rc;
@@ -568,9 +642,11 @@ int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out
     s->A.nsims = 1;
     s->A.ncells = S.ncells;
     s->A.np = 0;
-    if (dalloc(&s->d_obs, (size_t)S.ncells * 20 + 64, "observables") || dalloc(&s->d_tot, 64, "totals")) {
+    rc = arena_dalloc(s->A, &s->d_obs, obs_scratch_bytes(S.ncells), "observables");
+    if (!rc) rc = arena_dalloc(s->A, &s->d_tot, kTotScratchBytes, "totals");
+    if (rc) {
         cuba_destroy(s);
-        return fail(CUBA_ERR_OOM, "scratch allocation failed");
+        return rc;
     }
     rc = upload_desc(s, 0);
     if (!rc) {
@@ -585,13 +661,32 @@ int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out
     return CUBA_OK;
 }
 
+int cuba_create(const cuba_params* params, int64_t max_particles, cuba_sim** out)
+{
+    return create_sim(params, max_particles, nullptr, out);
+}
+
+int cuba_create_with_allocator(const cuba_params* params, int64_t max_particles, const cuba_allocator* allocator,
+                               cuba_sim** out)
+{
+    if (!allocator || !allocator->alloc || !allocator->free)
+        return fail(CUBA_ERR_INVALID, "allocator needs both alloc and free");
+    return create_sim(params, max_particles, allocator, out);
+}
+
+int64_t cuba_sim_bytes(const cuba_params* params, int64_t max_particles)
+{
+    SimDesc S;
+    if (make_desc(params, &S)) return -1;
+    if (max_particles < 0 || max_particles > (int64_t)0x7FFFFFF0) return -1;
+    return (int64_t)object_bytes(params->precision, (uint32_t)max_particles, S.ncells, 1);
+}
+
 void cuba_destroy(cuba_sim* s)
 {
     if (!s) return;
     cudaDeviceSynchronize();
     s->graphs.drop();
-    if (s->d_obs) cudaFree(s->d_obs);
-    if (s->d_tot) cudaFree(s->d_tot);
     arena_free(s->A);
     delete s;
 }
@@ -862,7 +957,7 @@ int cuba_trace_enable(cuba_sim* s, int on)
     if (!s) return fail(CUBA_ERR_INVALID, "sim is NULL");
     CUDA_TRY(cudaDeviceSynchronize(), "sync");
     if (on && !s->A.trace_keys) {
-        int rc = dalloc(&s->A.trace_keys, (size_t)std::max<uint32_t>(s->A.pcap, 1) * 4, "trace");
+        int rc = arena_dalloc(s->A, &s->A.trace_keys, (size_t)std::max<uint32_t>(s->A.pcap, 1) * 4, "trace");
         if (rc) return rc;
     }
     s->A.trace = on ? 1 : 0;

@@ -145,14 +145,15 @@ extern "C" {
 int64_t cuba_batch_bytes(const cuba_batch_config* cfg)
 {
     if (!cfg) return -1;
-    const int64_t es = cfg->precision == CUBA_FP64 ? 8 : 4;
-    const int64_t p = cfg->max_particles, c = cfg->max_cells;
-    return 2 * 6 * p * es + 4 * 4 * p + p / 8 + 4 * (3 * c + 3) + 8 * (c + 1) + 20 * c +
-           4 * 2 * kBinBins * (p / kSortTile + 2) + (int64_t)bin_scan_bytes() +
-           (int64_t)cfg->max_sims * (kStatCount * 8 + (int64_t)sizeof(SimDesc));
+    if (cfg->precision != CUBA_FP32 && cfg->precision != CUBA_FP64) return -1;
+    if (cfg->max_sims < 1 || cfg->max_sims > 65536) return -1;
+    if (cfg->max_particles < 1 || cfg->max_particles > (int64_t)0x7FFFFFF0) return -1;
+    if (cfg->max_cells < 1 || cfg->max_cells > (int64_t)(1 << 30)) return -1;
+    return (int64_t)object_bytes(cfg->precision, (uint32_t)cfg->max_particles, (uint32_t)cfg->max_cells,
+                                 cfg->max_sims);
 }
 
-int cuba_batch_create(const cuba_batch_config* cfg, cuba_batch** out)
+static int create_batch(const cuba_batch_config* cfg, const cuba_allocator* mem, cuba_batch** out)
 {
     if (!cfg || !out) return fail(CUBA_ERR_INVALID, "bad arguments");
     *out = nullptr;
@@ -164,9 +165,10 @@ int cuba_batch_create(const cuba_batch_config* cfg, cuba_batch** out)
     if (kernels_init()) return fail(CUBA_ERR_CUDA, "kernel attribute setup failed");
     cuba_batch* b = new cuba_batch();
     b->cfg = *cfg;
-    int rc = arena_alloc(b->A, cfg->precision, (uint32_t)cfg->max_particles, (uint32_t)cfg->max_cells, cfg->max_sims);
-    if (!rc) rc = dalloc(&b->d_obs, (size_t)cfg->max_cells * 20 + 64, "observables");
-    if (!rc) rc = dalloc(&b->d_tot, 64, "totals");
+    int rc = arena_alloc(b->A, cfg->precision, (uint32_t)cfg->max_particles, (uint32_t)cfg->max_cells, cfg->max_sims,
+                         mem);
+    if (!rc) rc = arena_dalloc(b->A, &b->d_obs, obs_scratch_bytes((uint32_t)cfg->max_cells), "observables");
+    if (!rc) rc = arena_dalloc(b->A, &b->d_tot, kTotScratchBytes, "totals");
     if (rc) {
         cuba_batch_destroy(b);
         return rc;
@@ -179,13 +181,20 @@ int cuba_batch_create(const cuba_batch_config* cfg, cuba_batch** out)
     return CUBA_OK;
 }
 
+int cuba_batch_create(const cuba_batch_config* cfg, cuba_batch** out) { return create_batch(cfg, nullptr, out); }
+
+int cuba_batch_create_with_allocator(const cuba_batch_config* cfg, const cuba_allocator* allocator, cuba_batch** out)
+{
+    if (!allocator || !allocator->alloc || !allocator->free)
+        return fail(CUBA_ERR_INVALID, "allocator needs both alloc and free");
+    return create_batch(cfg, allocator, out);
+}
+
 void cuba_batch_destroy(cuba_batch* b)
 {
     if (!b) return;
     cudaDeviceSynchronize();
     b->graphs.drop();
-    if (b->d_obs) cudaFree(b->d_obs);
-    if (b->d_tot) cudaFree(b->d_tot);
     arena_free(b->A);
     delete b;
 }

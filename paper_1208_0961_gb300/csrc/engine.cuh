@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "philox.cuh"
 
@@ -107,9 +108,11 @@ constexpr uint32_t kErrAccOverflow = 1u;   // accepted list ran out of room
 constexpr uint32_t kErrCapacity = 2u;      // list capacity of a step exceeds the allocation
 constexpr uint32_t kErrMove = 4u;          // a particle moved more than one cell along an axis
 
-// Radix sort geometry: 256 threads x 16 keys per tile; 8-bit digits for the
-// sort of a settled state, 11-bit digits for the sort inside a step (one pass
-// up to 2048 cells, two up to 2^22).
+// Radix sort geometry: 256 threads x 16 keys per tile.  11-bit digits for the
+// sort inside a step and the settling sort of a new state (one pass up to 2048
+// cells, two up to 2^22); 8-bit digits only for the allocation-free binning of
+// caller buffers (cuba_bin_noalloc), whose fixed scratch holds 256-bin
+// histograms.
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kBinBits = 11;
@@ -223,6 +226,17 @@ struct Arena {
     PhiloxKey key_sched = {};
     // which acceptance modes the resident simulations use; any adaptive dt
     int any_all_pairs = 1, any_skip = 0, any_adapt = 0;
+    // device memory: every buffer of the arena (and of the object that owns
+    // it) comes from mem_alloc — cudaMalloc when none was given — and is
+    // recorded in mem_blocks so that it goes back through mem_free
+    void* (*mem_alloc)(size_t, void*) = nullptr;
+    void (*mem_free)(void*, size_t, void*) = nullptr;
+    void* mem_ctx = nullptr;
+    struct Block {
+        void* ptr;
+        size_t bytes;
+    };
+    std::vector<Block> mem_blocks;
 };
 
 // ---- launchers (kernels_sort.cu) ----
@@ -231,7 +245,6 @@ int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double*
 int launch_init_hotspot(const Arena& A, const SimDesc& S, double T0, double dT, double width, cudaStream_t st);
 int launch_settle_bin(Arena& A, cudaStream_t st);   // present positions -> keys, sorted state, cell_start
 int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st);
-int launch_cell_bounds(const uint32_t* skey, uint32_t np, uint32_t* cell_start, uint32_t ncells, cudaStream_t st);
 int scan_u32(uint32_t* data, size_t n, void* tmp, size_t tmp_bytes, cudaStream_t st);
 
 // ---- launchers (kernels_bin.cu) ----

@@ -28,20 +28,50 @@ int cuda_fail(cudaError_t e, const char* what);
 // Validate parameters (Sec. 2, Sec. 5) and fill the device descriptor.
 int make_desc(const cuba_params* p, SimDesc* S);
 
+// Device memory of an arena and of the object owning it: from the caller's
+// allocator when one was given, else cudaMalloc; every block is recorded and
+// returned by arena_dfree or arena_free.
+int arena_dalloc_raw(Arena& A, void** ptr, size_t bytes, const char* what);
 template <typename P>
-int dalloc(P** ptr, size_t bytes, const char* what)
+int arena_dalloc(Arena& A, P** ptr, size_t bytes, const char* what)
 {
-    *ptr = nullptr;
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc((void**)ptr, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CUBA_ERR_OOM, "cudaMalloc %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    void* p = nullptr;
+    int rc = arena_dalloc_raw(A, &p, bytes, what);
+    *ptr = static_cast<P*>(p);
+    return rc;
+}
+void arena_dfree(Arena& A, void* ptr);
+
+// Sizes in bytes of the buffers arena_alloc allocates (state and keys and
+// permutation counted once per ping-pong copy in total()).
+struct ArenaPlan {
+    size_t state = 0, keys = 0, perm = 0, cell_start = 0, cell_work = 0, skip_work = 0, acc_count = 0, active = 0;
+    size_t radix_hist = 0, scan_tmp = 0, counters = 0, surv = 0, used_bits = 0, nbr_rel = 0, nbr_cs = 0;
+    size_t stats = 0, sims = 0;
+    uint32_t radix_hist_cap = 0, surv_cap = 0, nbr_cap = 0;
+    size_t total() const
+    {
+        return 2 * state + 2 * keys + 2 * perm + cell_start + cell_work + skip_work + acc_count + active + radix_hist +
+               scan_tmp + counters + surv + used_bits + nbr_rel + nbr_cs + stats + sims;
     }
-    return CUBA_OK;
+};
+ArenaPlan arena_plan(int precision, uint32_t pcap, uint32_t ccap, int simcap);
+// Entries of the smallest accepted-pair list settle_arena allocates.
+constexpr uint64_t kMinAccEntries = 1ull << 20;
+// Observables scratch of a simulation or batch with ccap cells, and the
+// totals scratch.
+inline size_t obs_scratch_bytes(uint32_t ccap) { return (size_t)ccap * 20 + 64; }
+constexpr size_t kTotScratchBytes = 64;
+// Bytes an object with this arena allocates at creation plus the smallest
+// accepted-pair list.
+inline size_t object_bytes(int precision, uint32_t pcap, uint32_t ccap, int simcap)
+{
+    return arena_plan(precision, pcap, ccap, simcap).total() + obs_scratch_bytes(ccap) + kTotScratchBytes +
+           kMinAccEntries * sizeof(unsigned long long);
 }
 
-int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simcap);
+// mem: the caller's allocator, or NULL for cudaMalloc.
+int arena_alloc(Arena& A, int precision, uint32_t pcap, uint32_t ccap, int simcap, const cuba_allocator* mem);
 void arena_free(Arena& A);
 int enqueue_step(Arena& A, cudaStream_t st);
 int split_counts(int64_t n, const cuba_region* R, int nreg, std::vector<int64_t>& counts);

@@ -571,17 +571,20 @@ __global__ void __launch_bounds__(256) k_keys_raw(SimDesc S, const T* __restrict
     }
 }
 
-// cell_start[c] = first sorted position with key >= c (keys sorted).
+// cell_start[c] = first sorted position with key >= c (keys sorted), for
+// c = 0 .. ncells: one lower-bound search per cell, so empty cells cost one
+// search each wherever they lie (no serial fill of runs of empty cells).
 __global__ void __launch_bounds__(256) k_cell_bounds(const uint32_t* __restrict__ skey, uint32_t np,
                                                      uint32_t* __restrict__ cell_start, uint32_t ncells)
 {
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
-        const uint32_t kk = skey[k];
-        const int64_t prev = (k == 0) ? -1 : (int64_t)skey[k - 1];
-        for (int64_t c = prev + 1; c <= (int64_t)kk; ++c) cell_start[c] = k;
-        if (k == np - 1)
-            for (int64_t c = (int64_t)kk + 1; c <= (int64_t)ncells; ++c) cell_start[c] = np;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncells; c += stride) {
+        uint32_t lo = 0, hi = np;
+        while (lo < hi) {
+            const uint32_t mid = lo + ((hi - lo) >> 1);
+            if (skey[mid] < c) lo = mid + 1; else hi = mid;
+        }
+        cell_start[c] = lo;
     }
 }
 
@@ -638,13 +641,6 @@ int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st)
 {
     if (n == 0) return 0;
     k_fill_u32<<<grid_for(n, 256, 4), 256, 0, st>>>(p, n, v);
-    return last_err();
-}
-
-int launch_cell_bounds(const uint32_t* skey, uint32_t np, uint32_t* cell_start, uint32_t ncells, cudaStream_t st)
-{
-    if (np == 0) return launch_fill_u32(cell_start, ncells + 1, 0u, st);
-    k_cell_bounds<<<grid_for(np, 256, 8), 256, 0, st>>>(skey, np, cell_start, ncells);
     return last_err();
 }
 
@@ -739,7 +735,7 @@ int launch_bin_raw(const SimDesc& S, int precision, const void* xyz, uint32_t n,
         k_iota<<<grid_for(n, 256, 4), 256, 0, st>>>(perm, n);
     else if (cudaMemcpyAsync(perm, idx[src], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return -1;
-    k_cell_bounds<<<g, 256, 0, st>>>(keys[src], n, cell_start, S.ncells);
+    k_cell_bounds<<<grid_for((uint64_t)S.ncells + 1, 256, 8), 256, 0, st>>>(keys[src], n, cell_start, S.ncells);
     return last_err();
 }
 

@@ -63,6 +63,14 @@ class cuba_launch_shape(C.Structure):
     _fields_ = [("small_max", C.c_int32), ("small_blocks", C.c_int32), ("tile_blocks", C.c_int32)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class cuba_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
 class CubaError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("cuba error %d: %s" % (code, msg))
@@ -113,6 +121,11 @@ def load(build_if_missing=True):
         "cuba_step_profiled": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), vp]),
         "cuba_bin_noalloc": (C.c_int, [C.POINTER(cuba_params), vp, C.c_int64, vp, vp, vp]),
         "cuba_batch_create": (C.c_int, [C.POINTER(cuba_batch_config), C.POINTER(vp)]),
+        "cuba_create_with_allocator": (C.c_int, [C.POINTER(cuba_params), C.c_int64, C.POINTER(cuba_allocator),
+                                                 C.POINTER(vp)]),
+        "cuba_batch_create_with_allocator": (C.c_int, [C.POINTER(cuba_batch_config), C.POINTER(cuba_allocator),
+                                                       C.POINTER(vp)]),
+        "cuba_sim_bytes": (C.c_int64, [C.POINTER(cuba_params), C.c_int64]),
         "cuba_batch_destroy": (None, [vp]),
         "cuba_batch_add": (C.c_int, [vp, C.POINTER(cuba_params), C.c_int64, C.POINTER(cuba_region), C.c_int,
                                      C.POINTER(C.c_int32), vp]),
@@ -211,6 +224,58 @@ def cuba_create(params, max_particles):
     h = C.c_void_p()
     _check(load().cuba_create(C.byref(params), int(max_particles), C.byref(h)))
     return h
+
+
+def cuba_create_with_allocator(params, max_particles, allocator):
+    """allocator: a DeviceAllocator (its C struct must outlive the handle)."""
+    h = C.c_void_p()
+    _check(load().cuba_create_with_allocator(C.byref(params), int(max_particles), C.byref(allocator.c_struct),
+                                             C.byref(h)))
+    return h
+
+
+def cuba_sim_bytes(params, max_particles):
+    return int(load().cuba_sim_bytes(C.byref(params), int(max_particles)))
+
+
+class DeviceAllocator:
+    """A cuba_allocator whose callbacks are Python callables:
+    alloc(nbytes) -> device address (int, 256-byte aligned) or 0, and
+    free(address, nbytes).  Keeps the ctypes callbacks alive and counts the
+    bytes handed out (live_bytes, peak_bytes, calls)."""
+
+    def __init__(self, alloc, free):
+        self._alloc, self._free = alloc, free
+        self.live = {}
+        self.live_bytes = 0
+        self.peak_bytes = 0
+        self.calls = 0
+
+        def _a(nbytes, _ctx):
+            ptr = int(self._alloc(int(nbytes)) or 0)
+            if ptr:
+                self.live[ptr] = int(nbytes)
+                self.live_bytes += int(nbytes)
+                self.peak_bytes = max(self.peak_bytes, self.live_bytes)
+                self.calls += 1
+            return ptr
+
+        def _f(ptr, nbytes, _ctx):
+            self.live_bytes -= self.live.pop(int(ptr), 0)
+            self._free(int(ptr), int(nbytes))
+
+        self._cb_alloc = ALLOC_FN(_a)
+        self._cb_free = FREE_FN(_f)
+        self.c_struct = cuba_allocator(self._cb_alloc, self._cb_free, None)
+
+
+def torch_allocator(device=None):
+    """Device memory from PyTorch's caching allocator: freed blocks return to
+    torch's cache, so the library's HBM counts against what torch manages."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    return DeviceAllocator(lambda n: torch.cuda.caching_allocator_alloc(n, dev),
+                           lambda ptr, n: torch.cuda.caching_allocator_delete(ptr))
 
 
 def cuba_destroy(sim):
@@ -402,6 +467,12 @@ def cuba_batch_create(cfg):
     return h
 
 
+def cuba_batch_create_with_allocator(cfg, allocator):
+    h = C.c_void_p()
+    _check(load().cuba_batch_create_with_allocator(C.byref(cfg), C.byref(allocator.c_struct), C.byref(h)))
+    return h
+
+
 def cuba_batch_destroy(b):
     load().cuba_batch_destroy(b)
 
@@ -476,9 +547,10 @@ def cuba_batch_bytes(cfg):
 class Batch:
     """Owns one batch handle; members are addressed by the ids cuba returns."""
 
-    def __init__(self, cfg):
+    def __init__(self, cfg, allocator=None):
         self.cfg = cfg
-        self.h = cuba_batch_create(cfg)
+        self.allocator = allocator
+        self.h = cuba_batch_create(cfg) if allocator is None else cuba_batch_create_with_allocator(cfg, allocator)
         self.dtype = "float64" if cfg.precision == CUBA_FP64 else "float32"
         self.members = {}
 
@@ -562,9 +634,11 @@ def cuba_last_error():
 class Sim:
     """Owns one simulation handle; state exchange via numpy (host) arrays."""
 
-    def __init__(self, params, max_particles):
+    def __init__(self, params, max_particles, allocator=None):
         self.params = params
-        self.h = cuba_create(params, max_particles)
+        self.allocator = allocator
+        self.h = (cuba_create(params, max_particles) if allocator is None
+                  else cuba_create_with_allocator(params, max_particles, allocator))
         self.dtype = "float64" if params.precision == CUBA_FP64 else "float32"
 
     def close(self):

@@ -62,12 +62,32 @@ class Result:
         return self.finished - self.arrival
 
 
-def state_bytes(n, n_cells, precision_bytes=4):
-    """Device bytes a resident simulation occupies in a batch arena: two
-    state copies (6 components), keys and permutation ping-pong, per-cell
-    tables (start, work, counts, active)."""
-    return n * (2 * 6 * precision_bytes + 16 + 1) + n_cells * (4 + 8 + 4 + 4 + 20)
+def list_room(req):
+    """Accepted-pair list entries the library reserves for a request's cells
+    at admission (per cell mu + 8 sqrt(mu) + 16, mu = 2.0001 C n (n - 1) / 2,
+    C = sigma dt / (N_test V_cell)), with each region's cells at their mean
+    occupancy plus one standard deviation (Poisson)."""
+    nc = req.n_cells[0] * req.n_cells[1] * req.n_cells[2]
+    V = (req.L[0] / req.n_cells[0]) * (req.L[1] / req.n_cells[1]) * (req.L[2] / req.n_cells[2])
+    C = req.sigma_fm2 * req.dt / (req.n_test * V)
+    if C <= 0.0 or req.n == 0:
+        return 0
+    wsum = sum(T ** 3 * np.prod(np.subtract(hi, lo)) for lo, hi, T in req.regions)
+    room = 0.0
+    for lo, hi, T in req.regions:
+        vol = float(np.prod(np.subtract(hi, lo)))
+        cells_r = max(1.0, nc * vol / float(np.prod(req.L)))
+        n_r = req.n * (T ** 3 * vol) / wsum
+        occ = n_r / cells_r
+        occ += math.sqrt(occ)
+        mu = 2.0001 * C * occ * max(occ - 1.0, 0.0) / 2.0
+        room += cells_r * (mu + 8.0 * math.sqrt(mu) + 16.0)
+    return int(math.ceil(room))
 
+
+# the library allocates four times the residents' list room plus 2^20 entries
+LIST_FACTOR = 4
+LIST_MIN_ENTRIES = 1 << 20
 
 # ---------------------------------------------------------------------------
 # Synthetic request streams (stand-ins for a real request log)
@@ -121,32 +141,77 @@ def poisson_stream(n_requests=400, rate_hz=20.0, seed=7, n_min=1e4, n_max=8e6, s
 # ---------------------------------------------------------------------------
 
 class CudaBackend:
-    """The device: one cuba batch sized from an HBM budget."""
+    """The device: one cuba batch sized from an HBM budget.
 
-    def __init__(self, budget_bytes, precision=None, max_sims=256, cells_per_particle=0.01, stream=None):
+    The arena (everything the batch allocates at creation, cuba_batch_bytes)
+    takes the budget minus a reserve for the accepted-pair list, which the
+    library sizes from the residents' occupancy at each admission; a request
+    is admitted only while the list room of all residents fits that reserve.
+    """
+
+    def __init__(self, budget_bytes, precision=None, max_sims=256, cells_per_particle=0.01, stream=None,
+                 list_fraction=0.15, allocator=None, sizes=None):
         from . import cuba
         self.cuba = cuba
         precision = cuba.CUBA_FP32 if precision is None else precision
-        pb = 4 if precision == cuba.CUBA_FP32 else 8
-        per_particle = 2 * 6 * pb + 16 + 1
-        self.max_particles = int(min(0x7FFFFFF0, budget_bytes * 0.9 / (per_particle + 40 * cells_per_particle)))
-        self.max_cells = int(max(1 << 16, self.max_particles * cells_per_particle))
+        if sizes is None:
+            reserve = max(16 << 20, int(list_fraction * budget_bytes))
+            self.max_particles, self.max_cells = self.size_for(cuba, precision, max_sims, budget_bytes - reserve,
+                                                               cells_per_particle)
+            if self.max_particles < 1:
+                raise ValueError("budget of %d bytes is too small for a batch" % budget_bytes)
+            self.list_entries = (reserve // 8 - LIST_MIN_ENTRIES) // LIST_FACTOR
+        else:
+            self.max_particles, self.max_cells, self.list_entries = sizes
         cfg = cuba.make_batch_config(precision, max_sims=max_sims, max_particles=self.max_particles,
                                      max_cells=self.max_cells)
-        self.batch = cuba.Batch(cfg)
+        self.arena_bytes = cuba.cuba_batch_bytes(cfg)
+        self.room_used = 0
+        self._room = {}
+        self.batch = cuba.Batch(cfg, allocator=allocator)
         self.precision = precision
         self.stream = stream
         self.max_sims = max_sims
 
+    @classmethod
+    def for_request(cls, req, precision=None, stream=None, allocator=None):
+        """A backend holding exactly one request (the plain one-at-a-time
+        loop): its particles, its cells and its list room."""
+        nc = req.n_cells[0] * req.n_cells[1] * req.n_cells[2]
+        return cls(0, precision=precision, max_sims=1, stream=stream, allocator=allocator,
+                   sizes=(max(1, req.n), nc, list_room(req)))
+
+    @staticmethod
+    def size_for(cuba, precision, max_sims, arena_budget, cells_per_particle):
+        """Largest (max_particles, max_cells) whose batch fits arena_budget."""
+        def cells(p):
+            return int(min(1 << 30, max(1 << 16, p * cells_per_particle)))
+
+        def nbytes(p):
+            cfg = cuba.make_batch_config(precision, max_sims=max_sims, max_particles=p, max_cells=cells(p))
+            return cuba.cuba_batch_bytes(cfg)
+        lo, hi = 0, 0x7FFFFFF0
+        while lo < hi:
+            mid = (lo + hi + 1) // 2
+            if nbytes(mid) <= arena_budget:
+                lo = mid
+            else:
+                hi = mid - 1
+        return lo, cells(lo) if lo else 0
+
     def fits(self, req, used_particles, used_cells, used_sims):
         nc = req.n_cells[0] * req.n_cells[1] * req.n_cells[2]
+        room_used = self.room_used if used_sims else 0
         return (used_particles + req.n <= self.max_particles and used_cells + nc <= self.max_cells
-                and used_sims < self.max_sims)
+                and used_sims < self.max_sims and room_used + list_room(req) <= self.list_entries)
 
     def admit(self, req):
         p = self.cuba.make_params(L=req.L, n_cells=req.n_cells, dt=req.dt, sigma_fm2=req.sigma_fm2,
                                   n_test=req.n_test, precision=self.precision, seed=req.seed)
-        return self.batch.add(p, req.n, req.regions, self.stream)
+        h = self.batch.add(p, req.n, req.regions, self.stream)
+        self._room[h] = list_room(req)
+        self.room_used += self._room[h]
+        return h
 
     def step(self, k):
         self.batch.step(k, self.stream)
@@ -165,6 +230,7 @@ class CudaBackend:
     def finish(self, handle):
         obs = self.batch.observables(handle, self.stream)
         self.batch.remove(handle)
+        self.room_used -= self._room.pop(handle, 0)
         return obs
 
     def close(self):

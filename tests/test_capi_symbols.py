@@ -29,7 +29,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_sizes_match_header_layout(tmp_path):
     # the C compiler's layout of the header's structs against the binding's
     structs = {"cuba_params": cuba.cuba_params, "cuba_region": cuba.cuba_region,
-               "cuba_counters": cuba.cuba_counters, "cuba_batch_config": cuba.cuba_batch_config}
+               "cuba_counters": cuba.cuba_counters, "cuba_batch_config": cuba.cuba_batch_config,
+               "cuba_allocator": cuba.cuba_allocator}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cuba.h"', 'int main(void) {']
     for name, ct in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))

@@ -67,9 +67,13 @@ def test_massive_screened_energy_conservation():
         try:
             sim.init_riemann(20000, 0.4, 0.32)
             E0 = sim.totals()[0][0]
-            sim.step(50)
-            E1 = sim.totals()[0][0]
-            assert abs(E1 - E0) / E0 < (1e-6 * 50 if fp32 else 1e-12)
+            Eprev = E0
+            for k in range(50):
+                sim.step(1)
+                E1 = sim.totals()[0][0]
+                assert abs(E1 - Eprev) / E0 < (1e-6 if fp32 else 1e-13), "step %d" % k
+                assert abs(E1 - E0) / E0 < (1e-6 * (k + 1) if fp32 else 1e-12)
+                Eprev = E1
             assert sim.stats()["executed"] > 0
         finally:
             sim.close()

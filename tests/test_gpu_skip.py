@@ -83,11 +83,14 @@ def test_skip_multi_step_energy():
         try:
             sim.init_riemann(20000, 0.4, 0.32)
             E0 = sim.totals()[0][0]
-            for _ in range(5):
-                sim.step(10)
+            Eprev = E0
+            for k in range(50):
+                sim.step(1)
                 E1, n = sim.totals()
                 assert n == 20000
-                assert abs(E1[0] - E0) / E0 < (1e-6 * 50 if fp32 else 1e-12)
+                assert abs(E1[0] - Eprev) / E0 < (1e-6 if fp32 else 1e-13), "step %d" % k
+                assert abs(E1[0] - E0) / E0 < (1e-6 * (k + 1) if fp32 else 1e-12)
+                Eprev = E1[0]
             st = sim.stats()
             assert st["steps"] == 50 and st["overflow"] == 0
             # candidates of 50 steps: P_max n(n - 1) / 2 summed over cells
