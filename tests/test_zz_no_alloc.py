@@ -37,7 +37,8 @@ def _run_cases(cases):
         regs = [((0.0, 0.0, 0.0), L, 0.4)]
         dtype = np.float64 if prec == cuba.CUBA_FP64 else np.float32
         st = W.thermal_state(n, regs, seed=100 + call).astype(dtype) if n else np.zeros((6, 0), dtype)
-        p = cuba.make_params(L=L, n_cells=cells, dt=0.01, sigma_fm2=0.0, n_test=1.0, precision=prec, seed=call)
+        dt = 0.5 * min(L[a] / cells[a] for a in range(3))
+        p = cuba.make_params(L=L, n_cells=cells, dt=dt, sigma_fm2=0.0, n_test=1.0, precision=prec, seed=call)
         ref_perm, ref_cs = _reference(p, st)
         ncells = cells[0] * cells[1] * cells[2]
         xyz = torch.from_numpy(np.ascontiguousarray(st[:3])).cuda()
