@@ -136,6 +136,29 @@ __device__ __forceinline__ uint32_t block_byte(uint4 r, uint32_t bit)
     return (w >> (8u * (bit & 3u))) & 0xFFu;
 }
 
+// Could some pair of a block survive both random-byte filters?  The 16
+// prefixes r16 = (top byte << 8) | middle byte of the block r and its
+// middle-byte block mb, as 16-bit fields (byte_perm), are tested against
+// thr16 all at once: a field below t = thr16 + 1 <= 0x8000 drops bit 15 in
+// (f | 0x8000) - t without a borrow into the next field.  r16 <= thr16
+// implies top byte <= thr8, so a false answer is exact; thr16 >= 0x7FFF
+// (2.0001 C >= 1/2) always answers true.
+__device__ __forceinline__ bool prefix16_any(uint4 r, uint4 mb, uint32_t thr16)
+{
+    if (thr16 >= 0x7FFFu) return true;
+    const uint32_t t16 = 0x00010001u * (thr16 + 1u);
+    const uint32_t rw[4] = {r.x, r.y, r.z, r.w}, mw[4] = {mb.x, mb.y, mb.z, mb.w};
+    uint32_t any = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t lo = __byte_perm(mw[w], rw[w], 0x5140);   // fields (r0 m0), (r1 m1)
+        const uint32_t hi = __byte_perm(mw[w], rw[w], 0x7362);   // fields (r2 m2), (r3 m3)
+        any |= ~((lo | 0x80008000u) - t16) & ~lo;
+        any |= ~((hi | 0x80008000u) - t16) & ~hi;
+    }
+    return (any & 0x80008000u) != 0;
+}
+
 struct CellCtx {
     uint32_t c;       // global cell
     uint32_t lc;      // cell index inside its simulation
@@ -336,63 +359,130 @@ __device__ __forceinline__ void drain_survivors(uint4* sv, uint32_t* svn, uint32
                                     active, stats, Kp);
 }
 
-// Resolve queued blocks [e0, e1) of the warp, one block per lane.  The bytes
-// <= thr8 at real pairs j (i < j < n) are first refined by the pair's middle
-// byte, drawn from the block (step, cell, i, TAG_MID | g) shared by the 16
-// pairs of the group: a 16-bit prefix above thr16 also proves u_ij >= P22.
-// Only the rare survivors draw their low 16 bits (block (step, cell, i,
-// TAG_FINE | j)), load momenta and evaluate P22; accepted pairs are appended
-// to the cell's list.
+// Resolve one queued block r of row i, group g: the bytes <= thr8 at real
+// pairs j (i < j < n) are refined by the pair's middle byte, drawn from the
+// block (step, cell, i, TAG_MID | g) shared by the 16 pairs of the group: a
+// 16-bit prefix above thr16 also proves u_ij >= P22.  Only the rare
+// survivors draw their low 16 bits (block (step, cell, i, TAG_FINE | j)),
+// load momenta and evaluate P22 (in the warp's survivor buffer, or here when
+// it is full); accepted pairs are appended to the cell's list.
 template <typename T, bool kMark>
-__device__ __forceinline__ void resolve_blocks(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
-                                               uint32_t thr16, T C, T m2, const T* __restrict__ st, uint32_t pcap,
-                                               const QEntry* q, uint32_t e0,
-                                               uint32_t e1, uint4* sv, uint32_t* svn,
-                                               uint32_t* __restrict__ acc_count,
-                                               unsigned long long* __restrict__ acc, uint64_t acc_cap,
-                                               uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
-                                               unsigned long long* __restrict__ stats)
+__device__ __forceinline__ void resolve_block(const CellCtx& cc, const PhiloxKey& K, uint32_t step, uint32_t thr8,
+                                              uint32_t thr16, T C, T m2, const T* __restrict__ st, uint32_t pcap,
+                                              uint4 r, uint32_t i, uint32_t g, uint4* sv, uint32_t* svn,
+                                              uint32_t* __restrict__ acc_count,
+                                              unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                              uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                              unsigned long long* __restrict__ stats)
+{
+    const uint4 mb = philox4x32_10(make_uint4(step, cc.lc, i, kTagMid | g), K);
+    // the exact per-byte walk runs only for blocks with a flagged prefix (at
+    // thr8 = thr16 = 0 about one pushed block in 250)
+    if (!prefix16_any(r, mb, thr16)) return;
+    uint32_t m = block_le_mask(r, thr8) & valid_cols(g, i, cc.n);
+    while (m) {
+        const uint32_t bit = (uint32_t)__ffs(m) - 1u;
+        m &= m - 1u;
+        const uint32_t r16 = (block_byte(r, bit) << 8) | block_byte(mb, bit);
+        if (r16 > thr16) continue;
+        const uint32_t j = 16u * g + bit;
+        const uint32_t pos = atomicAdd(svn, 1u);
+        if (pos < kSurvBuf)
+            sv[pos] = make_uint4(cc.c, i, j, r16 | (kMark ? 0x80000000u : 0u));
+        else
+            eval_survivor<T, kMark>(cc, K, step, C, m2, st, pcap, i, j, r16, acc_count, acc, acc_cap, counters,
+                                    active, stats);
+    }
+}
+
+// Per-lane rings of the 32-row item kernel: lane L keeps the Philox blocks
+// of its row that hold a byte <= thr8 (about one block in 16 at thr8 = 0) in
+// its column of the ring, entry k at r[k][0][L] (the block) and r[k][1][L].x
+// (its first-round word Z1 = A ^ group), so that a push is two predicated
+// shared stores and one address increment per block, with no warp-wide vote.
+// The warp drains the rings when a lane could not take NB more entries, and
+// at the end of its rows.
+constexpr int kRingDepth = 12;
+struct __align__(16) PairRing {
+    uint4 r[kRingDepth][2][32];   // [k][0][L]: the block, [k][1][L].x: its Z1
+};
+constexpr uint32_t kRingRowBytes = 2u * 32u * sizeof(uint4);  // r[k + 1][0][L] - r[k][0][L]
+constexpr uint32_t kRingZOff = 32u * sizeof(uint4);          // r[k][1][L] - r[k][0][L]
+
+// Push block r (first-round word z) onto this lane's ring iff its test word x
+// has a bit of 0x80808080 set; ra: shared address of the lane's next entry.
+__device__ __forceinline__ void ring_push(uint32_t x, uint32_t& ra, uint4 r, uint32_t z)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+        "and.b32 t, %1, 0x80808080;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "@p st.shared.v4.u32 [%0], {%2, %3, %4, %5};\n\t"
+        "@p st.shared.u32 [%0+%7], %6;\n\t"
+        "@p add.u32 %0, %0, %8;\n\t}"
+        : "+r"(ra)
+        : "r"(x), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(z), "n"(kRingZOff), "n"(kRingRowBytes)
+        : "memory");
+}
+
+// Warp-collective: resolve the cnt entries of every lane's ring (rows
+// 32 rb + L), one entry per lane in compacted order: entry e of the warp
+// belongs to the lane L with pre[L] <= e < pre[L + 1] (pre: exclusive prefix
+// of the counts), found by a binary search over the lanes' prefixes.
+template <typename T, bool kMark>
+__device__ __forceinline__ void drain_ring(const CellCtx& cc, uint32_t rb, const PhiloxKey& K, uint32_t step,
+                                           uint32_t thr8, uint32_t thr16, T C, T m2, const T* __restrict__ st,
+                                           uint32_t pcap, const PairRing& ring, uint32_t A, uint32_t cnt, uint4* sv,
+                                           uint32_t* svn, uint32_t* __restrict__ acc_count,
+                                           unsigned long long* __restrict__ acc, uint64_t acc_cap,
+                                           uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
+                                           unsigned long long* __restrict__ stats)
 {
     const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t e = e0 + lane; e < e1; e += 32) {
-        const uint4 r = q[e].r;
-        const uint32_t i = q[e].i, g = q[e].g;
-        uint32_t m = block_le_mask(r, thr8) & valid_cols(g, i, cc.n);
-        if (!m) continue;
-        const uint4 mb = philox4x32_10(make_uint4(step, cc.lc, i, kTagMid | g), K);
-        while (m) {
-            const uint32_t bit = (uint32_t)__ffs(m) - 1u;
-            m &= m - 1u;
-            const uint32_t r16 = (block_byte(r, bit) << 8) | block_byte(mb, bit);
-            if (r16 > thr16) continue;
-            const uint32_t j = 16u * g + bit;
-            const uint32_t pos = atomicAdd(svn, 1u);
-            if (pos < kSurvBuf)
-                sv[pos] = make_uint4(cc.c, i, j, r16 | (kMark ? 0x80000000u : 0u));
-            else
-                eval_survivor<T, kMark>(cc, K, step, C, m2, st, pcap, i, j, r16, acc_count, acc, acc_cap, counters,
-                                        active, stats);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += v;
+    }
+    const uint32_t pre = inc - cnt;
+    const uint32_t total = __shfl_sync(kFull, inc, 31);
+    __syncwarp();
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t e = base + lane;
+        uint32_t L = 0;
+#pragma unroll
+        for (uint32_t s = 16; s >= 1; s >>= 1) {
+            const uint32_t pc = __shfl_sync(kFull, pre, L + s);
+            if (pc <= e) L += s;
+        }
+        const uint32_t pL = __shfl_sync(kFull, pre, L);
+        if (e < total) {
+            const uint32_t k = e - pL;
+            resolve_block<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, ring.r[k][0][L], rb * kPairRows + L,
+                                    ring.r[k][1][L].x ^ A, sv, svn, acc_count, acc, acc_cap, counters, active, stats);
         }
     }
+    __syncwarp();
 }
 
 // All pairs (i, j), i < j, of the rows [32 rb, 32 rb + 32) of one cell: one
 // lane per row walks the row's 16-pair Philox blocks NB at a time (2, 4 or 8,
-// by the launch shape); blocks holding a byte <= thr8 are queued in the
-// warp's shared-memory queue and resolved 32 at a time.  kMark: the first accepted pair of the cell appends
-// it to the active-cell list (the small-cell path finds its cells by scanning).
+// by the launch shape); blocks holding a byte <= thr8 go to the lane's ring
+// and are resolved when the warp drains it.  kMark: the first accepted pair of
+// the cell appends it to the active-cell list (the small-cell path finds its
+// cells by scanning).
 template <typename T, bool kMark, int NB>
 __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32_t step, uint32_t thr8, uint32_t thr16,
                                           T C, T m2, const PhiloxKey& K, const T* __restrict__ st, uint32_t pcap,
-                                          QEntry* q, uint4* sv, uint32_t* svn,
+                                          PairRing& ring, uint4* sv, uint32_t* svn,
                                           uint32_t* __restrict__ acc_count,
                                           unsigned long long* __restrict__ acc, uint64_t acc_cap,
                                           uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
                                           unsigned long long* __restrict__ stats)
 {
-    constexpr int kQueueCap = queue_cap(NB);  // a warp pushes up to 32 NB blocks onto at most 32 queued ones
+    static_assert(NB <= kRingDepth, "a lane pushes up to NB blocks per iteration");
     const uint32_t lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const uint32_t i = rb * kPairRows + lane;
     const bool row_ok = i + 1 < cc.n;
     PhiloxRow R;
@@ -404,37 +494,35 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
     // "any" answer is exact).  Rows without partners test against m = 0,
     // which flags nothing; thr8 >= 128 flags every block of a row with
     // partners.  Blocks of pairs outside i < j < n (before the row's diagonal
-    // or past the cell's end) may be queued: the resolve drops their columns.
+    // or past the cell's end) may be pushed: the resolve drops their columns.
     const uint32_t t8 = row_ok ? 0x01010101u * (thr8 + 1u) : 0u;
     const uint32_t x0 = (row_ok && thr8 >= 128u) ? 0x80000000u : 0u;
-    // qa: shared address of the next free queue entry; past qa_drain a
-    // warp could not push 32 NB more blocks, so it drains 32 first
-    const uint32_t q_s = (uint32_t)__cvta_generic_to_shared(q);
-    const uint32_t qa_drain = q_s + 32u * (uint32_t)(kQueueCap - 32 * NB);
-    uint32_t qa = q_s;  // warp-uniform
-    for (uint32_t g = gfirst; g <= glast; g += NB) {
-        while (qa > qa_drain) {
-            const uint32_t qn = (qa - q_s) >> 5;
-            __syncwarp();
-            resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, q, qn - 32, qn, sv, svn, acc_count,
-                                     acc, acc_cap, counters, active, stats);
-            __syncwarp();
-            qa -= 32u * 32u;
+    const uint32_t ra0 = (uint32_t)__cvta_generic_to_shared(&ring.r[0][0][lane]);
+    // past ra_full a lane could not take NB more entries
+    const uint32_t ra_full = ra0 + kRingRowBytes * (uint32_t)(kRingDepth - NB);
+    uint32_t ra = ra0;
+    // groups are walked from a multiple of NB, so that group g + b = g | b and
+    // the first-round word of its block is (A ^ g) ^ b; blocks before the
+    // row's first group are drawn and dropped by the resolve
+    for (uint32_t g = gfirst & ~(uint32_t)(NB - 1); g <= glast; g += NB) {
+        if (__any_sync(kFull, ra > ra_full)) {
+            drain_ring<T, kMark>(cc, rb, K, step, thr8, thr16, C, m2, st, pcap, ring, R.A, (ra - ra0) / kRingRowBytes,
+                                 sv, svn, acc_count, acc, acc_cap, counters, active, stats);
+            ra = ra0;
         }
+        const uint32_t Ag = R.A ^ g;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            const uint4 r = R.block(g + b, K);
+            const uint32_t z = Ag ^ (uint32_t)b;
+            const uint4 r = R.block_z(z, K);
             const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
                                ((r.w - t8) & ~r.w) | x0;
-            qa = queue_push<false>(x, lt, qa, r, i, g + b, cc.c);
+            ring_push(x, ra, r, z);
         }
     }
-    if (qa != q_s) {
-        __syncwarp();
-        resolve_blocks<T, kMark>(cc, K, step, thr8, thr16, C, m2, st, pcap, q, 0, (qa - q_s) >> 5, sv, svn, acc_count,
-                                 acc, acc_cap, counters, active, stats);
-        __syncwarp();
-    }
+    if (__any_sync(kFull, ra != ra0))
+        drain_ring<T, kMark>(cc, rb, K, step, thr8, thr16, C, m2, st, pcap, ring, R.A, (ra - ra0) / kRingRowBytes, sv,
+                             svn, acc_count, acc, acc_cap, counters, active, stats);
 }
 
 // The warp-per-cell path keeps its block queue across cells: queued blocks
@@ -458,14 +546,14 @@ __device__ __forceinline__ void resolve_entries(const QEntry* q, uint32_t e0, ui
         const uint32_t i = q[e].i, g = q[e].g, c = q[e].c;
         const int s = sim_of_cell(sims, nsims, c);
         const SimDesc& S = sims[s];
-        const uint32_t cbase = cell_start[c];
-        const uint32_t n = cell_start[c + 1] - cbase;
-        uint32_t m = block_le_mask(r, S.thr8) & valid_cols(g, i, n);
-        if (!m) continue;
         const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
         const PhiloxKey& K = kOneKey ? Kp : Kl;
         const uint32_t lc = c - S.cell_off;
         const uint4 mb = philox4x32_10(make_uint4(S.step, lc, i, kTagMid | g), K);
+        if (!prefix16_any(r, mb, S.thr16)) continue;
+        const uint32_t cbase = cell_start[c];
+        const uint32_t n = cell_start[c + 1] - cbase;
+        uint32_t m = block_le_mask(r, S.thr8) & valid_cols(g, i, n);
         while (m) {
             const uint32_t bit = (uint32_t)__ffs(m) - 1u;
             m &= m - 1u;
@@ -703,7 +791,8 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
                 uint4* __restrict__ surv, uint32_t surv_cap, const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    __shared__ QEntry q_e[kWarps][queue_cap(NB)];
+    extern __shared__ __align__(16) unsigned char pair_smem[];
+    PairRing* ring = reinterpret_cast<PairRing*>(pair_smem);
     __shared__ uint4 s_v[kWarps][kSurvBuf];
     __shared__ uint32_t s_vn[kWarps], s_left[kWarps];
     const int w = threadIdx.x >> 5;
@@ -753,7 +842,7 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
         const uint32_t rb = item - w0.x;
         const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
         const PhiloxKey& K = kOneKey ? Kp : Kl;
-        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, q_e[w],
+        pair_rows<T, true, NB>(cc, rb, S.step, S.thr8, S.thr16, sim_C<T>(S), sim_m2<T>(S), K, st, pcap, ring[w],
                                s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active, stats);
         __syncwarp();
         if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
@@ -1294,13 +1383,19 @@ int launch_kinematics_check(const SimDesc& S, const float* pin, int64_t npairs, 
 // ---------------------------------------------------------------------------
 static int last_err() { return cudaPeekAtLastError() == cudaSuccess ? 0 : -1; }
 
+// dynamic shared memory of the item kernel: one ring per warp
+constexpr size_t kPairRingSmem = (kPairThreads / 32) * sizeof(PairRing);
+
 template <typename T, bool kOneKey, int NB>
 static unsigned pair_grid()
 {
     static unsigned g = 0;
     if (!g) {
+        cudaFuncSetAttribute(k_pair_tile<T, kOneKey, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPairRingSmem);
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_tile<T, kOneKey, NB>, kPairThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_tile<T, kOneKey, NB>, kPairThreads,
+                                                      kPairRingSmem);
         if (per < 1) per = 1;
         g = (unsigned)(per * sm_count());
     }
@@ -1344,7 +1439,7 @@ static void launch_small(const Arena& A, cudaStream_t st)
 template <typename T, bool kOneKey, int NB>
 static void launch_tile(const Arena& A, cudaStream_t st)
 {
-    k_pair_tile<T, kOneKey, NB><<<pair_grid<T, kOneKey, NB>(), kPairThreads, 0, st>>>(
+    k_pair_tile<T, kOneKey, NB><<<pair_grid<T, kOneKey, NB>(), kPairThreads, kPairRingSmem, st>>>(
         A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.acc_count, A.acc,
         A.acc_capacity, A.counters, A.active, A.stats, A.surv, A.surv_cap, A.key_sched);
 }

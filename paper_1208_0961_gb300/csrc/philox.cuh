@@ -70,9 +70,12 @@ struct PhiloxRow {
         G = W2 ^ k.k1[2];
     }
 
-    __device__ __forceinline__ uint4 block(uint32_t d, const PhiloxKey& k) const
+    __device__ __forceinline__ uint4 block(uint32_t d, const PhiloxKey& k) const { return block_z(A ^ d, k); }
+
+    // the block whose first-round word Z1 = A ^ d is given (A depends on the
+    // first counter word only)
+    __device__ __forceinline__ uint4 block_z(uint32_t Z1, const PhiloxKey& k) const
     {
-        const uint32_t Z1 = A ^ d;
         const uint64_t q1 = (uint64_t)0xCD9E8D57u * Z1;       // round 1, word Z
         const uint32_t X2 = (uint32_t)(q1 >> 32) ^ B;
         const uint32_t Y2 = (uint32_t)q1;
