@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -68,7 +68,12 @@ def parse():
                     help="small_max,small_blocks,tile_blocks: set the collision launch shape (no autotuning)")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
-    return ap.parse_args()
+    ap.add_argument("--extras", type=int, default=1,
+                    help="on one GPU, add the other workloads to the line: config1 (20 k particles, FP64, "
+                         "100 steps), hotspot3d (64 M particles, 128^3 cells), batch (256-member ensemble) and "
+                         "serve (400 Poisson requests at 20/s, and a sustainable rate)")
+    ap.add_argument("--extra-steps", type=int, default=20, help="timed steps of the hotspot3d and batch extras")
+    return ap.parse_args(argv)
 
 
 def workload(args):
@@ -240,24 +245,21 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def pair_tile_traffic():
-    """DRAM bytes of one full-size pair-tile launch from the committed ncu
-    summary, if the kernel's sources are unchanged since the capture."""
+def pair_tile_traffic(cfg, pairs_per_step):
+    """DRAM bytes of one pair-tile launch from ncu_traffic.json (written by
+    ncu_traffic.py from a one-pass ncu capture of this workload), or None if
+    the kernel's sources or the workload differ from the capture's."""
     import hashlib
-    import re
-    prof = os.path.join(ROOT, "profiles", "k_pair_tile_riemann1d_fp32.md")
-    srcs = ["kernels_pairs.cu", "engine.cuh", "philox.cuh", "fp.cuh"]
     try:
-        text = open(prof).read()
+        with open(os.path.join(ROOT, "ncu_traffic.json")) as f:
+            rec = json.load(f)["k_pair_tile"]
         h = hashlib.sha256()
-        for f in srcs:
-            with open(os.path.join(ROOT, "paper_1208_0961_gb300", "csrc", f), "rb") as fh:
+        for name in ["kernels_pairs.cu", "engine.cuh", "philox.cuh", "fp.cuh"]:
+            with open(os.path.join(ROOT, "paper_1208_0961_gb300", "csrc", name), "rb") as fh:
                 h.update(fh.read())
-        m = re.search(r"source-sha256[^:]*:\s*([0-9a-f]{64})", text)
-        t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
-        if m and t and m.group(1) == h.hexdigest():
-            return int(t.group(1))
-    except OSError:
+        if rec["source_sha256"] == h.hexdigest() and rec["workload"] == cfg["name"]:
+            return rec["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
         pass
     return None
 
@@ -432,10 +434,12 @@ def shard_members(members, rank, world):
     return members[rank::world]
 
 
-def run_batch_mode(args):
+def batch_result(args, world, rank):
+    """The batched ensemble (256 independent 1D Riemann runs in one arena, one
+    captured graph per step) against the plain loop (each member alone through
+    the single-simulation API, same steps).  Returns the line on rank 0."""
     import torch
     from paper_1208_0961_gb300 import cuba
-    world, rank, local = dist_setup(args)
     cuba.load()
     prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
     members = shard_members(ensemble(args.batch_sims, args.seed), rank, world)
@@ -461,6 +465,9 @@ def run_batch_mode(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -468,12 +475,15 @@ def run_batch_mode(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
+    clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     ids = list(b.members)
     pair_tests = sum(b.stats(i)["pair_tests"] for i in ids) / (args.warmup + args.steps)
     b.close()
     # the plain loop: each member alone (single-simulation API), same steps
     alone_ms = 0.0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for m, p in zip(members, params):
         sim = cuba.Sim(p, m["n"])
         sim.init_thermal(m["n"], m["regions"], stream)
@@ -487,43 +497,52 @@ def run_batch_mode(args):
         torch.cuda.synchronize()
         alone_ms += a0.elapsed_time(a1)
         sim.close()
+    clk_alone = clocks.stop()
     alone_ms = max_over_ranks(alone_ms, world)
     # the updates of all ranks over the slowest rank's time
     tot = sum_over_ranks(N, world)
-    if rank == 0:
-        line = {"mode": "batch", "metric": "particle-updates/s (stream+bin+collide), batched ensemble",
-                "value": tot * args.steps / (ms / 1000.0), "unit": "particle-updates/s", "steps": args.steps,
-                "n_gpus": world, "scaling": "weak", "ms_per_step": ms / args.steps, "members": args.batch_sims,
-                "particles": int(tot), "cells": int(sum_over_ranks(C, world)) if world > 1 else C,
-                "pair_tests_per_step": pair_tests,
-                "alone": {"value": tot * args.steps / (alone_ms / 1000.0), "ms_per_step": alone_ms / args.steps},
-                "launch_shape": shape, "autotune_ms": tune_ms,
-                "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
-        line["speedup_vs_alone"] = line["value"] / line["alone"]["value"]
+    cells = sum_over_ranks(C, world)
+    if rank != 0:
+        return None
+    line = {"mode": "batch", "metric": "particle-updates/s (stream+bin+collide), batched ensemble",
+            "config": {"workload": "ensemble-%d-riemann-1d" % args.batch_sims, "members": args.batch_sims,
+                       "particles": int(tot), "cells": int(cells),
+                       "members_drawn": "N log-uniform 5e4-4e6, cells log-uniform 100-2000, sigma log-uniform "
+                                        "0.5-50 mb, T_L/T_R from 400/320, 500/300, 350/250 MeV, "
+                                        "dt = min(dx/2, 0.1 lambda), seed 1000 + k",
+                       "timed_steps": args.steps, "steps_per_member_in_config": 300},
+            "value": tot * args.steps / (ms / 1000.0), "unit": "particle-updates/s", "steps": args.steps,
+            "warmup": args.warmup, "n_gpus": world, "scaling": "weak", "ms_per_step": ms / args.steps,
+            "pair_tests_per_step": pair_tests, "clocks": clk,
+            "alone": {"value": tot * args.steps / (alone_ms / 1000.0), "ms_per_step": alone_ms / args.steps,
+                      "clocks": clk_alone, "what": "each member alone, single-simulation API, default shape"},
+            "launch_shape": shape, "autotune_ms": tune_ms,
+            "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
+    line["speedup_vs_alone"] = line["value"] / line["alone"]["value"]
+    return line
+
+
+def run_batch_mode(args):
+    world, rank, local = dist_setup(args)
+    line = batch_result(args, world, rank)
+    if line is not None:
         print(json.dumps(line), flush=True)
-    elif world > 1:
-        sum_over_ranks(C, world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 
 
-
-
-
-def run_serve_mode(args):
-    """One server on one GPU; under torchrun only rank 0 serves (the request
-    stream is one queue) and the other ranks exit at once."""
-    if int(os.environ.get("RANK", "0")) != 0:
-        return 0
+def serve_result(args, rate_hz, n_requests, alone=True):
+    """The served request stream (Poisson arrivals at rate_hz, n_requests,
+    seed 7) through cost-class batches under the HBM budget, and the plain
+    one-at-a-time loop on the same requests; clocks sampled during each."""
     import torch
     from paper_1208_0961_gb300 import cuba
     from paper_1208_0961_gb300 import serve as S
-    torch.cuda.set_device(0)
     cuba.load()
     prec = cuba.CUBA_FP32 if args.precision == "fp32" else cuba.CUBA_FP64
-    reqs = S.poisson_stream(n_requests=args.serve_requests, rate_hz=args.serve_rate, seed=7)
+    reqs = S.poisson_stream(n_requests=n_requests, rate_hz=rate_hz, seed=7)
     stream = torch.cuda.Stream()
     budget = int(args.serve_budget_gb * 1e9)
     if args.serve_classes == 1:
@@ -535,35 +554,52 @@ def run_serve_mode(args):
         fractions = (0.1, 0.3, 0.6)
         backends = [S.CudaBackend(budget * f, precision=prec, max_sims=256, stream=torch.cuda.Stream())
                     for f in fractions]
-        srv = S.Server(backends, quantum=256, classify=S.cost_class, round_s=0.02)
+        srv = S.Server(backends, classify=S.cost_class)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     out = srv.run(reqs)
+    clk = clocks.stop()
+    host = {"admit_s": [round(be.admit_s, 3) for be in backends], "retire_s": [round(be.finish_s, 3) for be in backends]}
     for be in backends:
         be.close()
     line = {"mode": "serve", "metric": "served p50/p99 latency and particle-updates/s",
-            "requests": len(reqs), "rate_hz": args.serve_rate, "budget_gb": args.serve_budget_gb,
+            "config": {"workload": "poisson-%d-requests-%gHz" % (n_requests, rate_hz), "requests": n_requests,
+                       "rate_hz": rate_hz, "seed": 7, "budget_gb": args.serve_budget_gb,
+                       "mix": "half 1D Riemann (about 1000 particles per cell), half 3D thermal boxes (0.1 fm "
+                              "cells, about 30 per cell); N log-uniform 1e4-8e6, 50-500 steps, sigma 0-100 mb"},
             "served": out["served"], "rejected": out["rejected"], "p50_s": out["p50_s"], "p99_s": out["p99_s"],
-            "updates_per_s": out["updates_per_s"], "offered_updates_per_s": out["offered_updates_per_s"],
-            "makespan_s": out["makespan_s"], "classes": args.serve_classes,
+            "mean_s": out["mean_s"], "updates_per_s": out["updates_per_s"],
+            "offered_updates_per_s": out["offered_updates_per_s"], "makespan_s": out["makespan_s"],
+            "classes": args.serve_classes, "host_seconds_per_class": host, "clocks": clk,
             "dtype": "f32" if prec == cuba.CUBA_FP32 else "f64", "data": "synthetic"}
-    if args.serve_alone:
-        alone = S.run_alone(lambda r: S.CudaBackend.for_request(r, precision=prec, stream=stream), reqs)
-        line["alone"] = {"p50_s": alone["p50_s"], "p99_s": alone["p99_s"], "updates_per_s": alone["updates_per_s"],
-                         "makespan_s": alone["makespan_s"]}
+    if alone:
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        a = S.run_alone(lambda r: S.CudaBackend.for_request(r, precision=prec, stream=stream), reqs)
+        line["alone"] = {"p50_s": a["p50_s"], "p99_s": a["p99_s"], "mean_s": a["mean_s"],
+                         "updates_per_s": a["updates_per_s"], "makespan_s": a["makespan_s"],
+                         "clocks": clocks.stop(), "what": "one request at a time, in arrival order, each in a "
+                                                          "batch of its own"}
+    return line
+
+
+def run_serve_mode(args):
+    """One server on one GPU; under torchrun only rank 0 serves (the request
+    stream is one queue) and the other ranks exit at once."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(0)
+    line = serve_result(args, args.serve_rate, args.serve_requests, alone=bool(args.serve_alone))
     print(json.dumps(line), flush=True)
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.mode == "batch":
-        return run_batch_mode(args)
-    if args.mode == "serve":
-        return run_serve_mode(args)
-    import numpy as np
+def run_step(args, world, rank):
+    """One simulation (the workload args name) advanced K graph-replayed steps;
+    returns the JSON line (rank 0) with its roofline, phase split, end-to-end
+    rate and CPU baseline."""
     import torch
-    world, rank, local = dist_setup(args)
     from paper_1208_0961_gb300 import cuba
     from paper_1208_0961_gb300 import workloads as W
     cuba.load()
@@ -620,32 +656,31 @@ def main():
     pair_ms = phase[3] / max(1, args.profile_steps)
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    # pair tile: bound by the integer multiply pipe.  Every pair test costs
-    # one 32x32->64 multiply (16 per 16-pair Philox block once the
-    # row-invariant part of rounds 1-3 is hoisted); the FMA-heavy pipe issues
-    # them at 32 lanes per clock per SM, so the ceiling is n_SM x 32 x f_SM
-    # pair tests/s.  The issue-slot view (43 algorithmic lane-ops per block:
-    # 16 multiplies, 18 xors, 9 for the byte test, against 128 lanes per clock
-    # per SM) and the FP32 view are reported beside it.
+    # pair tile (the dominant kernel): the survey's FP32 view is the headline
+    # roofline -- 9 flops per pair test (dot product, P22, uniform conversion,
+    # compare) against n_SM x 128 FP32 lanes x 2 x f_SM.  Beside it, the units
+    # that bind this integer kernel: the 32x32->64 multiply pipe (one multiply
+    # per pair test: 16 per 16-pair Philox block once the row-invariant part
+    # of rounds 1-3 is hoisted, issued at 32 lanes per clock per SM), and the
+    # issue slots (43 algorithmic lane-ops per block: 16 multiplies, 18 xors,
+    # 9 for the byte test, against 128 lanes per clock per SM).
     ops_per_pair = 43.0 / 16.0
     pair_s = pair_ms / 1000.0
+    rate = pairs_per_step / pair_s
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6
     peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12
-    achieved_tops = pairs_per_step * ops_per_pair / pair_s / 1e12
     pipe_peak = n_sm * 32 * sm_mhz * 1e6
-    roofline = {"bound": "alu", "achieved": pairs_per_step / pair_s / 1e12, "peak": pipe_peak / 1e12,
-                "unit": "T pair tests/s (one 32x32->64 integer multiply each)",
-                "frac": pairs_per_step / pair_s / pipe_peak, "traffic": pair_tile_traffic(),
-                "kernel": "k_pair_tile (+ k_pair_finish)",
-                "peak_basis": "%d SMs x 32 multiplies/clk x %.0f MHz (sampled median)" % (n_sm, sm_mhz),
-                "issue_lane_ops": {"ops_per_pair": ops_per_pair, "achieved_tops": achieved_tops,
-                                   "peak_tops": peak_tops, "frac": achieved_tops / peak_tops},
-                # the pair-test rate against the FP32 peak, at the 9 flops per
-                # pair an FP32 all-pairs tile would spend (dot product, P22,
-                # uniform conversion, compare)
-                "fp32_equivalent": {"flops_per_pair": 9,
-                                    "achieved_tflops": 9.0 * pairs_per_step / pair_s / 1e12,
-                                    "peak_tflops": n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12,
-                                    "frac": 9.0 * pairs_per_step / pair_s / (n_sm * 128 * 2 * sm_mhz * 1e6)}}
+    roofline = {"bound": "alu", "achieved": 9.0 * rate / 1e12, "peak": fp32_peak / 1e12,
+                "unit": "TFLOP/s FP32-equivalent (9 flops per pair test)", "frac": 9.0 * rate / fp32_peak,
+                "traffic": pair_tile_traffic(cfg, pairs_per_step), "kernel": "k_pair_tile (+ k_pair_finish)",
+                "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled median)" % (n_sm, sm_mhz),
+                "pair_tests_per_s": rate,
+                "multiply_pipe": {"achieved": rate / 1e12, "peak": pipe_peak / 1e12,
+                                  "unit": "T pair tests/s (one 32x32->64 integer multiply each)",
+                                  "frac": rate / pipe_peak,
+                                  "peak_basis": "%d SMs x 32 multiplies/clk x %.0f MHz" % (n_sm, sm_mhz)},
+                "issue_lane_ops": {"ops_per_pair": ops_per_pair, "achieved_tops": rate * ops_per_pair / 1e12,
+                                   "peak_tops": peak_tops, "frac": rate * ops_per_pair / 1e12 / peak_tops}}
     # stream/bin phases against HBM: 56 algorithmic bytes per update (FP32)
     bpu = 56.0 if prec == cuba.CUBA_FP32 else 104.0
     sb_ms = (phase[0] + phase[1]) / max(1, args.profile_steps)
@@ -694,6 +729,7 @@ def main():
             # the FP32-vs-FP64-oracle error of this result, on the same strip
             cpu["fp32_vs_fp64_oracle"] = fp32_vs_fp64_oracle(args, cfg)
 
+    line = None
     if rank == 0:
         line = {
             "metric": "particle-updates/s (stream+bin+collide)", "value": value, "unit": "particle-updates/s",
@@ -722,8 +758,91 @@ def main():
             "cpu_baseline": cpu,
             "peaks": pk_kind,
         }
-        print(json.dumps(line), flush=True)
     sim.close()
+    return line
+
+
+def extras(args):
+    """The other workloads of the benchmark, each timed on its own with its
+    own clock record: config1 (the paper-sized 1D Riemann run, FP64, with the
+    oracle timed on the whole run), hotspot3d, the batched ensemble and the
+    served request stream (config rate, then a sustainable rate)."""
+    import copy
+    out = {}
+    # config 1: 20 k particles, 100 cells, dt = 0.05, 100 steps, FP64
+    a = copy.copy(args)
+    a.workload, a.n, a.cells, a.dt, a.sigma_mb, a.precision = "riemann1d", 20000, 100, 0.05, 10.0, "fp64"
+    a.steps, a.warmup, a.e2e_steps, a.no_cpu_baseline, a.profile_steps = 100, 5, 0, True, 3
+    line = run_step(a, 1, 0)
+    out["config1"] = _sub(line, "20 k particles, 10x1x1 fm, 100 cells, dt 0.05 fm/c, sigma 10 mb, FP64, 100 steps")
+    out["config1"]["oracle_full_run"] = oracle_full_run(a)
+    # config 3: 64 M particles, 128^3 cells, hot spot, sigma 5 mb, dt 0.01
+    a = copy.copy(args)
+    a.workload, a.n, a.cells, a.dt, a.sigma_mb, a.precision = "hotspot3d", 64_000_000, 128, 0.01, 5.0, "fp32"
+    a.steps, a.e2e_steps, a.no_cpu_baseline = args.extra_steps, 0, True
+    line = run_step(a, 1, 0)
+    out["hotspot3d"] = _sub(line, "12.8^3 fm box, 128^3 cells, 64 M particles at T = 400 MeV plus a hot spot "
+                                  "(600 MeV peak, width 1 fm), sigma 5 mb, dt 0.01 fm/c, FP32; %d timed steps "
+                                  "of the config's 200" % a.steps)
+    # config 4: the batched ensemble
+    a = copy.copy(args)
+    a.steps, a.precision = args.extra_steps, "fp32"
+    out["batch"] = batch_result(a, 1, 0)
+    # config 5: the served stream at its rate, then at a rate the server sustains
+    a = copy.copy(args)
+    a.precision = "fp32"
+    s5 = serve_result(a, args.serve_rate, args.serve_requests)
+    out["serve"] = s5
+    cap = s5["updates_per_s"]
+    sustain = min(args.serve_rate, args.serve_rate * 0.85 * cap / max(s5["offered_updates_per_s"], 1.0))
+    if sustain < args.serve_rate:
+        s_low = serve_result(a, round(sustain, 2), 200)
+        s_low["config"]["why"] = ("the config's rate offers more than the server carries: 85 % of the carried "
+                                  "rate, 200 requests")
+        out["serve_sustainable"] = s_low
+    return out
+
+
+def _sub(line, desc):
+    keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "clocks",
+            "gpu_launches", "roofline", "hbm_phases", "phase_ms_per_step", "pair_tests_per_step",
+            "accepted_per_step", "executed_per_step")
+    sub = {k: line[k] for k in keep if k in line}
+    sub["config"] = dict(sub["config"], description=desc)
+    return sub
+
+
+def oracle_full_run(a):
+    """The oracle on the whole config-1 run (20 k particles, 100 steps, FP64)
+    on the host cores."""
+    from oracle import oracle as O
+    cfg = workload(a)
+    op = O.make_params(L=cfg["L"], n=cfg["n_cells"], dt=cfg["dt"], sigma_fm2=cfg["sigma_fm2"], n_test=cfg["n_test"],
+                       seed=a.seed)
+    st = O.init_thermal(op, a.n, cfg["regions"])
+    st, _, _, _ = O.sort(op, st)
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        st, _ = O.step(op, k, st, trace=False)
+    dt = time.perf_counter() - t0
+    return {"value": a.n * a.steps / dt, "unit": "particle-updates/s", "cores": O.threads(), "kind": "oracle",
+            "seconds": dt, "sample": "the whole run: %d particles, %d steps" % (a.n, a.steps)}
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.mode == "batch":
+        return run_batch_mode(args)
+    if args.mode == "serve":
+        return run_serve_mode(args)
+    world, rank, local = dist_setup(args)
+    line = run_step(args, world, rank)
+    if line is not None and world == 1 and args.extras:
+        line["extras"] = extras(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

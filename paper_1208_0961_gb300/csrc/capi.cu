@@ -183,7 +183,7 @@ ArenaPlan arena_plan(int precision, uint32_t pcap, uint32_t ccap, int simcap)
         P.nbr_cs = ((size_t)ccap + 1) * 4;
     }
     P.stats = (size_t)simcap * kStatCount * 8;
-    P.sims = (size_t)simcap * sizeof(SimDesc);
+    P.sims = ((size_t)simcap + 1) * sizeof(SimDesc);  // + one scratch descriptor (settle_member)
     return P;
 }
 
@@ -325,14 +325,70 @@ int sample_regions(Arena& A, int sim_index, const SimDesc& S, int64_t n, const c
     return rc;
 }
 
+// The settling sort of one member's particles only (the others are sorted
+// already and members own disjoint cell ranges, so the arena stays sorted):
+// a view of the arena restricted to the member, with a descriptor copy at
+// offset 0 in the scratch slot after the table, sorts into the other state
+// buffer; the member's range is copied back and its cell_start entries
+// shifted by its first particle.  desc: the member's descriptor.
+static int settle_member(Arena& A, int member, const SimDesc& desc, cudaStream_t st)
+{
+    SimDesc L = desc;
+    L.p_off = 0;
+    L.cell_off = 0;
+    SimDesc* scratch = A.d_sims + A.simcap;
+    CUDA_TRY(cudaMemcpyAsync(scratch, &L, sizeof(SimDesc), cudaMemcpyHostToDevice, st), "member descriptor");
+    const size_t es = A.precision == CUBA_FP64 ? 8 : 4;
+    Arena V;  // borrows A's buffers; owns nothing
+    V.precision = A.precision;
+    V.pcap = A.pcap;
+    V.ccap = A.ccap;
+    V.np = desc.np;
+    V.ncells = desc.ncells;
+    V.nsims = 1;
+    V.simcap = 1;
+    V.st[0] = (char*)A.st[A.cur] + (size_t)desc.p_off * es;
+    V.st[1] = (char*)A.st[A.cur ^ 1] + (size_t)desc.p_off * es;
+    V.cur = 0;
+    V.key[0] = A.key[0];
+    V.key[1] = A.key[1];
+    V.idx[0] = A.idx[0];
+    V.idx[1] = A.idx[1];
+    V.cell_start = A.cell_start + desc.cell_off;
+    V.radix_hist = A.radix_hist;
+    V.radix_hist_cap = A.radix_hist_cap;
+    V.scan_tmp = A.scan_tmp;
+    V.scan_tmp_bytes = A.scan_tmp_bytes;
+    V.stats = A.stats;
+    V.d_sims = scratch;
+    (void)member;
+    if (launch_settle_bin(V, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
+    if (V.cur == 1)
+        for (int c = 0; c < 6; ++c)
+            CUDA_TRY(cudaMemcpyAsync((char*)V.st[0] + (size_t)c * A.pcap * es, (char*)V.st[1] + (size_t)c * A.pcap * es,
+                                     (size_t)desc.np * es, cudaMemcpyDeviceToDevice, st),
+                     "member state back");
+    if (launch_add_u32(V.cell_start, desc.ncells + 1, desc.p_off, st))
+        return fail(CUBA_ERR_CUDA, "cell_start shift failed");
+    return CUBA_OK;
+}
+
 // Keys of the present positions, stable sort, and the size of the
 // accepted-pair lists for the present occupancy (room for four times the
 // present need plus 2^20 entries: occupancy changes as the system evolves).
-// Returns 1 in *realloc if the list buffer was replaced.
-int settle_arena(Arena& A, cudaStream_t st, int* realloc)
+// member >= 0: only that member's particles are sorted (desc: its
+// descriptor); member == kSettleNoSort: the state and cell_start are sorted
+// already.  Returns 1 in *realloc if the list buffer was replaced.
+int settle_arena(Arena& A, cudaStream_t st, int* realloc, int member, const SimDesc* desc)
 {
     if (realloc) *realloc = 0;
-    if (launch_settle_bin(A, st)) return fail(CUBA_ERR_CUDA, "sort launch failed");
+    if (member == kSettleNoSort) {
+    } else if (member >= 0) {
+        int rc = settle_member(A, member, *desc, st);
+        if (rc) return rc;
+    } else if (launch_settle_bin(A, st)) {
+        return fail(CUBA_ERR_CUDA, "sort launch failed");
+    }
     if (launch_cell_prep(A, st, 0)) return fail(CUBA_ERR_CUDA, "cell preparation failed");
     uint2 tot;
     CUDA_TRY(cudaMemcpyAsync(&tot, A.cell_work + A.ncells, sizeof(uint2), cudaMemcpyDeviceToHost, st), "read list size");

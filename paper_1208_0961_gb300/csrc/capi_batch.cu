@@ -130,9 +130,11 @@ void unadmit(cuba_batch* b)
     push_table(b);
 }
 
+// Sort the newly admitted (last) member's particles and size the lists.
 int settle(cuba_batch* b, cudaStream_t st)
 {
-    int rc = settle_arena(b->A, st, nullptr);
+    const int k = (int)b->members.size() - 1;
+    int rc = settle_arena(b->A, st, nullptr, k, &b->members[k].desc);
     if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(st), "sync");
     return CUBA_OK;
@@ -246,6 +248,8 @@ int cuba_batch_remove(cuba_batch* b, int32_t id)
     if (rc) return rc;
     Arena& A = b->A;
     const bool last = k == (int)b->members.size() - 1;
+    const SimDesc gone = b->members[k].desc;
+    const uint32_t ncells_old = A.ncells;
     if (!last) {
         // copy every survivor to its new offset in the other state buffer
         const size_t es = A.precision == CUBA_FP64 ? 8 : 4;
@@ -262,13 +266,28 @@ int cuba_batch_remove(cuba_batch* b, int32_t id)
             p_new += d.np;
         }
         A.cur ^= 1;
+        // the later members keep their order: their cell_start entries move
+        // down by the removed member's cells and drop its particle count
+        // (through the per-cell work table as scratch, which the list sizing
+        // below recomputes)
+        const uint32_t from = gone.cell_off + gone.ncells;
+        const size_t cnt = (size_t)ncells_old - from + 1;
+        uint32_t* tmp = reinterpret_cast<uint32_t*>(A.cell_work);
+        CUDA_TRY(cudaMemcpyAsync(tmp, A.cell_start + from, cnt * 4, cudaMemcpyDeviceToDevice, 0), "cell_start");
+        CUDA_TRY(cudaMemcpyAsync(A.cell_start + gone.cell_off, tmp, cnt * 4, cudaMemcpyDeviceToDevice, 0),
+                 "cell_start");
+        if (launch_add_u32(A.cell_start + gone.cell_off, (uint32_t)cnt, 0u - gone.np, 0))
+            return fail(CUBA_ERR_CUDA, "cell_start shift failed");
     }
     b->free_slots.push_back(b->members[k].desc.stat_slot);
     b->members.erase(b->members.begin() + k);
     rc = push_table(b);
     if (rc) return rc;
     if (A.np == 0) return CUBA_OK;
-    return settle(b, 0);
+    rc = settle_arena(A, 0, nullptr, kSettleNoSort, nullptr);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(0), "sync");
+    return CUBA_OK;
 }
 
 int cuba_batch_step(cuba_batch* b, int n_steps, void* stream)

@@ -245,6 +245,7 @@ int launch_init_thermal(const Arena& A, int sim, const SimDesc& S, const double*
 int launch_init_hotspot(const Arena& A, const SimDesc& S, double T0, double dT, double width, cudaStream_t st);
 int launch_settle_bin(Arena& A, cudaStream_t st);   // present positions -> keys, sorted state, cell_start
 int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st);
+int launch_add_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st);
 int scan_u32(uint32_t* data, size_t n, void* tmp, size_t tmp_bytes, cudaStream_t st);
 
 // ---- launchers (kernels_bin.cu) ----

@@ -77,7 +77,10 @@ int enqueue_step(Arena& A, cudaStream_t st);
 int split_counts(int64_t n, const cuba_region* R, int nreg, std::vector<int64_t>& counts);
 int sample_regions(Arena& A, int sim_index, const SimDesc& S, int64_t n, const cuba_region* regions, int n_regions,
                    const double* L, cudaStream_t st);
-int settle_arena(Arena& A, cudaStream_t st, int* realloc);
+// member >= 0: only that member's particles are sorted (desc: its
+// descriptor); kSettleNoSort: only the list sizing (state already sorted)
+constexpr int kSettleNoSort = -2;
+int settle_arena(Arena& A, cudaStream_t st, int* realloc, int member = -1, const SimDesc* desc = nullptr);
 int read_kernel_errors(Arena& A);
 int autotune_arena(Arena& A, int n_steps, cudaStream_t st, int32_t* chosen, double* ms);
 int set_small_max(Arena& A, int32_t v);

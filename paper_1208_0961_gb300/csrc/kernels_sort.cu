@@ -350,6 +350,11 @@ __global__ void k_fill_u32(uint32_t* p, uint32_t n, uint32_t v)
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
 
+__global__ void k_add_u32(uint32_t* p, uint32_t n, uint32_t v)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] += v;
+}
+
 __global__ void k_iota(uint32_t* p, uint32_t n)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
@@ -641,6 +646,13 @@ int launch_fill_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st)
 {
     if (n == 0) return 0;
     k_fill_u32<<<grid_for(n, 256, 4), 256, 0, st>>>(p, n, v);
+    return last_err();
+}
+
+int launch_add_u32(uint32_t* p, uint32_t n, uint32_t v, cudaStream_t st)
+{
+    if (n == 0) return 0;
+    k_add_u32<<<grid_for(n, 256, 4), 256, 0, st>>>(p, n, v);
     return last_err();
 }
 

@@ -168,6 +168,8 @@ class CudaBackend:
         self.arena_bytes = cuba.cuba_batch_bytes(cfg)
         self.room_used = 0
         self._room = {}
+        self.admit_s = 0.0    # host seconds in admissions (sampling and the settling sort)
+        self.finish_s = 0.0   # host seconds in retirements (observables and compaction)
         self.batch = cuba.Batch(cfg, allocator=allocator)
         self.precision = precision
         self.stream = stream
@@ -208,7 +210,9 @@ class CudaBackend:
     def admit(self, req):
         p = self.cuba.make_params(L=req.L, n_cells=req.n_cells, dt=req.dt, sigma_fm2=req.sigma_fm2,
                                   n_test=req.n_test, precision=self.precision, seed=req.seed)
+        t0 = time.perf_counter()
         h = self.batch.add(p, req.n, req.regions, self.stream)
+        self.admit_s += time.perf_counter() - t0
         self._room[h] = list_room(req)
         self.room_used += self._room[h]
         return h
@@ -228,8 +232,10 @@ class CudaBackend:
             torch.cuda.synchronize()
 
     def finish(self, handle):
+        t0 = time.perf_counter()
         obs = self.batch.observables(handle, self.stream)
         self.batch.remove(handle)
+        self.finish_s += time.perf_counter() - t0
         self.room_used -= self._room.pop(handle, 0)
         return obs
 
@@ -273,38 +279,70 @@ def cost_class(r, bounds=(1e-4, 1e-3)):
 # ---------------------------------------------------------------------------
 
 class Server:
-    """Continuous batching over one or more backends (cost classes).
+    """Continuous batching over cost classes that share the device in turn.
 
     Requests go to the class of their estimated step cost (promoted to a
     larger class if they do not fit an empty one; rejected if they fit none).
-    Each round: in every class, admit queued requests in arrival order while
-    the class's backend has room (a request that does not fit blocks the ones
-    behind it in its class, so large requests are not starved); then give
-    every class with residents a quantum of steps sized so that the class's
-    steps take about `round_s` of device time (at most the smallest remaining
-    step count of its residents), launch all classes (their streams overlap on
-    the device) and wait; retire residents that are done.  One class is plain
-    continuous batching with a common quantum.
+    Each round visits the classes in order, smallest first.  A class admits
+    queued requests while its backend has room and its resident limit allows
+    -- in arrival order, or (order "sjf") shortest remaining work first with
+    aging: a request's work is divided by 1 + waiting time / aging_s, so a
+    large request waiting long enough is served before newer small ones --
+    then advances all its residents by a quantum of steps worth about its
+    budget of device time -- the budget grows with the age of the class's
+    oldest resident, budget (1 + age / budget_aging_s), so that a class whose
+    requests have waited long catches up -- (at most the smallest remaining
+    step count, so a finished resident leaves at once), waits for it and
+    retires the finished residents.  Classes take turns instead of running concurrently because a
+    large simulation's pair kernel occupies every SM for its whole duration:
+    a small request's kernels queued beside it would wait for it at every
+    step.  With one large resident at a time the large requests run nearly
+    at full speed, and small ones never wait behind them.
     """
 
-    def __init__(self, backend, quantum=64, clock: Callable[[], float] = time.perf_counter,
-                 sleep: Callable[[float], None] = time.sleep, classify=None, round_s=0.01):
+    def __init__(self, backend, quantum=256, clock: Callable[[], float] = time.perf_counter,
+                 sleep: Callable[[float], None] = time.sleep, classify=None, round_s=0.01, budgets=None,
+                 max_resident=None, order=None, aging_s=2.0, budget_aging_s=0.2, budget_cap=4.0):
         self.backends = list(backend) if isinstance(backend, (list, tuple)) else [backend]
+        nb = len(self.backends)
         self.classify = classify or (lambda r: 0)
         self.quantum = quantum
-        self.round_s = round_s
         self.clock = clock
         self.sleep = sleep
-
-    def _quantum(self, backend, residents):
-        if len(self.backends) == 1:
-            return self.quantum
-        reqs = [v[0] for v in residents.values()]
-        if hasattr(backend, "step_time"):
-            cost = backend.step_time(reqs)
+        if nb == 1:
+            self.budgets = [round_s]
+            self.max_resident = [None]
+            self.order = ["fifo"]
         else:
-            cost = STEP_FIXED_S + sum(step_cost(r) for r in reqs)
-        return int(max(1, min(self.quantum, round(self.round_s / cost))))
+            # device seconds per round: the small class's steps are short and
+            # its requests finish in a few rounds; medium and large share
+            self.budgets = budgets or [round_s * f for f in ((0.2, 1.0, 1.0) if nb == 3 else [1.0] * nb)]
+            # the large class runs one simulation at a time and the medium
+            # class a few: their batches stay small, so a step's time and the
+            # cost of an admission (a sort of the class's arena) or a
+            # retirement (its compaction) stay small too
+            self.max_resident = max_resident or ([None] * (nb - 2) + [8, 1] if nb >= 2 else [None])
+            self.order = order or (["fifo"] * (nb - 2) + ["sjf", "sjf"] if nb >= 2 else ["fifo"])
+        self.aging_s = aging_s
+        self.budget_aging_s = budget_aging_s
+        self.budget_cap = budget_cap
+
+    def _steps(self, k, residents, now):
+        reqs = [v[0] for v in residents.values()]
+        be = self.backends[k]
+        cost = be.step_time(reqs) if hasattr(be, "step_time") else STEP_FIXED_S + sum(step_cost(r) for r in reqs)
+        budget = self.budgets[k]
+        if self.budget_aging_s:
+            age = max(now - v[2] for v in residents.values())   # time since admission
+            budget *= min(self.budget_cap, 1.0 + age / self.budget_aging_s)
+        q = int(max(1, min(self.quantum, round(budget / max(cost, 1e-9)))))
+        return min(q, min(v[1] for v in residents.values()))
+
+    def _next(self, k, queue, now):
+        if self.order[k] != "sjf":
+            return 0
+        key = [(work(r) / (1.0 + max(0.0, now - r.arrival) / self.aging_s), r.arrival) for r in queue]
+        return min(range(len(queue)), key=lambda i: key[i])
 
     def run(self, requests: List[Request], keep_observables=False):
         reqs = sorted(requests, key=lambda r: r.arrival)
@@ -328,45 +366,48 @@ class Server:
                     rejected.append(r)
                 else:
                     queues[k].append(r)
+            ran = False
             for k in range(nb):
                 be, q, res, u = self.backends[k], queues[k], resident[k], used[k]
-                while q:
-                    r = q[0]
+                lim = self.max_resident[k]
+                while q and (lim is None or len(res) < lim):
+                    i = self._next(k, q, now())
+                    r = q[i]
                     if not be.fits(r, u[0], u[1], len(res)):
                         break
                     h = be.admit(r)
                     res[h] = [r, r.steps, now()]
                     u[0] += r.n
                     u[1] += r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
-                    q.pop(0)
-            if not any(resident):
-                if nxt < len(reqs):
-                    wait = reqs[nxt].arrival - now()
-                    if wait > 0:
-                        self.sleep(wait)
-                continue
-            ks = [0] * nb
-            for k in range(nb):
-                if resident[k]:
-                    ks[k] = min(self._quantum(self.backends[k], resident[k]), min(v[1] for v in resident[k].values()))
-                    self.backends[k].step(ks[k])
-            for k in range(nb):
-                if ks[k] and hasattr(self.backends[k], "sync"):
-                    self.backends[k].sync()
-            for k in range(nb):
-                res = resident[k]
+                    q.pop(i)
+                if not res:
+                    continue
+                ks = self._steps(k, res, now())
+                be.step(ks)
+                if hasattr(be, "sync"):
+                    be.sync()
+                ran = True
                 for h in list(res):
                     v = res[h]
-                    v[1] -= ks[k]
+                    v[1] -= ks
                     if v[1] == 0:
                         r = v[0]
-                        obs = self.backends[k].finish(h)
+                        obs = be.finish(h)
                         results.append(Result(r.rid, r.arrival, v[2], now(), r.n, r.steps,
                                               obs if keep_observables else None))
-                        used[k][0] -= r.n
-                        used[k][1] -= r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
+                        u[0] -= r.n
+                        u[1] -= r.n_cells[0] * r.n_cells[1] * r.n_cells[2]
                         del res[h]
+            if not ran and not any(queues) and nxt < len(reqs):
+                wait = reqs[nxt].arrival - now()
+                if wait > 0:
+                    self.sleep(wait)
         return summarize(results, rejected, now(), reqs)
+
+
+def work(r):
+    """Estimated device seconds of a whole request run alone."""
+    return (STEP_FIXED_S + step_cost(r)) * r.steps
 
 
 def run_alone(backend_factory, requests: List[Request], clock=time.perf_counter, sleep=time.sleep,

@@ -153,3 +153,45 @@ def test_full_size_ensemble_sampled_members():
         assert np.all(d[~moved] == 0), k
         assert np.all(d[moved] <= 1e-5 * tol[moved]), k
         assert res.n_exe > 0, k
+
+
+def test_removal_keeps_later_members_exact_on_the_neighbour_sort():
+    """3D boxes of about 30 particles per cell (more than 2048 cells in the
+    arena: the step sorts by neighbour moves, which reads the previous
+    cell_start).  Removing a middle member shifts the later ones; their
+    observables read right after the removal, and the steps after it, must
+    equal the same simulations run alone."""
+    def box(k, seed):
+        L = (0.1 * k,) * 3
+        regs = [((0.0, 0.0, 0.0), L, 0.4)]
+        n = 30 * k ** 3
+        nt = W.n_test_for(n, regs)
+        p = cuba.make_params(L=L, n_cells=(k, k, k), dt=0.05, sigma_fm2=3.0, n_test=nt, precision=cuba.CUBA_FP32,
+                             seed=seed)
+        return p, W.thermal_state(n, regs, seed=seed).astype(np.float32)
+
+    pA, sA = box(14, 21)
+    pB, sB = box(12, 22)
+    pC, sC = box(13, 23)
+    refC1 = _alone(pC, sC, 2, cuba.CUBA_FP32)
+    refC2 = _alone(pC, sC, 5, cuba.CUBA_FP32)
+    refA = _alone(pA, sA, 5, cuba.CUBA_FP32)
+    b = cuba.Batch(cuba.make_batch_config(cuba.CUBA_FP32, max_sims=4, max_particles=300000, max_cells=9000))
+    try:
+        iA = b.add_state(pA, sA)
+        iB = b.add_state(pB, sB)
+        iC = b.add_state(pC, sC)
+        b.step(2)
+        b.remove(iB)                          # C moves down
+        oC1 = b.observables(iC)               # before any further step
+        b.step(3)
+        gC = b.get_state(iC)
+        gA = b.get_state(iA)
+        oC2 = b.observables(iC)
+    finally:
+        b.close()
+    for x, y in zip(oC1, refC1[1]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(gC, refC2[0]) and np.array_equal(gA, refA[0])
+    for x, y in zip(oC2, refC2[1]):
+        assert np.array_equal(x, y)
