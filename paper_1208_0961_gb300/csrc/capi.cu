@@ -56,6 +56,8 @@ int make_desc(const cuba_params* p, SimDesc* S)
         S->dx[a] = p->L[a] / (double)p->n_cells[a];
         S->Lf[a] = (float)p->L[a];
         S->dxf[a] = (float)S->dx[a];
+        S->rdx[a] = 1.0 / S->dx[a];
+        S->rdxf[a] = (float)(1.0 / (double)S->dxf[a]);
         if (!(p->dt < S->dx[a]))
             return fail(CUBA_ERR_INVALID, "dt = %g must be below the cell edge %g on axis %d", p->dt, S->dx[a], a);
     }

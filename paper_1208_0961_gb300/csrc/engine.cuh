@@ -21,6 +21,8 @@ struct SimDesc {
     double dx[3];     // cell edges L / n, fm
     float Lf[3];      // FP32 copies (rounded once)
     float dxf[3];
+    double rdx[3];    // RN(1 / dx) and RN(1 / dxf): the fast path of the cell coordinate
+    float rdxf[3];
     int32_t n[3];     // cells per axis
     uint32_t ncells;  // n0 n1 n2
     uint32_t cell_off;

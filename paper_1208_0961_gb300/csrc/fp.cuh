@@ -33,6 +33,10 @@ template <typename T> __device__ __forceinline__ T sim_dx(const SimDesc& S, int 
 template <> __device__ __forceinline__ double sim_dx<double>(const SimDesc& S, int a) { return S.dx[a]; }
 template <> __device__ __forceinline__ float sim_dx<float>(const SimDesc& S, int a) { return S.dxf[a]; }
 
+template <typename T> __device__ __forceinline__ T sim_rdx(const SimDesc& S, int a);
+template <> __device__ __forceinline__ double sim_rdx<double>(const SimDesc& S, int a) { return S.rdx[a]; }
+template <> __device__ __forceinline__ float sim_rdx<float>(const SimDesc& S, int a) { return S.rdxf[a]; }
+
 template <typename T> __device__ __forceinline__ T sim_C(const SimDesc& S);
 template <> __device__ __forceinline__ double sim_C<double>(const SimDesc& S) { return S.C; }
 template <> __device__ __forceinline__ float sim_C<float>(const SimDesc& S) { return S.Cf; }

@@ -352,7 +352,12 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
 
 // One pass: rank by the (only) digit, re-stream each particle from the old
 // state and write it into its sorted slot; perm (tracing only) receives the
-// origin of each slot.
+// origin of each slot.  The slots of all rounds come first (they need only
+// the keys), then the particles are loaded FinalGroup rounds at a time, so
+// that their loads are in flight together (two in FP32; in FP64 the
+// registers of a second particle would spill under the 64-register budget).
+template <typename T> struct FinalGroup { static constexpr int value = sizeof(T) == 8 ? 1 : 2; };
+
 template <typename T, bool kStream>
 __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
     k_bin_final(const SimDesc* __restrict__ sims, int nsims, const uint32_t* __restrict__ key_in,
@@ -373,15 +378,25 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t i = base + r * 32 + lane;
-        const bool ok = i < n;
-        const uint32_t p = rank_next(R, k[r], ok, 0);
-        if (ok) {
-            const int s = sim_of_particle(sims, nsims, i);
-            T x[3], m[3];
-            load_particle<T>(st_old, pcap, i, x, m);
-            if (kStream && !StreamInPlace<T>::value) stream_one<T>(sims[s], x, m);
-            store_particle<T>(st_new, pcap, p, x, m);
-            if (perm) perm[p] = i;
+        k[r] = rank_next(R, k[r], i < n, 0);   // the key's register now holds the slot
+    }
+    constexpr int kG = FinalGroup<T>::value;
+#pragma unroll
+    for (int r0 = 0; r0 < kSortItems; r0 += kG) {
+        T x[kG][3], m[kG][3];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            const uint32_t i = base + (r0 + g) * 32 + lane;
+            if (i < n) load_particle<T>(st_old, pcap, i, x[g], m[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            const uint32_t i = base + (r0 + g) * 32 + lane;
+            if (i < n) {
+                if (kStream && !StreamInPlace<T>::value) stream_one<T>(sims[sim_of_particle(sims, nsims, i)], x[g], m[g]);
+                store_particle<T>(st_new, pcap, k[r0 + g], x[g], m[g]);
+                if (perm) perm[k[r0 + g]] = i;
+            }
         }
     }
 }

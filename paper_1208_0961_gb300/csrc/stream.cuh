@@ -10,13 +10,44 @@
 
 namespace cuba {
 
-// Cell coordinates: i_a = clamp(floor(x_a / dx_a), 0, n_a - 1).
+// Margin of the fast path of floor_quot: 2^-20 (FP32) and 2^-49 (FP64), four
+// times the largest distance between q and the rounded quotient.
+template <typename T> __device__ __forceinline__ T quot_margin();
+template <> __device__ __forceinline__ float quot_margin<float>() { return 0x1p-20f; }
+template <> __device__ __forceinline__ double quot_margin<double>() { return 0x1p-49; }
+
+// floor(RN(x / dx)), the floor of the correctly rounded quotient, without a
+// division in all but rare cases.  q = RN(x rdx) with rdx = RN(1 / dx) carries
+// two roundings of relative size 2^-24 (FP32; 2^-53 in FP64) and RN(x / dx)
+// one, so |q - RN(x / dx)| < 2^-22 |q| (2^-51 |q|).  When the fraction
+// f = q - floor(q) (exact: Sterbenz) keeps m = max(|q|, 1) 2^-20 (2^-49) from
+// both 0 and 1, RN(x / dx) lies strictly between the same two integers as q
+// and floor(q) is the answer; otherwise (x within a few ulps of a cell face)
+// the quotient is rounded correctly and floored.
+template <typename T>
+__device__ __forceinline__ T floor_quot(T x, T dx, T rdx)
+{
+    const T q = mul_rn(x, rdx);
+    const T k = floor_t(q);
+    const T f = sub_rn(q, k);
+    const T aq = q < T(0) ? -q : q;
+    const T m = mul_rn(aq > T(1) ? aq : T(1), quot_margin<T>());
+    if (f >= m && f <= sub_rn(T(1), m)) return k;
+    return floor_t(div_rn(x, dx));
+}
+
+// Cell coordinates: i_a = clamp(floor(x_a / dx_a), 0, n_a - 1) with the
+// quotient rounded correctly (floor_quot); an axis with one cell needs none.
 template <typename T>
 __device__ __forceinline__ void cell_coords(const SimDesc& S, const T pos[3], uint32_t id[3])
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const T c = floor_t(div_rn(pos[a], sim_dx<T>(S, a)));
+        if (S.n[a] == 1) {
+            id[a] = 0;
+            continue;
+        }
+        const T c = floor_quot(pos[a], sim_dx<T>(S, a), sim_rdx<T>(S, a));
         uint32_t ic;
         if (c < T(0)) ic = 0;
         else if (c >= (T)S.n[a]) ic = (uint32_t)(S.n[a] - 1);

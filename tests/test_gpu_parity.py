@@ -425,3 +425,41 @@ def test_small_cells_with_many_accepted_pairs_hand_over():
     # about 29 particles per cell, C = 0.15: about 60 accepted pairs per cell
     na, ne = _one_step_compare(L, (8, 8, 8), 0.09, 1.0 / 3.0 * 1e-3, 0.2, False, 13, st0, small_max=64)
     assert na > 32 * 512 * 0.5
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("L,cells", [((10.0, 1.0, 1.0), (2000, 1, 1)), ((1.3, 0.7, 2.9), (7, 5, 3)),
+                                     ((12.8, 12.8, 12.8), (128, 128, 128))])
+def test_cell_keys_on_and_next_to_every_face(fp32, L, cells):
+    """Positions exactly on each cell face and one ulp either side (the cases
+    where the quotient x / dx sits on an integer or rounds onto one): the
+    library's keys equal the oracle's correctly rounded floor(x / dx)."""
+    dtype = np.float32 if fp32 else np.float64
+    rng = np.random.default_rng(5)
+    cols = []
+    for a in range(3):
+        dx = dtype(L[a] / cells[a]) if fp32 else L[a] / cells[a]
+        faces = np.arange(cells[a] + 1, dtype=dtype) * dtype(dx)
+        faces = np.minimum(faces, dtype(L[a]))
+        near = np.concatenate([faces, np.nextafter(faces, dtype(np.inf)), np.nextafter(faces, dtype(0))])
+        near = near[(near >= 0) & (near <= dtype(L[a]))]
+        cols.append(near)
+    n = max(len(c) for c in cols) * 3
+    st = np.zeros((6, n), dtype=dtype)
+    for a in range(3):
+        c = cols[a]
+        st[a] = np.concatenate([c] * (n // len(c) + 1))[:n]
+        st[a] = st[a][rng.permutation(n)]
+        st[3 + a] = rng.normal(size=n).astype(dtype)
+    p, op = _pair(L, cells, 0.5 * min(L[a] / cells[a] for a in range(3)), 0.0, 1.0, fp32, 0)
+    sim = cuba.Sim(p, n)
+    try:
+        cuba.cuba_trace_enable(sim.h, True)
+        sim.set_state(st)
+        keys, perm, cs, _, _ = sim.trace()
+    finally:
+        sim.close()
+    _, okeys, operm, ocs = O.sort(op, st.astype(np.float64))
+    assert np.array_equal(keys, okeys)
+    assert np.array_equal(perm.astype(np.int64), operm)
+    assert np.array_equal(cs.astype(np.int64), ocs)
