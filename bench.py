@@ -803,6 +803,15 @@ def extras(args):
     return out
 
 
+def default_workload(args):
+    """Whether args name the headline workload (the extras run beside it
+    only, so that a run of another workload, e.g. under a profiler, times
+    that workload alone)."""
+    d = parse([])
+    keys = ("workload", "n", "cells", "dt", "sigma_mb", "precision", "acceptance", "mass", "mu", "kappa", "seed")
+    return all(getattr(args, k) == getattr(d, k) for k in keys)
+
+
 def _sub(line, desc):
     keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "clocks",
             "gpu_launches", "roofline", "hbm_phases", "phase_ms_per_step", "pair_tests_per_step",
@@ -839,7 +848,7 @@ def main(argv=None):
         return run_serve_mode(args)
     world, rank, local = dist_setup(args)
     line = run_step(args, world, rank)
-    if line is not None and world == 1 and args.extras:
+    if line is not None and world == 1 and args.extras and default_workload(args):
         line["extras"] = extras(args)
     if line is not None:
         print(json.dumps(line), flush=True)
