@@ -221,19 +221,23 @@ def neighbour_sort(n, cfg):
     return cells > 2048 and n <= 64 * cells and edges_ok
 
 
-def launches_per_step(ncells, small_max, skip=False, adaptive=False, neighbour=False):
+def launches_per_step(ncells, small_max, skip=False, adaptive=False, neighbour=False, split_stream=False):
     """Kernels of one step: the stream/sort kernels — radix: streaming
-    histogram; per radix pass the digit histogram (passes after the first), 3
-    scan kernels and the ranking kernel, then (two passes or more) the gather;
+    histogram (FP64 with fewer 4096-particle tiles than SMs: a streaming
+    kernel first, split_stream); per radix pass the digit histogram (passes
+    after the first), 3 scan kernels and the ranking kernel, then (two passes
+    or more) the gather;
     neighbour-move sort: count pass, offsets, 3 scan kernels, scatter pass —;
-    cell preparation + 3 scan kernels; small-cell and tiled pair kernels and
-    the survivor kernel (skip-ahead: 3 scan kernels of its row blocks and its
-    pair kernel); small-cell and per-cell resolve kernels; the step counter."""
+    cell preparation + its scan (one kernel up to 4095 cells, else 3);
+    small-cell and tiled pair kernels and the survivor kernel (skip-ahead: the
+    scan of its row blocks and its pair kernel); small-cell and per-cell
+    resolve kernels; the step counter."""
     p = bin_passes(ncells)
-    sort = 6 if neighbour else 1 + 4 * p + (p - 1) + (1 if p > 1 else 0)
+    scan = 1 if ncells + 1 <= 4096 else 3   # one-block scan of up to two 2048-entry tiles
+    sort = 3 + scan if neighbour else 1 + 4 * p + (p - 1) + (1 if p > 1 else 0) + (1 if split_stream else 0)
     small = 1 if small_max else 0
-    pairs = 3 + 1 if skip else 1 + small + 1
-    return (1 if adaptive else 0) + sort + 4 + pairs + (1 + small) + 1
+    pairs = scan + 1 if skip else 1 + small + 1
+    return (1 if adaptive else 0) + sort + 1 + scan + pairs + (1 + small) + 1
 
 
 def peaks():
@@ -746,7 +750,8 @@ def run_step(args, world, rank):
             "clocks": clk,
             "gpu_launches": launches_per_step(cfg["n_cells"][0] * cfg["n_cells"][1] * cfg["n_cells"][2],
                                               cuba.cuba_get_small_max(sim.h), args.acceptance == "skip",
-                                              args.kappa > 0, neighbour_sort(args.n, cfg)) * args.steps,
+                                              args.kappa > 0, neighbour_sort(args.n, cfg),
+                                              prec == cuba.CUBA_FP64 and (args.n + 4095) // 4096 < n_sm) * args.steps,
             "roofline": roofline,
             "hbm_phases": hbm,
             "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in zip(phase_names, phase)},

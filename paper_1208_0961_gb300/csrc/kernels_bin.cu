@@ -129,6 +129,40 @@ __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __r
     store_tile_hist(h, hist);
 }
 
+// Streaming and the cell key, one particle per thread, the streamed state
+// written back in place: used in FP64 when the arena has fewer 4096-particle
+// tiles than SMs, where the histogram kernel's 16 particles per thread would
+// run their FP64 divisions and square roots one after another on a few SMs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_inplace(const SimDesc* __restrict__ sims, int nsims,
+                                                        T* __restrict__ st, uint32_t pcap, uint32_t n,
+                                                        uint32_t* __restrict__ keys_out,
+                                                        unsigned long long* __restrict__ stats)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t cur_slot = 0xFFFFFFFFu, nref = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SimDesc& S = sims[sim_of_particle(sims, nsims, i)];
+        T pos[3], mom[3];
+        load_particle<T>(st, pcap, i, pos, mom);
+        const int nr = stream_one<T>(S, pos, mom);
+        store_particle<T>(st, pcap, i, pos, mom);
+        keys_out[i] = S.cell_off + cell_key<T>(S, pos);
+        if (nr) {
+            if (S.stat_slot != cur_slot) {
+                if (nref) atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)nref);
+                nref = 0;
+                cur_slot = S.stat_slot;
+            }
+            nref += (uint32_t)nr;
+        }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, cur_slot);
+    const unsigned sum = __reduce_add_sync(peers, nref);
+    if (lane == __ffs(peers) - 1 && cur_slot != 0xFFFFFFFFu && sum)
+        atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)sum);
+}
+
 // Histogram of a later digit.
 __global__ void __launch_bounds__(kSortThreads) k_bin_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
                                                            uint32_t* __restrict__ hist)
@@ -489,7 +523,14 @@ static int step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
     uint32_t* hist = A.radix_hist;
     uint32_t* off = A.radix_hist + (size_t)kBinBins * ntiles;
     const bool fp64 = A.precision == 1;
-    if (fp64)
+    if (fp64 && kStream && ntiles < (uint32_t)sm_count()) {
+        // few tiles: stream and key one particle per thread first (FP64
+        // writes the streamed state back in place in either case), then the
+        // digit histogram of the keys
+        k_stream_inplace<double><<<(n + 255) / 256, 256, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, n,
+                                                                  A.key[0], A.stats);
+        k_bin_hist<<<ntiles, kSortThreads, 0, st>>>(A.key[0], n, 0, hist);
+    } else if (fp64)
         k_stream_hist<double, kStream><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, n,
                                                                A.key[0], 0, hist, A.stats);
     else

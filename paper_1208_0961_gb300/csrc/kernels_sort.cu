@@ -247,11 +247,19 @@ struct U32Add {
     __host__ __device__ uint32_t operator()(uint32_t a, uint32_t b) const { return a + b; }
 };
 
+constexpr size_t kScanOneBlockTiles = 2;
+
 template <typename V, typename Op>
 static int exclusive_scan(V* data, size_t n, V zero, Op op, void* tmp, size_t tmp_bytes, cudaStream_t st)
 {
     if (n == 0) return 0;
     const size_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb <= kScanOneBlockTiles) {
+        // short arrays: one block scans them tile by tile (one launch instead
+        // of three)
+        k_scan_partials<V, Op><<<1, kScanThreads, 0, st>>>(data, n, zero, op);
+        return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+    }
     if (nb * sizeof(V) > tmp_bytes) return -1;
     V* partial = reinterpret_cast<V*>(tmp);
     k_scan_reduce<V, Op><<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, partial, zero, op);

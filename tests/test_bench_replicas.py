@@ -80,9 +80,12 @@ def test_launch_count():
     # one 11-bit pass up to 2048 cells, two up to 2^22
     assert bench.bin_passes(1) == 1 and bench.bin_passes(2000) == 1 and bench.bin_passes(2048) == 1
     assert bench.bin_passes(2049) == 2 and bench.bin_passes(128 ** 3) == 2 and bench.bin_passes(1 << 23) == 3
-    # counted against the ncu launch lists of one step: 13 (16 M, 2000 cells,
-    # no small-cell kernels) and 21 (64 M, 128^3 cells, small-cell kernels)
-    assert bench.launches_per_step(2000, 0) == 13
+    # counted against the ncu launch lists of one step: 11 (16 M, 2000 cells,
+    # no small-cell kernels; the cell table's scan is one kernel up to 4095
+    # cells), 14 (20 k FP64 particles in 100 cells: a streaming kernel before
+    # the histogram) and 21 (64 M, 128^3 cells, small-cell kernels)
+    assert bench.launches_per_step(2000, 0) == 11
+    assert bench.launches_per_step(100, 32, split_stream=True) == 14
     assert bench.launches_per_step(128 ** 3, 64) == 21
     # the neighbour-move sort of the 64 M hot spot: 16 per step
     assert bench.launches_per_step(128 ** 3, 256, neighbour=True) == 16
@@ -90,5 +93,5 @@ def test_launch_count():
     assert bench.neighbour_sort(64_000_000, hs) and not bench.neighbour_sort(300_000_000, hs)
     rm = {"n_cells": (2000, 1, 1), "L": (10.0, 1.0, 1.0), "dt": 0.0025}
     assert not bench.neighbour_sort(16_000_000, rm)
-    # skip-ahead (15 per step of the 16 M workload in its ncu launch list)
-    assert bench.launches_per_step(2000, 0, skip=True) == 15
+    # skip-ahead: 11 per step of the 16 M workload (both scans one kernel)
+    assert bench.launches_per_step(2000, 0, skip=True) == 11
