@@ -78,7 +78,7 @@ __device__ __forceinline__ void store_tile_hist(const uint32_t* h, uint32_t* __r
 
 // Pass 0: stream, key, digit histogram of the tile.  The particles of a warp
 // are taken four rounds at a time so that their loads overlap.
-template <typename T, bool kStream>
+template <typename T, bool kStream, bool kOne>
 __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __restrict__ sims, int nsims,
                                                               T* __restrict__ st, uint32_t pcap, uint32_t n,
                                                               uint32_t* __restrict__ keys_out, int shift,
@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __r
         const bool ok = i < n;
         uint32_t d = 0xFFFFFFFFu;
         if (ok) {
-            const int s = sim_of_particle(sims, nsims, i);
-            const SimDesc& S = sims[s];
+            const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, i)];
             T pos[3], mom[3];
             load_particle<T>(st, pcap, i, pos, mom);
             const int nr = kStream ? stream_one<T>(S, pos, mom) : 0;
@@ -392,7 +391,7 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
 // registers of a second particle would spill under the 64-register budget).
 template <typename T> struct FinalGroup { static constexpr int value = sizeof(T) == 8 ? 1 : 2; };
 
-template <typename T, bool kStream>
+template <typename T, bool kStream, bool kOne>
 __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
     k_bin_final(const SimDesc* __restrict__ sims, int nsims, const uint32_t* __restrict__ key_in,
                 const T* __restrict__ st_old, T* __restrict__ st_new, uint32_t pcap, uint32_t n,
@@ -427,7 +426,8 @@ __global__ void __launch_bounds__(kSortThreads, CUBA_BIN_MIN_BLOCKS)
         for (int g = 0; g < kG; ++g) {
             const uint32_t i = base + (r0 + g) * 32 + lane;
             if (i < n) {
-                if (kStream && !StreamInPlace<T>::value) stream_one<T>(sims[sim_of_particle(sims, nsims, i)], x[g], m[g]);
+                if (kStream && !StreamInPlace<T>::value)
+                    stream_one<T>(sims[kOne ? 0 : sim_of_particle(sims, nsims, i)], x[g], m[g]);
                 store_particle<T>(st_new, pcap, k[r0 + g], x[g], m[g]);
                 if (perm) perm[k[r0 + g]] = i;
             }
@@ -465,23 +465,45 @@ __global__ void __launch_bounds__(256) k_bin_gather(const SimDesc* __restrict__ 
 // ---------------------------------------------------------------------------
 static const size_t kBinSmem = sizeof(RankSmem);
 
+template <typename T, bool kStream, bool kOne>
+static int final_attr()
+{
+    return cudaFuncSetAttribute(k_bin_final<T, kStream, kOne>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kBinSmem) == cudaSuccess ? 0 : -1;
+}
+
 int bin_kernels_init()
 {
     if (cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) != cudaSuccess)
         return -1;
-    if (cudaFuncSetAttribute(k_bin_final<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
-        cudaSuccess)
-        return -1;
-    if (cudaFuncSetAttribute(k_bin_final<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
-        cudaSuccess)
-        return -1;
-    if (cudaFuncSetAttribute(k_bin_final<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
-        cudaSuccess)
-        return -1;
-    if (cudaFuncSetAttribute(k_bin_final<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinSmem) !=
-        cudaSuccess)
-        return -1;
-    return 0;
+    int rc = final_attr<float, true, true>() | final_attr<float, true, false>() | final_attr<float, false, true>() |
+             final_attr<float, false, false>() | final_attr<double, true, true>() | final_attr<double, true, false>() |
+             final_attr<double, false, true>() | final_attr<double, false, false>();
+    return rc ? -1 : 0;
+}
+
+// The stream/key and ranking kernels of one step, one simulation (kOne: its
+// descriptor read once, outside the particle loops) or several.
+template <typename T, bool kStream>
+static void stream_hist(const Arena& A, uint32_t ntiles, uint32_t* hist, cudaStream_t st)
+{
+    if (A.nsims == 1)
+        k_stream_hist<T, kStream, true><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (T*)A.st[A.cur], A.pcap,
+                                                                         A.np, A.key[0], 0, hist, A.stats);
+    else
+        k_stream_hist<T, kStream, false><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (T*)A.st[A.cur], A.pcap,
+                                                                          A.np, A.key[0], 0, hist, A.stats);
+}
+
+template <typename T, bool kStream>
+static void bin_final(const Arena& A, uint32_t ntiles, const uint32_t* off, uint32_t* perm, cudaStream_t st)
+{
+    if (A.nsims == 1)
+        k_bin_final<T, kStream, true><<<ntiles, kSortThreads, kBinSmem, st>>>(
+            A.d_sims, A.nsims, A.key[0], (const T*)A.st[A.cur], (T*)A.st[A.cur ^ 1], A.pcap, A.np, off, perm);
+    else
+        k_bin_final<T, kStream, false><<<ntiles, kSortThreads, kBinSmem, st>>>(
+            A.d_sims, A.nsims, A.key[0], (const T*)A.st[A.cur], (T*)A.st[A.cur ^ 1], A.pcap, A.np, off, perm);
 }
 
 // scan_tmp layout of the histogram scan: csum, coff (kBinChunks rows each), dtot
@@ -530,27 +552,20 @@ static int step_bin(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
         k_stream_inplace<double><<<(n + 255) / 256, 256, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, n,
                                                                   A.key[0], A.stats);
         k_bin_hist<<<ntiles, kSortThreads, 0, st>>>(A.key[0], n, 0, hist);
-    } else if (fp64)
-        k_stream_hist<double, kStream><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (double*)A.st[A.cur], A.pcap, n,
-                                                               A.key[0], 0, hist, A.stats);
-    else
-        k_stream_hist<float, kStream><<<ntiles, kSortThreads, 0, st>>>(A.d_sims, A.nsims, (float*)A.st[A.cur], A.pcap, n,
-                                                              A.key[0], 0, hist, A.stats);
+    } else if (fp64) {
+        stream_hist<double, kStream>(A, ntiles, hist, st);
+    } else {
+        stream_hist<float, kStream>(A, ntiles, hist, st);
+    }
     if (after_stream) cudaEventRecord(after_stream, st);
     if (A.trace) cudaMemcpyAsync(A.trace_keys, A.key[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
     if (passes == 1) {
         if (col_scan(A, hist, off, ntiles, A.cell_start, st)) return -1;
         uint32_t* perm = A.trace ? A.idx[1] : nullptr;
         if (fp64)
-            k_bin_final<double, kStream><<<ntiles, kSortThreads, kBinSmem, st>>>(A.d_sims, A.nsims, A.key[0],
-                                                                        (const double*)A.st[A.cur],
-                                                                        (double*)A.st[A.cur ^ 1], A.pcap, n,
-                                                                        off, perm);
+            bin_final<double, kStream>(A, ntiles, off, perm, st);
         else
-            k_bin_final<float, kStream><<<ntiles, kSortThreads, kBinSmem, st>>>(A.d_sims, A.nsims, A.key[0],
-                                                                       (const float*)A.st[A.cur],
-                                                                       (float*)A.st[A.cur ^ 1], A.pcap, n,
-                                                                       off, perm);
+            bin_final<float, kStream>(A, ntiles, off, perm, st);
         A.sorted_buf = 1;
     } else {
         int src = 0;

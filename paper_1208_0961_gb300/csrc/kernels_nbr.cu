@@ -75,7 +75,7 @@ __device__ __forceinline__ bool nbr_move(const SimDesc& S, T pos[3], T mom[3], u
 // += particles of old cell c moving in direction d (rel zeroed before), one
 // atomic per (cell, direction) group of a warp's 32 particles; trace keys;
 // reflections.
-template <typename T>
+template <typename T, bool kOne>
 __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __restrict__ sims, int nsims,
                                                            const T* __restrict__ st, uint32_t pcap, uint32_t n,
                                                            uint32_t* __restrict__ rel, size_t rel_stride,
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __rest
         uint32_t key = 0xFFFFFFFFu, c = 0;
         int d = 0;
         if (i < n) {
-            const SimDesc& S = sims[sim_of_particle(sims, nsims, i)];
+            const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, i)];
             if (S.stat_slot != cur_slot) {
                 if (nref) atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)nref);
                 nref = 0;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __rest
 // direction.  Within a warp range the rank is carried from round to round for
 // the cell that spans them (run[d]); the part of the first cell that lies
 // before the range is streamed again and counted first.
-template <typename T>
+template <typename T, bool kOne>
 __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __restrict__ sims, int nsims,
                                                              const T* __restrict__ st_old, T* __restrict__ st_new,
                                                              uint32_t pcap, uint32_t n,
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
         uint32_t key = 0xFFFFFFFFu;
         int d = 0;
         if (j < base) {
-            const SimDesc& S = sims[sim_of_particle(sims, nsims, j)];
+            const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, j)];
             T pos[3], mom[3];
             nbr_load<T>(st_old, pcap, j, pos, mom);
             uint32_t c, kn, nr = 0;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
             dest[k] = 0;
             d[k] = 0;
             if (i < n) {
-                const SimDesc& S = sims[sim_of_particle(sims, nsims, i)];
+                const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, i)];
                 nbr_load<T>(st_old, pcap, i, pos[k], mom[k]);
                 uint32_t nr = 0;
                 if (nbr_move<T>(S, pos[k], mom[k], c[k], d[k], dest[k], nr))
@@ -269,6 +269,32 @@ bool nbr_path(const Arena& A)
            (uint64_t)A.np <= 64ull * A.ncells;
 }
 
+// The count and scatter passes for one simulation (kOne: its descriptor read
+// once, outside the particle loops) or several.
+template <typename T>
+static void nbr_count(const Arena& A, uint32_t ntiles, uint32_t* tk, cudaStream_t st)
+{
+    if (A.nsims == 1)
+        k_nbr_count<T, true><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.np,
+                                                             A.nbr_rel, A.nbr_cap, tk, A.counters, A.stats);
+    else
+        k_nbr_count<T, false><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.np,
+                                                              A.nbr_rel, A.nbr_cap, tk, A.counters, A.stats);
+}
+
+template <typename T>
+static void nbr_scatter(const Arena& A, uint32_t ntiles, uint32_t* perm, cudaStream_t st)
+{
+    if (A.nsims == 1)
+        k_nbr_scatter<T, true><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur],
+                                                               (T*)A.st[A.cur ^ 1], A.pcap, A.np, A.cell_start,
+                                                               A.nbr_rel, A.nbr_cap, A.nbr_cs, perm, A.counters);
+    else
+        k_nbr_scatter<T, false><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur],
+                                                                (T*)A.st[A.cur ^ 1], A.pcap, A.np, A.cell_start,
+                                                                A.nbr_rel, A.nbr_cap, A.nbr_cs, perm, A.counters);
+}
+
 int launch_step_nbr(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
 {
     const uint32_t n = A.np, nc = A.ncells;
@@ -279,11 +305,9 @@ int launch_step_nbr(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
     cudaMemsetAsync(A.nbr_rel, 0, (size_t)kNbrDirs * rs * sizeof(uint32_t), st);
     if (ntiles) {
         if (A.precision == 1)
-            k_nbr_count<double><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const double*)A.st[A.cur], A.pcap,
-                                                                n, A.nbr_rel, rs, tk, A.counters, A.stats);
+            nbr_count<double>(A, ntiles, tk, st);
         else
-            k_nbr_count<float><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const float*)A.st[A.cur], A.pcap,
-                                                               n, A.nbr_rel, rs, tk, A.counters, A.stats);
+            nbr_count<float>(A, ntiles, tk, st);
     }
     if (after_stream) cudaEventRecord(after_stream, st);
     const unsigned g2 = (unsigned)std::min<uint32_t>((nc + 256) / 256, (uint32_t)sm_count() * 16);
@@ -291,13 +315,9 @@ int launch_step_nbr(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
     if (scan_u32(A.nbr_cs, (size_t)nc + 1, A.scan_tmp, A.scan_tmp_bytes, st)) return -1;
     if (ntiles) {
         if (A.precision == 1)
-            k_nbr_scatter<double><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const double*)A.st[A.cur],
-                                                                  (double*)A.st[A.cur ^ 1], A.pcap, n, A.cell_start,
-                                                                  A.nbr_rel, rs, A.nbr_cs, perm, A.counters);
+            nbr_scatter<double>(A, ntiles, perm, st);
         else
-            k_nbr_scatter<float><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const float*)A.st[A.cur],
-                                                                 (float*)A.st[A.cur ^ 1], A.pcap, n, A.cell_start,
-                                                                 A.nbr_rel, rs, A.nbr_cs, perm, A.counters);
+            nbr_scatter<float>(A, ntiles, perm, st);
     }
     cudaMemcpyAsync(A.cell_start, A.nbr_cs, ((size_t)nc + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
     A.sorted_buf = 1;
