@@ -145,8 +145,6 @@ template <bool kOneKey, int NB>
 struct PairShape {
     static constexpr int min_blocks = kOneKey ? (NB >= 8 ? 2 : 1) : (NB >= 4 ? 2 : 3);  // resident blocks per SM
 };
-// Queued Philox blocks per warp for nb blocks per iteration.
-__host__ __device__ constexpr int queue_cap(int nb) { return 32 + 32 * nb; }
 
 // Resolve: per-cell accepted lists up to this size are sorted in shared memory.
 constexpr int kResolveThreads = 256;

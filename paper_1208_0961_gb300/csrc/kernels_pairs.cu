@@ -170,58 +170,6 @@ struct CellCtx {
     uint32_t slot;    // its counters row
 };
 
-// One entry of a warp's block queue: the Philox block, its row and group and
-// its cell (32 bytes, so an entry's address is one shift-add of its slot).
-struct __align__(16) QEntry {
-    uint4 r;
-    uint32_t i, g, c, pad;
-};
-
-// Push a block onto the warp's queue iff its test word x has a bit of
-// 0x80808080 set: one predicate feeds the ballot and the two predicated
-// shared-memory stores (kCell: the entry's cell too, for a queue that spans
-// cells).  qa is the shared address of the next free entry; returns it after
-// the warp's pushes.
-template <bool kCell>
-__device__ __forceinline__ uint32_t queue_push(uint32_t x, uint32_t lt, uint32_t qa, uint4 r, uint32_t i, uint32_t g,
-                                               uint32_t c)
-{
-    uint32_t qa_out;
-    if (kCell)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t.reg .b32 t, b, a;\n\t"
-            "and.b32 t, %1, 0x80808080;\n\t"
-            "setp.ne.u32 p, t, 0;\n\t"
-            "vote.sync.ballot.b32 b, p, 0xffffffff;\n\t"
-            "and.b32 t, b, %2;\n\t"
-            "popc.b32 t, t;\n\t"
-            "mad.lo.u32 a, t, 32, %3;\n\t"
-            "@p st.shared.v4.u32 [a], {%4, %5, %6, %7};\n\t"
-            "@p st.shared.v4.u32 [a+16], {%8, %9, %10, %10};\n\t"
-            "popc.b32 t, b;\n\t"
-            "mad.lo.u32 %0, t, 32, %3;\n\t}"
-            : "=r"(qa_out)
-            : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g), "r"(c)
-            : "memory");
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t.reg .b32 t, b, a;\n\t"
-            "and.b32 t, %1, 0x80808080;\n\t"
-            "setp.ne.u32 p, t, 0;\n\t"
-            "vote.sync.ballot.b32 b, p, 0xffffffff;\n\t"
-            "and.b32 t, b, %2;\n\t"
-            "popc.b32 t, t;\n\t"
-            "mad.lo.u32 a, t, 32, %3;\n\t"
-            "@p st.shared.v4.u32 [a], {%4, %5, %6, %7};\n\t"
-            "@p st.shared.v2.u32 [a+16], {%8, %9};\n\t"
-            "popc.b32 t, b;\n\t"
-            "mad.lo.u32 %0, t, 32, %3;\n\t}"
-            : "=r"(qa_out)
-            : "r"(x), "r"(lt), "r"(qa), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(i), "r"(g)
-            : "memory");
-    return qa_out;
-}
-
 // Append accepted pair (i, j) to its cell's list; kMark: the cell's first
 // accepted pair enters it in the active-cell list.
 template <bool kMark>
@@ -525,110 +473,132 @@ __device__ __forceinline__ void pair_rows(const CellCtx& cc, uint32_t rb, uint32
                              svn, acc_count, acc, acc_cap, counters, active, stats);
 }
 
-// The warp-per-cell path keeps its block queue across cells: queued blocks
-// are resolved 32 at a time, each lane rebuilding its entry's cell context
-// (simulation, cell bounds, list segment), instead of a mostly idle resolve
-// at the end of every small cell.
-template <typename T, bool kOneKey>
-__device__ __forceinline__ void resolve_entries(const QEntry* q, uint32_t e0, uint32_t e1,
-                                                const SimDesc* __restrict__ sims, int nsims,
-                                                const T* __restrict__ st, uint32_t pcap,
-                                                const uint32_t* __restrict__ cell_start,
-                                                const uint2* __restrict__ work, uint4* sv, uint32_t* svn,
-                                                uint32_t* __restrict__ acc_count,
-                                                unsigned long long* __restrict__ acc, uint64_t acc_cap,
-                                                uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
-                                                unsigned long long* __restrict__ stats, const PhiloxKey& Kp)
+// Per-lane rings of the small-cell kernel: entry k of lane L holds the block
+// at r[k][0][L] and its tag (row i, cell, (n << 8) | group, simulation) at
+// r[k][1][L].  Same entry layout as PairRing, so a push is two predicated
+// shared stores and one address increment.
+constexpr int kSmallRingDepth = 7;
+struct __align__(16) SmallRing {
+    uint4 r[kSmallRingDepth][2][32];
+};
+
+__device__ __forceinline__ void small_ring_push(uint32_t x, uint32_t& ra, uint4 r, uint4 tag)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t e = e0 + lane; e < e1; e += 32) {
-        const uint4 r = q[e].r;
-        const uint32_t i = q[e].i, g = q[e].g, c = q[e].c;
-        const int s = sim_of_cell(sims, nsims, c);
-        const SimDesc& S = sims[s];
-        const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
-        const PhiloxKey& K = kOneKey ? Kp : Kl;
-        const uint32_t lc = c - S.cell_off;
-        const uint4 mb = philox4x32_10(make_uint4(S.step, lc, i, kTagMid | g), K);
-        if (!prefix16_any(r, mb, S.thr16)) continue;
-        const uint32_t cbase = cell_start[c];
-        const uint32_t n = cell_start[c + 1] - cbase;
-        uint32_t m = block_le_mask(r, S.thr8) & valid_cols(g, i, n);
-        while (m) {
-            const uint32_t bit = (uint32_t)__ffs(m) - 1u;
-            m &= m - 1u;
-            const uint32_t r16 = (block_byte(r, bit) << 8) | block_byte(mb, bit);
-            if (r16 > S.thr16) continue;
-            const uint32_t j = 16u * g + bit;
-            const uint32_t pos = atomicAdd(svn, 1u);
-            if (pos < kSurvBuf) {
-                sv[pos] = make_uint4(c, i, j, r16);
-            } else {
-                CellCtx cc;
-                cc.c = c;
-                cc.s = s;
-                cc.slot = S.stat_slot;
-                cc.lc = lc;
-                cc.cbase = cbase;
-                cc.n = n;
-                const uint2 w0 = work[c], w1 = work[c + 1];
-                cc.list0 = w0.y;
-                cc.room = w1.y - w0.y;
-                eval_survivor<T, false>(cc, K, S.step, sim_C<T>(S), sim_m2<T>(S), st, pcap, i, j, r16, acc_count, acc,
-                                        acc_cap, counters, active, stats);
-            }
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+        "and.b32 t, %1, 0x80808080;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "@p st.shared.v4.u32 [%0], {%2, %3, %4, %5};\n\t"
+        "@p st.shared.v4.u32 [%0+%10], {%6, %7, %8, %9};\n\t"
+        "@p add.u32 %0, %0, %11;\n\t}"
+        : "+r"(ra)
+        : "r"(x), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(tag.x), "r"(tag.y), "r"(tag.z), "r"(tag.w),
+          "n"(kRingZOff), "n"(kRingRowBytes)
+        : "memory");
+}
+
+// Step, cell offset and thresholds of a one-simulation arena, kernel-wide.
+struct OneSim {
+    uint32_t step, cell_off, thr8, thr16;
+};
+
+// Resolve one ringed block of a small cell: the bytes <= thr8 at real pairs
+// j (i < j < n, n carried in the tag) are found first; only a block with one
+// draws its middle-byte block (step, cell, i, TAG_MID | g), and the pairs
+// whose 16-bit prefix is <= thr16 become survivors (the warp's buffer, or
+// evaluated here when it is full).
+template <typename T, bool kOneKey>
+__device__ __forceinline__ void resolve_small(uint4 r, uint4 tag, const OneSim& one,
+                                              const SimDesc* __restrict__ sims, const T* __restrict__ st,
+                                              uint32_t pcap, const uint32_t* __restrict__ cell_start,
+                                              const uint2* __restrict__ work, uint4* sv, uint32_t* svn,
+                                              uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
+                                              uint64_t acc_cap, uint32_t* __restrict__ counters,
+                                              uint32_t* __restrict__ active, unsigned long long* __restrict__ stats,
+                                              const PhiloxKey& Kp)
+{
+    const uint32_t i = tag.x, c = tag.y, g = tag.z & 0xFFu, n = tag.z >> 8;
+    uint32_t step = one.step, off_c = one.cell_off, thr8 = one.thr8, thr16 = one.thr16;
+    if (!kOneKey) {
+        const SimDesc& S = sims[tag.w];
+        step = S.step;
+        off_c = S.cell_off;
+        thr8 = S.thr8;
+        thr16 = S.thr16;
+    }
+    uint32_t m = block_le_mask(r, thr8) & valid_cols(g, i, n);
+    if (!m) return;
+    PhiloxKey Kl;
+    if (!kOneKey) Kl = philox_schedule(sims[tag.w].key0, sims[tag.w].key1);
+    const PhiloxKey& K = kOneKey ? Kp : Kl;
+    const uint4 mb = philox4x32_10(make_uint4(step, c - off_c, i, kTagMid | g), K);
+    while (m) {
+        const uint32_t bit = (uint32_t)__ffs(m) - 1u;
+        m &= m - 1u;
+        const uint32_t r16 = (block_byte(r, bit) << 8) | block_byte(mb, bit);
+        if (r16 > thr16) continue;
+        const uint32_t j = 16u * g + bit;
+        const uint32_t pos = atomicAdd(svn, 1u);
+        if (pos < kSurvBuf) {
+            sv[pos] = make_uint4(c, i, j, r16);
+        } else {
+            const int s = kOneKey ? 0 : (int)tag.w;
+            const SimDesc& S = sims[s];
+            CellCtx cc;
+            cc.c = c;
+            cc.s = s;
+            cc.slot = S.stat_slot;
+            cc.lc = c - off_c;
+            cc.cbase = cell_start[c];
+            cc.n = n;
+            const uint2 w0 = work[c], w1 = work[c + 1];
+            cc.list0 = w0.y;
+            cc.room = w1.y - w0.y;
+            eval_survivor<T, false>(cc, K, step, sim_C<T>(S), sim_m2<T>(S), st, pcap, i, j, r16, acc_count, acc,
+                                    acc_cap, counters, active, stats);
         }
     }
 }
 
-// All pairs of one small cell (n <= small_max) on the warp, pushing onto the
-// warp's persistent queue at shared address qa (returned); full queues are
-// drained with resolve_entries.
-template <typename T, bool kOneKey, int NB>
-__device__ __forceinline__ uint32_t pair_cell_small(uint32_t c, uint32_t lc, uint32_t n, uint32_t step, uint32_t thr8,
-                                                    const PhiloxKey& K, QEntry* q, uint32_t qa,
-                                                    const SimDesc* __restrict__ sims, int nsims,
-                                                    const T* __restrict__ st, uint32_t pcap,
-                                                    const uint32_t* __restrict__ cell_start,
-                                                    const uint2* __restrict__ work, uint4* sv, uint32_t* svn,
-                                                    uint32_t* __restrict__ acc_count,
-                                                    unsigned long long* __restrict__ acc, uint64_t acc_cap,
-                                                    uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
-                                                    unsigned long long* __restrict__ stats, const PhiloxKey& Kp)
+// Warp-collective: resolve the cnt entries of every lane's ring, one entry
+// per lane in compacted order (the owner of entry e found by a binary search
+// over the lanes' exclusive prefixes, as in drain_ring).
+template <typename T, bool kOneKey>
+__device__ __forceinline__ void drain_small(const SmallRing& ring, uint32_t cnt, const OneSim& one,
+                                            const SimDesc* __restrict__ sims, const T* __restrict__ st,
+                                            uint32_t pcap, const uint32_t* __restrict__ cell_start,
+                                            const uint2* __restrict__ work, uint4* sv, uint32_t* svn,
+                                            uint32_t* __restrict__ acc_count, unsigned long long* __restrict__ acc,
+                                            uint64_t acc_cap, uint32_t* __restrict__ counters,
+                                            uint32_t* __restrict__ active, unsigned long long* __restrict__ stats,
+                                            const PhiloxKey& Kp)
 {
-    constexpr int kQueueCap = queue_cap(NB);
     const uint32_t lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const uint32_t q_s = (uint32_t)__cvta_generic_to_shared(q);
-    const uint32_t qa_drain = q_s + 32u * (uint32_t)(kQueueCap - 32 * NB);
-    const uint32_t nrb = (n - 1 + kPairRows - 1) / kPairRows;
-    const uint32_t glast = (n - 1) >> 4;
-    for (uint32_t rb = 0; rb < nrb; ++rb) {
-        const uint32_t i = rb * kPairRows + lane;
-        const bool row_ok = i + 1 < n;
-        PhiloxRow R;
-        R.init(step, lc, i, K);
-        const uint32_t t8 = row_ok ? 0x01010101u * (thr8 + 1u) : 0u;
-        const uint32_t x0 = (row_ok && thr8 >= 128u) ? 0x80000000u : 0u;
-        for (uint32_t g = (rb * kPairRows + 1) >> 4; g <= glast; g += NB) {
-            while (qa > qa_drain) {
-                const uint32_t qn = (qa - q_s) >> 5;
-                __syncwarp();
-                resolve_entries<T, kOneKey>(q, qn - 32, qn, sims, nsims, st, pcap, cell_start, work, sv, svn,
-                                            acc_count, acc, acc_cap, counters, active, stats, Kp);
-                __syncwarp();
-                qa -= 32u * 32u;
-            }
+    uint32_t inc = cnt;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const uint4 r = R.block(g + b, K);
-                const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
-                                   ((r.w - t8) & ~r.w) | x0;
-                qa = queue_push<true>(x, lt, qa, r, i, g + b, c);
-            }
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += v;
+    }
+    const uint32_t pre = inc - cnt;
+    const uint32_t total = __shfl_sync(kFull, inc, 31);
+    __syncwarp();
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t e = base + lane;
+        uint32_t L = 0;
+#pragma unroll
+        for (uint32_t s = 16; s >= 1; s >>= 1) {
+            const uint32_t pc = __shfl_sync(kFull, pre, L + s);
+            if (pc <= e) L += s;
+        }
+        const uint32_t pL = __shfl_sync(kFull, pre, L);
+        if (e < total) {
+            const uint32_t k = e - pL;
+            resolve_small<T, kOneKey>(ring.r[k][0][L], ring.r[k][1][L], one, sims, st, pcap, cell_start, work, sv,
+                                      svn, acc_count, acc, acc_cap, counters, active, stats, Kp);
         }
     }
-    return qa;
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -852,11 +822,19 @@ __global__ void __launch_bounds__(kPairThreads, PairShape<kOneKey, NB>::min_bloc
                                 acc_count, acc, acc_cap, counters, active, stats, Kp);
 }
 
-// Small cells (2 <= n <= small_max): one warp per cell, all its rows, found
-// by a grid-stride scan over groups of 32 cells (no work queue, no per-cell
-// atomic); the particle counts of a group are read in one coalesced round,
-// one cell per lane, and handed to the cells' turns by shuffles.  The warp's
-// block queue spans cells (pair_cell_small, resolve_entries).
+// Small cells (2 <= n <= small_max): each warp takes 32 cells at a time
+// (grid-stride), one per lane.  Row i of a cell with G = (n - 1) >> 4 draws
+// the blocks of groups (i + 1) >> 4 .. G: rows of one band h = (i + 1) >> 4
+// draw m = G + 1 - h blocks each.  The warp walks m = 1, 2, ... and for each
+// m takes the band with m blocks per row of each of its cells as one flat
+// row list, 32 rows per round, one per lane: every lane draws exactly m
+// blocks in a round (no lane waits for a longer row) and builds its row's
+// Philox constants once for them.  Lane L's row is the (t + L)-th of the
+// list: its cell comes from the cells whose band starts inside the round
+// (one bit each, OR-reduced over the warp) and the rank of the cell holding
+// the row before the round.  Blocks with a byte <= thr8 go to the lane's ring
+// (dynamic shared memory, one SmallRing per warp), drained when some lane
+// could not take NB more entries.
 template <typename T, bool kOneKey, int NB>
 __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* __restrict__ sims, int nsims,
                                                              const T* __restrict__ st, uint32_t pcap,
@@ -871,45 +849,112 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pair_small(const SimDesc* _
                                                              const PhiloxKey Kp)
 {
     constexpr int kWarps = kPairThreads / 32;
-    __shared__ QEntry q_e[kWarps][queue_cap(NB)];
+    extern __shared__ __align__(16) unsigned char small_smem[];
     __shared__ uint4 s_v[kWarps][kSurvBuf];
+    __shared__ uint4 s_band[kWarps][32];  // (cell, first row in the list, first row i | n << 16, simulation)
     __shared__ uint32_t s_vn[kWarps], s_left[kWarps];
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) s_vn[w] = s_left[w] = 0;
+    const uint32_t lane = threadIdx.x & 31;
+    SmallRing& ring = reinterpret_cast<SmallRing*>(small_smem)[w];
+    if (lane == 0) s_vn[w] = s_left[w] = 0;
     __syncwarp();
     if ((uint64_t)work[ncells].y > acc_cap) return;  // reported by k_pair_tile
-    const uint32_t lane = threadIdx.x & 31;
+    // one simulation: its step, cell offset and thresholds are kernel-wide
+    const OneSim one{sims[0].step, sims[0].cell_off, sims[0].thr8, sims[0].thr16};
+    if (kOneKey && (!(sims[0].C > 0.0) || sims[0].skip)) return;  // skip-ahead cells: k_pair_skip
+    const uint32_t lt = (1u << lane) - 1u, le = lt | (1u << lane);
     const uint32_t nwarps = gridDim.x * kWarps;
-    const uint32_t q_s = (uint32_t)__cvta_generic_to_shared(q_e[w]);
-    uint32_t qa = q_s;  // the warp's queue, kept across cells
+    const uint32_t ra0 = (uint32_t)__cvta_generic_to_shared(&ring.r[0][0][lane]);
+    const uint32_t ra_lim = ra0 + (uint32_t)(kSmallRingDepth - NB) * kRingRowBytes;  // room for NB more
+    uint32_t ra = ra0;
     for (uint32_t c0 = (blockIdx.x * kWarps + w) * 32u; c0 < ncells; c0 += nwarps * 32u) {
         const uint32_t cl = c0 + lane;
         const uint32_t my_n = cl < ncells ? cell_start[cl + 1] - cell_start[cl] : 0u;
-        unsigned todo = __ballot_sync(kFull, cl < ncells && my_n >= 2 && my_n <= small_max);
-        while (todo) {
-            const int k = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t c = c0 + (uint32_t)k;
-            const uint32_t n = __shfl_sync(kFull, my_n, k);
-            const int s = sim_of_cell(sims, nsims, c);
-            const SimDesc& S = sims[s];
-            if (!(S.C > 0.0) || S.skip) continue;  // skip-ahead cells: k_pair_skip
-            const PhiloxKey Kl = kOneKey ? PhiloxKey{} : philox_schedule(S.key0, S.key1);
-            const PhiloxKey& K = kOneKey ? Kp : Kl;
-            qa = pair_cell_small<T, kOneKey, NB>(c, c - S.cell_off, n, S.step, S.thr8, K, q_e[w], qa, sims, nsims, st,
-                                                 pcap, cell_start, work, s_v[w], &s_vn[w], acc_count, acc, acc_cap,
-                                                 counters, active, stats, Kp);
-            __syncwarp();
-            if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
-                flush_survivors(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, counters);
+        bool ok = cl < ncells && my_n >= 2 && my_n <= small_max;
+        int s = 0;
+        if (!kOneKey && ok) {
+            s = sim_of_cell(sims, nsims, cl);
+            ok = sims[s].C > 0.0 && !sims[s].skip;
         }
-    }
-    if (qa != q_s) {
+        const uint32_t G = ok ? (my_n - 1u) >> 4 : 0u;
+        const uint32_t mmax = __reduce_max_sync(kFull, ok ? G + 1u : 0u);
+        for (uint32_t m = 1; m <= mmax; ++m) {
+            // this cell's band with m blocks per row: h = G + 1 - m, rows
+            // max(16 h - 1, 0) .. min(16 h + 14, n - 2)
+            const bool in = ok && m <= G + 1u;
+            const uint32_t h = G + 1u - m;
+            const uint32_t lo = h ? 16u * h - 1u : 0u;
+            const uint32_t hi = min(16u * h + 14u, my_n - 2u);
+            const uint32_t cnt = in ? hi - lo + 1u : 0u;
+            uint32_t E = cnt;  // inclusive prefix of the band sizes
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(kFull, E, d);
+                if (lane >= (uint32_t)d) E += v;
+            }
+            const uint32_t total = __shfl_sync(kFull, E, 31);
+            if (total == 0) continue;
+            const uint32_t first = E - cnt;
+            const unsigned has = __ballot_sync(kFull, cnt != 0);
+            __syncwarp();
+            if (cnt) s_band[w][__popc(has & lt)] = make_uint4(cl, first, lo | (my_n << 16), (uint32_t)s);
+            __syncwarp();
+            uint32_t rank_prev = ~0u;  // rank of the band holding the row before the round
+            for (uint32_t t = 0; t < total; t += 32u) {
+                const uint32_t off = first - t;  // wraps above 31 for bands starting before the round
+                const uint32_t M = __reduce_or_sync(kFull, (cnt != 0 && off < 32u) ? 1u << off : 0u);
+                // lanes past the list keep the last band's rank (no band starts there)
+                const uint32_t rank = min(rank_prev + (uint32_t)__popc(M & le), 31u);
+                rank_prev += (uint32_t)__popc(M);
+                const uint32_t k = t + lane;
+                const bool act = k < total;
+                const uint4 be = s_band[w][rank];
+                const uint32_t c = be.x;
+                const uint32_t i = (be.z & 0xFFFFu) + (k - be.y);
+                const uint32_t g0 = (i + 1u) >> 4;
+                uint32_t step = one.step, off_c = one.cell_off, thr8 = one.thr8;
+                PhiloxKey Kl;
+                if (!kOneKey) {
+                    const SimDesc& S = sims[be.w];
+                    step = S.step;
+                    off_c = S.cell_off;
+                    thr8 = S.thr8;
+                    Kl = philox_schedule(S.key0, S.key1);
+                }
+                const PhiloxKey& K = kOneKey ? Kp : Kl;
+                PhiloxRow R;
+                R.init(step, c - off_c, i, K);
+                const uint32_t t8 = act ? 0x01010101u * (thr8 + 1u) : 0u;
+                const uint32_t x0 = (act && thr8 >= 128u) ? 0x80000000u : 0u;
+                const uint32_t tag_n = (be.z >> 16) << 8;
+                for (uint32_t b = 0; b < m; b += NB) {
+                    if (__any_sync(kFull, ra > ra_lim)) {
+                        drain_small<T, kOneKey>(ring, (ra - ra0) / kRingRowBytes, one, sims, st, pcap, cell_start,
+                                                work, s_v[w], &s_vn[w], acc_count, acc, acc_cap, counters, active,
+                                                stats, Kp);
+                        ra = ra0;
+                        if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
+                            flush_survivors(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, counters);
+                    }
+#pragma unroll
+                    for (int bb = 0; bb < NB; ++bb) {
+                        if (bb > 0 && b + (uint32_t)bb >= m) break;  // warp-uniform
+                        const uint32_t g = g0 + b + (uint32_t)bb;
+                        const uint4 r = R.block(g, K);
+                        const uint32_t x = ((r.x - t8) & ~r.x) | ((r.y - t8) & ~r.y) | ((r.z - t8) & ~r.z) |
+                                           ((r.w - t8) & ~r.w) | x0;
+                        small_ring_push(x, ra, r, make_uint4(i, c, tag_n | g, be.w));
+                    }
+                }
+            }
+        }
         __syncwarp();
-        resolve_entries<T, kOneKey>(q_e[w], 0, (qa - q_s) >> 5, sims, nsims, st, pcap, cell_start, work, s_v[w],
-                                    &s_vn[w], acc_count, acc, acc_cap, counters, active, stats, Kp);
-        __syncwarp();
+        if (s_vn[w] - kSurvFlush < kSurvFull - kSurvFlush)
+            flush_survivors(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, counters);
     }
+    if (__any_sync(kFull, ra != ra0))
+        drain_small<T, kOneKey>(ring, (ra - ra0) / kRingRowBytes, one, sims, st, pcap, cell_start, work, s_v[w],
+                                &s_vn[w], acc_count, acc, acc_cap, counters, active, stats, Kp);
     drain_survivors<T, kOneKey>(s_v[w], &s_vn[w], &s_left[w], surv, surv_cap, sims, nsims, st, pcap, cell_start, work,
                                 acc_count, acc, acc_cap, counters, active, stats, Kp);
 }
@@ -1402,13 +1447,19 @@ static unsigned pair_grid()
     return g;
 }
 
+// dynamic shared memory of the small-cell kernel: one ring per warp
+constexpr size_t kSmallRingSmem = (kPairThreads / 32) * sizeof(SmallRing);
+
 template <typename T, bool kOneKey, int NB>
 static unsigned small_grid()
 {
     static unsigned g = 0;
     if (!g) {
+        cudaFuncSetAttribute(k_pair_small<T, kOneKey, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmallRingSmem);
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_small<T, kOneKey, NB>, kPairThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_small<T, kOneKey, NB>, kPairThreads,
+                                                      kSmallRingSmem);
         if (per < 1) per = 1;
         g = (unsigned)(per * sm_count());
     }
@@ -1431,7 +1482,7 @@ static unsigned skip_grid()
 template <typename T, bool kOneKey, int NB>
 static void launch_small(const Arena& A, cudaStream_t st)
 {
-    k_pair_small<T, kOneKey, NB><<<small_grid<T, kOneKey, NB>(), kPairThreads, 0, st>>>(
+    k_pair_small<T, kOneKey, NB><<<small_grid<T, kOneKey, NB>(), kPairThreads, kSmallRingSmem, st>>>(
         A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.cell_start, A.cell_work, A.ncells, A.small_max,
         A.acc_count, A.acc, A.acc_capacity, A.counters, A.active, A.stats, A.surv, A.surv_cap, A.key_sched);
 }
