@@ -7,19 +7,20 @@
 // cells around its old one: direction d = (dx+1) + 3 (dy+1) + 9 (dz+1), with
 // d_a the change of its cell coordinate along axis a.  The stable sort by
 // new cell then needs no radix passes:
-//   count:   every particle is streamed (A1, A2); its old cell is the key of
-//            its position before streaming, its direction that of its new
-//            cell (A3); rel[d][c] counts the particles of old cell c moving
-//            in direction d (one atomic per group of a warp's 32 particles);
+//   count:   every particle is streamed (A1, A2) and written back to its
+//            slot; its old cell is the key of its position before streaming,
+//            its direction that of its new cell (A3), kept as c << 5 | d;
+//            rel[d][c] counts the particles of old cell c moving in
+//            direction d (one atomic per group of a warp's 32 particles);
 //   offsets: one thread per new cell c visits its 27 possible source cells in
 //            increasing key order (decreasing d: the source is c - delta_d,
 //            delta_d = d_x + n_x (d_y + n_y d_z)), replacing each count by the
 //            number of earlier particles of c, and writes c's total;
 //   scan:    the totals give the new cell_start;
-//   scatter: every particle is streamed again (the same IEEE operations, so
-//            the same bits) and written into slot cell_start[c'] + rel[d][c]
-//            + (rank among its old cell's earlier particles of the same
-//            direction), the rank carried along each warp's 512 particles.
+//   scatter: every streamed particle is moved into slot cell_start[c'] +
+//            rel[d][c] + (rank among its old cell's earlier particles of the
+//            same direction), the rank carried along each warp's 512
+//            particles; the stream arithmetic runs once per step.
 // Within a new cell the particles come source cell by source cell in key
 // order and, inside a source cell, in their old order: the stable order.
 #include <cuda_runtime.h>
@@ -37,7 +38,7 @@ constexpr int kNbrDirs = 27;
 constexpr int kNbrThreads = 256;
 constexpr int kNbrWarps = kNbrThreads / 32;
 constexpr unsigned kNbrFull = 0xffffffffu;
-constexpr int kNbrGroup = 2;   // scatter rounds whose loads are issued together
+constexpr int kNbrGroup = 4;   // scatter rounds whose loads are issued together
 
 template <typename T>
 __device__ __forceinline__ void nbr_load(const T* __restrict__ st, uint32_t pcap, uint32_t g, T pos[3], T mom[3])
@@ -74,11 +75,14 @@ __device__ __forceinline__ bool nbr_move(const SimDesc& S, T pos[3], T mom[3], u
 // Count pass, 4096 particles per block (512 per warp, 32 at a time): rel[d][c]
 // += particles of old cell c moving in direction d (rel zeroed before), one
 // atomic per (cell, direction) group of a warp's 32 particles; trace keys;
-// reflections.
+// reflections.  The streamed particle goes back to its slot (positions, and
+// the momentum when it reflected) and keys[i] = c << 5 | d (all ones for a
+// move of more than one cell), so that the scatter pass only moves data.
 template <typename T, bool kOne>
 __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __restrict__ sims, int nsims,
-                                                           const T* __restrict__ st, uint32_t pcap, uint32_t n,
+                                                           T* __restrict__ st, uint32_t pcap, uint32_t n,
                                                            uint32_t* __restrict__ rel, size_t rel_stride,
+                                                           uint32_t* __restrict__ keys,
                                                            uint32_t* __restrict__ trace_keys,
                                                            uint32_t* __restrict__ counters,
                                                            unsigned long long* __restrict__ stats)
@@ -101,10 +105,18 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __rest
             T pos[3], mom[3];
             nbr_load<T>(st, pcap, i, pos, mom);
             uint32_t kn;
+            const uint32_t r0 = nref;
             if (nbr_move<T>(S, pos, mom, c, d, kn, nref))
                 key = (c << 5) | (uint32_t)d;
             else
                 atomicOr(&counters[1], kErrMove);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) st[(size_t)a * pcap + i] = pos[a];
+            if (nref != r0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) st[(size_t)(3 + a) * pcap + i] = mom[a];
+            }
+            keys[i] = key;
             if (trace_keys) trace_keys[i] = kn;
         }
         const unsigned peers = __match_any_sync(kNbrFull, key);
@@ -117,17 +129,19 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __rest
         atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)sum);
 }
 
-// Scatter pass over the same 512-particle warp ranges.  A particle's slot is
-// cell_start_new[new cell] + rel[d][old cell] (earlier source cells of the new
-// cell) + its rank among the earlier particles of its old cell with the same
-// direction.  Within a warp range the rank is carried from round to round for
-// the cell that spans them (run[d]); the part of the first cell that lies
-// before the range is streamed again and counted first.
+// Scatter pass over the same 512-particle warp ranges: moves the streamed
+// particles (the count pass wrote them back in place, with their keys
+// c << 5 | d).  A particle's slot is cell_start_new[new cell] + rel[d][old
+// cell] (earlier source cells of the new cell) + its rank among the earlier
+// particles of its old cell with the same direction.  Within a warp range the
+// rank is carried from round to round for the cell that spans them (run[d]);
+// the keys of the first cell's particles before the range are counted first.
 template <typename T, bool kOne>
 __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __restrict__ sims, int nsims,
                                                              const T* __restrict__ st_old, T* __restrict__ st_new,
-                                                             uint32_t pcap, uint32_t n,
+                                                             uint32_t pcap, uint32_t n, uint32_t ncells,
                                                              const uint32_t* __restrict__ cs_old,
+                                                             const uint32_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ rel, size_t rel_stride,
                                                              const uint32_t* __restrict__ cs_new,
                                                              uint32_t* __restrict__ perm,
@@ -139,30 +153,18 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
     const uint32_t base = blockIdx.x * kSortTile + w * (32 * kSortItems);
     if (base >= n) return;
     run[w][lane] = 0;
-    // the first cell of the range and its particles before the range
-    uint32_t carry;
-    {
-        const SimDesc& S = sims[sim_of_particle(sims, nsims, base)];
-        T pos[3], mom[3];
-        nbr_load<T>(st_old, pcap, base, pos, mom);
-        uint32_t io[3];
-        cell_coords<T>(S, pos, io);
-        carry = S.cell_off + io[0] + (uint32_t)S.n[0] * (io[1] + (uint32_t)S.n[1] * io[2]);
-    }
+    // one simulation: the key offsets of the 27 directions are kernel-wide
+    const int32_t nx1 = sims[0].n[0], nxy1 = sims[0].n[0] * sims[0].n[1];
+    // the first cell of the range (a move error leaves an all-ones key: the
+    // cell is clamped so that every read stays in bounds) and the ranks of
+    // its particles before the range
+    uint32_t carry = min(keys[base] >> 5, ncells - 1u);
     __syncwarp();
     for (uint32_t k = cs_old[carry]; k < base; k += 32) {
         const uint32_t j = k + lane;
-        uint32_t key = 0xFFFFFFFFu;
-        int d = 0;
-        if (j < base) {
-            const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, j)];
-            T pos[3], mom[3];
-            nbr_load<T>(st_old, pcap, j, pos, mom);
-            uint32_t c, kn, nr = 0;
-            if (nbr_move<T>(S, pos, mom, c, d, kn, nr)) key = (uint32_t)d;
-        }
+        const uint32_t key = j < base ? keys[j] : 0xFFFFFFFFu;
         const unsigned peers = __match_any_sync(kNbrFull, key);
-        if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1) run[w][d] += (uint32_t)__popc(peers);
+        if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1) run[w][key & 31u] += (uint32_t)__popc(peers);
         __syncwarp();
     }
     // rounds are taken kNbrGroup at a time: their loads and the gathers of
@@ -170,37 +172,39 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
     // round by round
     for (int r0 = 0; r0 < kSortItems; r0 += kNbrGroup) {
         if (base + r0 * 32 >= n) break;
-        uint32_t key[kNbrGroup], c[kNbrGroup], dest[kNbrGroup], sb[kNbrGroup];
-        int d[kNbrGroup];
+        uint32_t key[kNbrGroup], sb[kNbrGroup];
         T pos[kNbrGroup][3], mom[kNbrGroup][3];
 #pragma unroll
         for (int k = 0; k < kNbrGroup; ++k) {
             const uint32_t i = base + (r0 + k) * 32 + lane;
-            key[k] = 0xFFFFFFFFu;
-            c[k] = 0xFFFFFFFFu;
-            dest[k] = 0;
-            d[k] = 0;
-            if (i < n) {
-                const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, i)];
-                nbr_load<T>(st_old, pcap, i, pos[k], mom[k]);
-                uint32_t nr = 0;
-                if (nbr_move<T>(S, pos[k], mom[k], c[k], d[k], dest[k], nr))
-                    key[k] = (c[k] << 5) | (uint32_t)d[k];
-                else
-                    atomicOr(&counters[1], kErrMove);
-            }
+            key[k] = i < n ? keys[i] : 0xFFFFFFFFu;
+            if (key[k] != 0xFFFFFFFFu) nbr_load<T>(st_old, pcap, i, pos[k], mom[k]);
         }
 #pragma unroll
-        for (int k = 0; k < kNbrGroup; ++k)
-            sb[k] = key[k] != 0xFFFFFFFFu ? cs_new[dest[k]] + rel[(size_t)d[k] * rel_stride + c[k]] : 0u;
+        for (int k = 0; k < kNbrGroup; ++k) {
+            sb[k] = 0;
+            if (key[k] != 0xFFFFFFFFu) {
+                const uint32_t c = key[k] >> 5, d = key[k] & 31u;
+                int32_t nx = nx1, nxy = nxy1;
+                if (!kOne) {
+                    const SimDesc& S = sims[sim_of_cell(sims, nsims, c)];
+                    nx = S.n[0];
+                    nxy = S.n[0] * S.n[1];
+                }
+                const int32_t dx = (int32_t)(d % 3u) - 1, dy = (int32_t)((d / 3u) % 3u) - 1, dz = (int32_t)(d / 9u) - 1;
+                const uint32_t dest = c + (uint32_t)(dx + nx * dy + nxy * dz);
+                sb[k] = cs_new[dest] + rel[(size_t)d * rel_stride + c];
+            }
+        }
 #pragma unroll
         for (int k = 0; k < kNbrGroup; ++k) {
             const uint32_t r_lo = base + (r0 + k) * 32;
             if (r_lo >= n) break;
             const uint32_t i = r_lo + lane;
+            const uint32_t c = key[k] == 0xFFFFFFFFu ? 0xFFFFFFFFu : key[k] >> 5, d = key[k] & 31u;
             const unsigned peers = __match_any_sync(kNbrFull, key[k]);
             if (key[k] != 0xFFFFFFFFu) {
-                const uint32_t slot = sb[k] + (c[k] == carry ? run[w][d[k]] : 0u) + (uint32_t)__popc(peers & lt);
+                const uint32_t slot = sb[k] + (c == carry ? run[w][d] : 0u) + (uint32_t)__popc(peers & lt);
                 if (slot < n) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
@@ -214,15 +218,15 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
             }
             // the cell of the round's last particle carries into the next round
             const uint32_t last_lane = min(31u, n - 1 - r_lo);
-            const uint32_t last = __shfl_sync(kNbrFull, c[k], (int)last_lane);
+            const uint32_t last = __shfl_sync(kNbrFull, c, (int)last_lane);
             __syncwarp();
             if (last != carry) {
                 run[w][lane] = 0;
                 carry = last;
             }
             __syncwarp();
-            if (key[k] != 0xFFFFFFFFu && c[k] == carry && lane == __ffs(peers) - 1)
-                run[w][d[k]] += (uint32_t)__popc(peers);
+            if (key[k] != 0xFFFFFFFFu && c == carry && lane == __ffs(peers) - 1)
+                run[w][d] += (uint32_t)__popc(peers);
             __syncwarp();
         }
     }
@@ -275,11 +279,12 @@ template <typename T>
 static void nbr_count(const Arena& A, uint32_t ntiles, uint32_t* tk, cudaStream_t st)
 {
     if (A.nsims == 1)
-        k_nbr_count<T, true><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.np,
-                                                             A.nbr_rel, A.nbr_cap, tk, A.counters, A.stats);
+        k_nbr_count<T, true><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (T*)A.st[A.cur], A.pcap, A.np,
+                                                             A.nbr_rel, A.nbr_cap, A.key[0], tk, A.counters, A.stats);
     else
-        k_nbr_count<T, false><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur], A.pcap, A.np,
-                                                              A.nbr_rel, A.nbr_cap, tk, A.counters, A.stats);
+        k_nbr_count<T, false><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (T*)A.st[A.cur], A.pcap, A.np,
+                                                              A.nbr_rel, A.nbr_cap, A.key[0], tk, A.counters,
+                                                              A.stats);
 }
 
 template <typename T>
@@ -287,12 +292,14 @@ static void nbr_scatter(const Arena& A, uint32_t ntiles, uint32_t* perm, cudaStr
 {
     if (A.nsims == 1)
         k_nbr_scatter<T, true><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur],
-                                                               (T*)A.st[A.cur ^ 1], A.pcap, A.np, A.cell_start,
-                                                               A.nbr_rel, A.nbr_cap, A.nbr_cs, perm, A.counters);
+                                                               (T*)A.st[A.cur ^ 1], A.pcap, A.np, A.ncells,
+                                                               A.cell_start, A.key[0], A.nbr_rel, A.nbr_cap,
+                                                               A.nbr_cs, perm, A.counters);
     else
         k_nbr_scatter<T, false><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur],
-                                                                (T*)A.st[A.cur ^ 1], A.pcap, A.np, A.cell_start,
-                                                                A.nbr_rel, A.nbr_cap, A.nbr_cs, perm, A.counters);
+                                                                (T*)A.st[A.cur ^ 1], A.pcap, A.np, A.ncells,
+                                                                A.cell_start, A.key[0], A.nbr_rel, A.nbr_cap,
+                                                                A.nbr_cs, perm, A.counters);
 }
 
 int launch_step_nbr(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
