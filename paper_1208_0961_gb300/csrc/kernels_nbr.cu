@@ -54,16 +54,15 @@ __device__ __forceinline__ void nbr_load(const T* __restrict__ st, uint32_t pcap
 // position before streaming (the key the last sort used), the direction from
 // the cell coordinates after streaming.  Returns false if it moved more than
 // one cell along an axis.
+// The same with the old cell's coordinates io given.
 template <typename T>
-__device__ __forceinline__ bool nbr_move(const SimDesc& S, T pos[3], T mom[3], uint32_t& c_old, int& d,
-                                         uint32_t& key_new, uint32_t& nref)
+__device__ __forceinline__ bool nbr_move_from(const SimDesc& S, const uint32_t io[3], T pos[3], T mom[3], int& d,
+                                              uint32_t& key_new, uint32_t& nref)
 {
-    uint32_t io[3], in[3];
-    cell_coords<T>(S, pos, io);
+    uint32_t in[3];
     nref += (uint32_t)stream_one<T>(S, pos, mom);
     cell_coords<T>(S, pos, in);
     const uint32_t n0 = (uint32_t)S.n[0], n1 = (uint32_t)S.n[1];
-    c_old = S.cell_off + io[0] + n0 * (io[1] + n1 * io[2]);
     key_new = S.cell_off + in[0] + n0 * (in[1] + n1 * in[2]);
     const int32_t m0 = (int32_t)in[0] - (int32_t)io[0], m1 = (int32_t)in[1] - (int32_t)io[1],
                   m2 = (int32_t)in[2] - (int32_t)io[2];
@@ -72,15 +71,32 @@ __device__ __forceinline__ bool nbr_move(const SimDesc& S, T pos[3], T mom[3], u
     return true;
 }
 
+template <typename T>
+__device__ __forceinline__ bool nbr_move(const SimDesc& S, T pos[3], T mom[3], uint32_t& c_old, int& d,
+                                         uint32_t& key_new, uint32_t& nref)
+{
+    uint32_t io[3];
+    cell_coords<T>(S, pos, io);
+    c_old = S.cell_off + io[0] + (uint32_t)S.n[0] * (io[1] + (uint32_t)S.n[1] * io[2]);
+    return nbr_move_from<T>(S, io, pos, mom, d, key_new, nref);
+}
+
 // Count pass, 4096 particles per block (512 per warp, 32 at a time): rel[d][c]
 // += particles of old cell c moving in direction d (rel zeroed before), one
 // atomic per (cell, direction) group of a warp's 32 particles; trace keys;
 // reflections.  The streamed particle goes back to its slot (positions, and
 // the momentum when it reflected) and keys[i] = c << 5 | d (all ones for a
 // move of more than one cell), so that the scatter pass only moves data.
+// One simulation (kOne): the old cell of particle i is read off cell_start
+// (the state is sorted by cell): the range's first particle's cell from its
+// position, then each lane walks the cell boundaries up to its particle,
+// carrying the cell's coordinates, instead of dividing three coordinates.
+template <typename T> struct NbrCountBlocks { static constexpr int value = sizeof(T) == 4 ? 5 : 3; };
+
 template <typename T, bool kOne>
-__global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __restrict__ sims, int nsims,
+__global__ void __launch_bounds__(kNbrThreads, NbrCountBlocks<T>::value) k_nbr_count(const SimDesc* __restrict__ sims, int nsims,
                                                            T* __restrict__ st, uint32_t pcap, uint32_t n,
+                                                           const uint32_t* __restrict__ cs,
                                                            uint32_t* __restrict__ rel, size_t rel_stride,
                                                            uint32_t* __restrict__ keys,
                                                            uint32_t* __restrict__ trace_keys,
@@ -90,11 +106,47 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __rest
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = blockIdx.x * kSortTile + w * (32 * kSortItems);
     uint32_t cur_slot = 0xFFFFFFFFu, nref = 0;
+    // kOne: cell (global key) of the last particle of the previous round and
+    // its coordinates
+    uint32_t cur = 0, cx = 0, cy = 0, cz = 0;
+    const uint32_t nx = (uint32_t)sims[0].n[0], ny = (uint32_t)sims[0].n[1];
+    if (kOne && base < n) {
+        T p0[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) p0[a] = st[(size_t)a * pcap + base];
+        uint32_t io[3];
+        cell_coords<T>(sims[0], p0, io);
+        cx = io[0];
+        cy = io[1];
+        cz = io[2];
+        cur = sims[0].cell_off + cx + nx * (cy + ny * cz);
+    }
 #pragma unroll 4
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t i = base + r * 32 + lane;
         uint32_t key = 0xFFFFFFFFu, c = 0;
         int d = 0;
+        uint32_t io[3] = {cx, cy, cz};
+        if (kOne) {
+            c = cur;
+            if (i < n)
+                while (cs[c + 1] <= i) {
+                    ++c;
+                    if (++io[0] == nx) {
+                        io[0] = 0;
+                        if (++io[1] == ny) {
+                            io[1] = 0;
+                            ++io[2];
+                        }
+                    }
+                }
+            const uint32_t r_lo = base + r * 32;
+            const int last = r_lo < n ? (int)min(31u, n - 1 - r_lo) : 0;
+            cur = __shfl_sync(kNbrFull, c, last);
+            cx = __shfl_sync(kNbrFull, io[0], last);
+            cy = __shfl_sync(kNbrFull, io[1], last);
+            cz = __shfl_sync(kNbrFull, io[2], last);
+        }
         if (i < n) {
             const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, i)];
             if (S.stat_slot != cur_slot) {
@@ -106,7 +158,7 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_count(const SimDesc* __rest
             nbr_load<T>(st, pcap, i, pos, mom);
             uint32_t kn;
             const uint32_t r0 = nref;
-            if (nbr_move<T>(S, pos, mom, c, d, kn, nref))
+            if (kOne ? nbr_move_from<T>(S, io, pos, mom, d, kn, nref) : nbr_move<T>(S, pos, mom, c, d, kn, nref))
                 key = (c << 5) | (uint32_t)d;
             else
                 atomicOr(&counters[1], kErrMove);
@@ -280,11 +332,12 @@ static void nbr_count(const Arena& A, uint32_t ntiles, uint32_t* tk, cudaStream_
 {
     if (A.nsims == 1)
         k_nbr_count<T, true><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (T*)A.st[A.cur], A.pcap, A.np,
-                                                             A.nbr_rel, A.nbr_cap, A.key[0], tk, A.counters, A.stats);
+                                                             A.cell_start, A.nbr_rel, A.nbr_cap, A.key[0], tk,
+                                                             A.counters, A.stats);
     else
         k_nbr_count<T, false><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (T*)A.st[A.cur], A.pcap, A.np,
-                                                              A.nbr_rel, A.nbr_cap, A.key[0], tk, A.counters,
-                                                              A.stats);
+                                                              A.cell_start, A.nbr_rel, A.nbr_cap, A.key[0], tk,
+                                                              A.counters, A.stats);
 }
 
 template <typename T>
