@@ -207,11 +207,18 @@ __device__ __forceinline__ void eval_survivor(const CellCtx& cc, const PhiloxKey
                                               uint32_t* __restrict__ counters, uint32_t* __restrict__ active,
                                               unsigned long long* __restrict__ stats)
 {
-    const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
-    const uint32_t rw = (r16 << 16) | (fine >> 16);
-    const T u = unit_u<T>(rw);
+    // u = unit_u(r16 << 16 | fine >> 16) lies between the values of the
+    // lowest and the highest 16 low bits (the conversion rounds monotonically
+    // and the scaling by 2^-32 is exact), so the low bits are drawn only when
+    // P22 falls between those two: the same decision as u < P22 in every case.
     const T P = pair_p22<T>(C, m2, st, pcap, cc.cbase + i, cc.cbase + j);
-    if (u < P) append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
+    if (!(P > unit_u<T>(r16 << 16))) return;
+    bool acc_it = unit_u<T>((r16 << 16) | 0xFFFFu) < P;
+    if (!acc_it) {
+        const uint32_t fine = philox4x32_10(make_uint4(step, cc.lc, i, kTagFine | j), K).x;
+        acc_it = unit_u<T>((r16 << 16) | (fine >> 16)) < P;
+    }
+    if (acc_it) append_accepted<kMark>(cc, i, j, acc_count, acc, acc_cap, counters, active, stats);
 }
 
 // A survivor record evaluated on its own (its cell's context reloaded).
