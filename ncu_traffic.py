@@ -69,8 +69,8 @@ def main():
     rec = {"k_pair_tile": {"dram_bytes_per_launch": nbytes, "launches": len(launches), "workload": workload,
                            "source_sha256": source_hash(),
                            "metrics": "dram__bytes_read.sum + dram__bytes_write.sum, one pass per launch",
-                           "command": " ".join(["ncu"] + cmd[1:10] + ["gpurun_out/ncu_traffic.csv", "python",
-                                                                      "bench.py"] + BENCH[2:])}}
+                           "command": " ".join(["ncu"] + cmd[1:9] + ["gpurun_out/ncu_traffic.csv", "python",
+                                                                     "bench.py"] + BENCH[2:])}}
     with open(OUT, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")
