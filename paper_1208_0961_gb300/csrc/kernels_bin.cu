@@ -92,13 +92,15 @@ __global__ void __launch_bounds__(kSortThreads) k_stream_hist(const SimDesc* __r
     const uint32_t base = blockIdx.x * kSortTile + w * (32 * kSortItems);
     uint32_t cur_slot = 0xFFFFFFFFu;
     uint32_t nref = 0;
+    SimDesc Sl;  // one simulation: the streaming's descriptor fields, read once
+    if (kOne) copy_stream_fields(Sl, sims[0]);
 #pragma unroll 4
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t i = base + r * 32 + lane;
         const bool ok = i < n;
         uint32_t d = 0xFFFFFFFFu;
         if (ok) {
-            const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, i)];
+            const SimDesc& S = kOne ? Sl : sims[sim_of_particle(sims, nsims, i)];
             T pos[3], mom[3];
             load_particle<T>(st, pcap, i, pos, mom);
             const int nr = kStream ? stream_one<T>(S, pos, mom) : 0;

@@ -106,6 +106,8 @@ __global__ void __launch_bounds__(kNbrThreads, NbrCountBlocks<T>::value) k_nbr_c
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = blockIdx.x * kSortTile + w * (32 * kSortItems);
     uint32_t cur_slot = 0xFFFFFFFFu, nref = 0;
+    SimDesc Sl;  // one simulation: the streaming's descriptor fields, read once
+    if (kOne) copy_stream_fields(Sl, sims[0]);
     // kOne: cell (global key) of the last particle of the previous round and
     // its coordinates
     uint32_t cur = 0, cx = 0, cy = 0, cz = 0;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kNbrThreads, NbrCountBlocks<T>::value) k_nbr_c
             cz = __shfl_sync(kNbrFull, io[2], last);
         }
         if (i < n) {
-            const SimDesc& S = sims[kOne ? 0 : sim_of_particle(sims, nsims, i)];
+            const SimDesc& S = kOne ? Sl : sims[sim_of_particle(sims, nsims, i)];
             if (S.stat_slot != cur_slot) {
                 if (nref) atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)nref);
                 nref = 0;

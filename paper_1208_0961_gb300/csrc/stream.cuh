@@ -101,4 +101,28 @@ __device__ __forceinline__ int stream_one(const SimDesc& S, T pos[3], T mom[3])
     return nref;
 }
 
+
+// The fields of a descriptor that the streaming and the cell key read, copied
+// into a local descriptor once per thread (one simulation), so that the
+// particle loops take them from registers.
+__device__ __forceinline__ void copy_stream_fields(SimDesc& d, const SimDesc& s)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d.L[a] = s.L[a];
+        d.Lf[a] = s.Lf[a];
+        d.dx[a] = s.dx[a];
+        d.dxf[a] = s.dxf[a];
+        d.rdx[a] = s.rdx[a];
+        d.rdxf[a] = s.rdxf[a];
+        d.n[a] = s.n[a];
+    }
+    d.cell_off = s.cell_off;
+    d.dt = s.dt;
+    d.dtf = s.dtf;
+    d.m2 = s.m2;
+    d.m2f = s.m2f;
+    d.stat_slot = s.stat_slot;
+}
+
 }  // namespace cuba
