@@ -74,7 +74,8 @@ __device__ __forceinline__ uint32_t cell_key(const SimDesc& S, const T pos[3])
 
 // Free streaming x <- x + (p/E) dt (Eq. 2, c = 1, E = sqrt(|p|^2 + m^2)) and elastic
 // reflection: beyond a wall the position is mirrored and that momentum
-// component flips.  Returns the number of reflections.
+// component flips (selected, not branched on: the same values without
+// divergence).  Returns the number of reflections.
 template <typename T>
 __device__ __forceinline__ int stream_one(const SimDesc& S, T pos[3], T mom[3])
 {
@@ -86,17 +87,12 @@ __device__ __forceinline__ int stream_one(const SimDesc& S, T pos[3], T mom[3])
     for (int a = 0; a < 3; ++a) {
         const T L = sim_L<T>(S, a);
         const T v = (E > T(0)) ? div_rn(mom[a], E) : T(0);
-        T x = add_rn(pos[a], mul_rn(v, dt));
-        if (x < T(0)) {
-            x = -x;
-            mom[a] = -mom[a];
-            ++nref;
-        } else if (x > L) {
-            x = sub_rn(add_rn(L, L), x);
-            mom[a] = -mom[a];
-            ++nref;
-        }
-        pos[a] = x;
+        const T x = add_rn(pos[a], mul_rn(v, dt));
+        const bool lo = x < T(0), out = lo || x > L;
+        const T xr = lo ? -x : sub_rn(add_rn(L, L), x);
+        pos[a] = out ? xr : x;
+        mom[a] = out ? -mom[a] : mom[a];
+        nref += out ? 1 : 0;
     }
     return nref;
 }
