@@ -302,7 +302,7 @@ class Server:
 
     def __init__(self, backend, quantum=256, clock: Callable[[], float] = time.perf_counter,
                  sleep: Callable[[float], None] = time.sleep, classify=None, round_s=0.01, budgets=None,
-                 max_resident=None, order=None, aging_s=2.0, budget_aging_s=0.2, budget_cap=2.0):
+                 max_resident=None, order=None, aging_s=2.0, budget_aging_s=0.2, budget_cap=4.0):
         self.backends = list(backend) if isinstance(backend, (list, tuple)) else [backend]
         nb = len(self.backends)
         self.classify = classify or (lambda r: 0)
@@ -315,10 +315,8 @@ class Server:
             self.order = ["fifo"]
         else:
             # device seconds per round: the small class's steps are short and
-            # its requests finish in a few rounds; the large class gets twice
-            # the medium class's share, since its requests' run times set the
-            # tail of the latency distribution
-            self.budgets = budgets or [round_s * f for f in ((0.2, 1.0, 2.0) if nb == 3 else [1.0] * nb)]
+            # its requests finish in a few rounds; medium and large share
+            self.budgets = budgets or [round_s * f for f in ((0.2, 1.0, 1.0) if nb == 3 else [1.0] * nb)]
             # the large class runs one simulation at a time and the medium
             # class a few: their batches stay small, so a step's time and the
             # cost of an admission (a sort of the class's arena) or a
