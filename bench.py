@@ -771,7 +771,8 @@ def extras(args):
     """The other workloads of the benchmark, each timed on its own with its
     own clock record: config1 (the paper-sized 1D Riemann run, FP64, with the
     oracle timed on the whole run), hotspot3d, the batched ensemble and the
-    served request stream (config rate, then a sustainable rate)."""
+    served request stream (config rate, then 85 % and 95 % of the rate the
+    server carried at it)."""
     import copy
     out = {}
     # config 1: 20 k particles, 100 cells, dt = 0.05, 100 steps, FP64
@@ -799,12 +800,13 @@ def extras(args):
     s5 = serve_result(a, args.serve_rate, args.serve_requests)
     out["serve"] = s5
     cap = s5["updates_per_s"]
-    sustain = min(args.serve_rate, args.serve_rate * 0.85 * cap / max(s5["offered_updates_per_s"], 1.0))
-    if sustain < args.serve_rate:
-        s_low = serve_result(a, round(sustain, 2), 200)
-        s_low["config"]["why"] = ("the config's rate offers more than the server carries: 85 % of the carried "
-                                  "rate, 200 requests")
-        out["serve_sustainable"] = s_low
+    for key, frac in (("serve_sustainable", 0.85), ("serve_near_capacity", 0.95)):
+        sustain = min(args.serve_rate, args.serve_rate * frac * cap / max(s5["offered_updates_per_s"], 1.0))
+        if sustain < args.serve_rate:
+            s_low = serve_result(a, round(sustain, 2), 200)
+            s_low["config"]["why"] = ("the config's rate offers more than the server carries: %d %% of the carried "
+                                      "rate, 200 requests" % round(100 * frac))
+            out[key] = s_low
     return out
 
 
