@@ -375,8 +375,20 @@ __global__ void k_iota(uint32_t* p, uint32_t n)
 // mu + 8 sqrt(mu) + 16 with mu = 2.0001 C n (n - 1) / 2: the accepted count is
 // dominated by a binomial with success probability max P22 <= 2 C, so the
 // room is exceeded with probability far below 1e-15 per cell and step.
-__device__ __forceinline__ uint32_t list_room(double C, uint32_t n)
+// The value is the FP64 evaluation's; an FP32 evaluation decides it first
+// (FP64 square roots are slow on this GPU): for n <= 4096, n (n - 1) / 2 is
+// exact in FP32 and the FP32 result r lies within 1e-6 r of the FP64 one, so
+// when no integer lies within 2^-16 r + 2^-10 of r both have the same
+// ceiling; otherwise, or for larger cells, FP64 decides.
+__device__ __forceinline__ uint32_t list_room(double C, float Cf, uint32_t n)
 {
+    if (n <= 4096u) {
+        const float mu = 2.0001f * Cf * (0.5f * (float)n * (float)(n - 1));
+        const float r = mu + 8.0f * sqrtf(mu) + 16.0f;
+        const float e = r * 0x1p-16f + 0x1p-10f;
+        const float lo = ceilf(r - e), hi = ceilf(r + e);
+        if (lo == hi && r < 1.0e9f) return (uint32_t)hi;
+    }
     const double mu = 2.0001 * C * (0.5 * (double)n * (double)(n - 1));
     const double room = ceil(mu + 8.0 * sqrt(mu) + 16.0);
     return room > 4.0e9 ? 0xFFFFFFFFu : (uint32_t)room;
@@ -411,7 +423,7 @@ __global__ void __launch_bounds__(256) k_cell_prep(const SimDesc* __restrict__ s
         if (n >= 2 && S.C > 0.0) {
             if (S.skip) skip_items = (n - 1 + kPairRows - 1) / kPairRows;
             else if (n > small_max) items = (n - 1 + kPairRows - 1) / kPairRows;
-            room = list_room(S.C, n);
+            room = list_room(S.C, S.Cf, n);
             if (count_pairs) {
                 if (S.stat_slot != cur_slot) {
                     if (tests) atomicAdd(&stats[cur_slot * kStatCount + kStatPairTests], tests);
