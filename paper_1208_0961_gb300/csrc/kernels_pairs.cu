@@ -1352,28 +1352,41 @@ __global__ void __launch_bounds__(256, 4) k_resolve_small(const SimDesc* __restr
         if (mine) {
             cur_slot = slot;
             // greedy in lexicographic order: repeatedly the smallest unvisited
-            // entry; the list is written back sorted, executed pairs flagged
+            // entry; the list is written back sorted, executed pairs flagged.
+            // The entries and the particles taken so far stay in registers
+            // (every index below is a compile-time constant): a visited entry
+            // becomes ~0, above every real (i << 32 | j).
             unsigned long long* gl = acc + list0;
             unsigned long long v[kLaneList];
-            for (uint32_t k = 0; k < m; ++k) v[k] = gl[k];
+#pragma unroll
+            for (uint32_t k = 0; k < kLaneList; ++k) v[k] = k < m ? gl[k] : ~0ull;
             uint32_t used[2 * kLaneList];
-            uint32_t nused = 0, done = 0;  // done: bit k = entry k visited
+#pragma unroll
+            for (uint32_t u = 0; u < 2 * kLaneList; ++u) used[u] = 0xFFFFFFFFu;
+            uint32_t nused = 0;
             for (uint32_t r = 0; r < m; ++r) {
-                unsigned long long best = ~0ull;
+                unsigned long long best = v[0];
                 uint32_t kb = 0;
-                for (uint32_t k = 0; k < m; ++k) {
-                    if (!((done >> k) & 1u) && v[k] < best) {
+#pragma unroll
+                for (uint32_t k = 1; k < kLaneList; ++k)
+                    if (v[k] < best) {
                         best = v[k];
                         kb = k;
                     }
-                }
-                done |= 1u << kb;
+#pragma unroll
+                for (uint32_t k = 0; k < kLaneList; ++k)
+                    if (k == kb) v[k] = ~0ull;
                 const uint32_t i = (uint32_t)(best >> 32), j = (uint32_t)best;
                 bool free_ij = true;
-                for (uint32_t u = 0; u < nused; ++u) free_ij &= (used[u] != i) & (used[u] != j);
+#pragma unroll
+                for (uint32_t u = 0; u < 2 * kLaneList; ++u) free_ij &= (used[u] != i) & (used[u] != j);
                 if (free_ij) {
-                    used[nused++] = i;
-                    used[nused++] = j;
+#pragma unroll
+                    for (uint32_t u = 0; u < 2 * kLaneList; ++u) {
+                        if (u == nused) used[u] = i;
+                        if (u == nused + 1) used[u] = j;
+                    }
+                    nused += 2;
                     best |= kExecFlag;
                     const uint32_t qs = atomicAdd(&qn[w], 1u);
                     q[w][qs] = make_uint4(c, i, j, cbase);
