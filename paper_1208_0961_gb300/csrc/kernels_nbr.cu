@@ -19,7 +19,7 @@
 //   scan:    the totals give the new cell_start;
 //   scatter: every streamed particle is moved into slot cell_start[c'] +
 //            rel[d][c] + (rank among its old cell's earlier particles of the
-//            same direction), the rank carried along each warp's 512
+//            same direction), the rank carried along each warp's 128
 //            particles; the stream arithmetic runs once per step.
 // Within a new cell the particles come source cell by source cell in key
 // order and, inside a source cell, in their old order: the stable order.
@@ -39,6 +39,12 @@ constexpr int kNbrThreads = 256;
 constexpr int kNbrWarps = kNbrThreads / 32;
 constexpr unsigned kNbrFull = 0xffffffffu;
 constexpr int kNbrGroup = 4;   // scatter rounds whose loads are issued together
+// The scatter's warps take 128 particles each (4 rounds of 32, all loaded
+// together): more, shorter ranges than the count pass's 512 keep more loads
+// in flight across the GPU (1.07 against 1.16 ms per step of the 64 M hot spot;
+// 2 or 8 rounds measured 1.09 and 1.08).
+constexpr int kScatRounds = 4;
+constexpr int kScatTile = kNbrThreads * kScatRounds;
 
 template <typename T>
 __device__ __forceinline__ void nbr_load(const T* __restrict__ st, uint32_t pcap, uint32_t g, T pos[3], T mom[3])
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kNbrThreads, NbrCountBlocks<T>::value) k_nbr_c
         atomicAdd(&stats[cur_slot * kStatCount + kStatReflections], (unsigned long long)sum);
 }
 
-// Scatter pass over the same 512-particle warp ranges: moves the streamed
+// Scatter pass over 128-particle warp ranges (kScatRounds): moves the streamed
 // particles (the count pass wrote them back in place, with their keys
 // c << 5 | d).  A particle's slot is cell_start_new[new cell] + rel[d][old
 // cell] (earlier source cells of the new cell) + its rank among the earlier
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
     __shared__ uint32_t run[kNbrWarps][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t base = blockIdx.x * kSortTile + w * (32 * kSortItems);
+    const uint32_t base = blockIdx.x * kScatTile + w * (32 * kScatRounds);
     if (base >= n) return;
     run[w][lane] = 0;
     // one simulation: the key offsets of the 27 directions are kernel-wide
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr_scatter(const SimDesc* __re
     // rounds are taken kNbrGroup at a time: their loads and the gathers of
     // their slot bases are issued together, the rank carry is then applied
     // round by round
-    for (int r0 = 0; r0 < kSortItems; r0 += kNbrGroup) {
+    for (int r0 = 0; r0 < kScatRounds; r0 += kNbrGroup) {
         if (base + r0 * 32 >= n) break;
         uint32_t key[kNbrGroup], sb[kNbrGroup];
         T pos[kNbrGroup][3], mom[kNbrGroup][3];
@@ -343,8 +349,9 @@ static void nbr_count(const Arena& A, uint32_t ntiles, uint32_t* tk, cudaStream_
 }
 
 template <typename T>
-static void nbr_scatter(const Arena& A, uint32_t ntiles, uint32_t* perm, cudaStream_t st)
+static void nbr_scatter(const Arena& A, uint32_t* perm, cudaStream_t st)
 {
+    const uint32_t ntiles = (A.np + kScatTile - 1) / kScatTile;
     if (A.nsims == 1)
         k_nbr_scatter<T, true><<<ntiles, kNbrThreads, 0, st>>>(A.d_sims, A.nsims, (const T*)A.st[A.cur],
                                                                (T*)A.st[A.cur ^ 1], A.pcap, A.np, A.ncells,
@@ -377,9 +384,9 @@ int launch_step_nbr(Arena& A, cudaStream_t st, cudaEvent_t after_stream)
     if (scan_u32(A.nbr_cs, (size_t)nc + 1, A.scan_tmp, A.scan_tmp_bytes, st)) return -1;
     if (ntiles) {
         if (A.precision == 1)
-            nbr_scatter<double>(A, ntiles, perm, st);
+            nbr_scatter<double>(A, perm, st);
         else
-            nbr_scatter<float>(A, ntiles, perm, st);
+            nbr_scatter<float>(A, perm, st);
     }
     cudaMemcpyAsync(A.cell_start, A.nbr_cs, ((size_t)nc + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
     A.sorted_buf = 1;
