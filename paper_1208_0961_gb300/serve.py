@@ -293,7 +293,10 @@ class Server:
     oldest resident, budget (1 + age / budget_aging_s), so that a class whose
     requests have waited long catches up -- (at most the smallest remaining
     step count, so a finished resident leaves at once), waits for it and
-    retires the finished residents.  Classes take turns instead of running concurrently because a
+    retires the finished residents.  While large requests wait for admission
+    and the queued work is small (no overload), the large class's budget is
+    doubled: its requests' waits set the tail of the latency distribution.
+    Classes take turns instead of running concurrently because a
     large simulation's pair kernel occupies every SM for its whole duration:
     a small request's kernels queued beside it would wait for it at every
     step.  With one large resident at a time the large requests run nearly
@@ -302,7 +305,8 @@ class Server:
 
     def __init__(self, backend, quantum=256, clock: Callable[[], float] = time.perf_counter,
                  sleep: Callable[[float], None] = time.sleep, classify=None, round_s=0.01, budgets=None,
-                 max_resident=None, order=None, aging_s=2.0, budget_aging_s=0.2, budget_cap=4.0):
+                 max_resident=None, order=None, aging_s=2.0, budget_aging_s=0.2, budget_cap=4.0,
+                 queue_boost=2.0, boost_backlog_s=2.0):
         self.backends = list(backend) if isinstance(backend, (list, tuple)) else [backend]
         nb = len(self.backends)
         self.classify = classify or (lambda r: 0)
@@ -326,12 +330,21 @@ class Server:
         self.aging_s = aging_s
         self.budget_aging_s = budget_aging_s
         self.budget_cap = budget_cap
+        # the largest class's budget is multiplied by queue_boost while requests
+        # of that class wait for admission and the estimated work queued in all
+        # classes is at most boost_backlog_s (not under overload, where it
+        # would starve the smaller classes)
+        self.queue_boost = queue_boost
+        self.boost_backlog_s = boost_backlog_s
+        self._boost = False
 
     def _steps(self, k, residents, now):
         reqs = [v[0] for v in residents.values()]
         be = self.backends[k]
         cost = be.step_time(reqs) if hasattr(be, "step_time") else STEP_FIXED_S + sum(step_cost(r) for r in reqs)
         budget = self.budgets[k]
+        if k == len(self.backends) - 1 and len(self.backends) > 1 and self._boost:
+            budget *= self.queue_boost
         if self.budget_aging_s:
             age = max(now - v[2] for v in residents.values())   # time since admission
             budget *= min(self.budget_cap, 1.0 + age / self.budget_aging_s)
@@ -382,6 +395,8 @@ class Server:
                     q.pop(i)
                 if not res:
                     continue
+                self._boost = bool(queues[nb - 1]) and \
+                    sum(work(r) for q_ in queues for r in q_) <= self.boost_backlog_s
                 ks = self._steps(k, res, now())
                 be.step(ks)
                 if hasattr(be, "sync"):

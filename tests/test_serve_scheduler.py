@@ -220,3 +220,37 @@ def test_served_beats_one_at_a_time_on_p50_and_p99():
         assert served["p50_s"] < 0.8 * alone["p50_s"]
         assert served["p99_s"] < alone["p99_s"]
         assert served["mean_s"] < 0.8 * alone["mean_s"]
+
+
+class StepLog(CostBackend):
+    """CostBackend that records the step count of every advance."""
+
+    def __init__(self, clock, **kw):
+        super().__init__(clock, **kw)
+        self.steps = []
+
+    def step(self, k):
+        self.steps.append(k)
+        super().step(k)
+
+
+def _large_pair(backlog_steps):
+    big = lambda rid, t, steps: S.Request(rid, t, "riemann", 4_000_000, (10.0, 1.0, 1.0), (2000, 1, 1), 0.002,  # noqa
+                                          1.0, 1e5, steps, [((0, 0, 0), (10, 1, 1), 0.4)], rid)
+    return [big(0, 0.0, 400), big(1, 0.0, backlog_steps)]
+
+
+def test_large_class_budget_doubles_while_large_requests_wait():
+    """The largest class's quanta double while a large request waits for
+    admission and the queued work is small, and not once the queued work
+    exceeds boost_backlog_s (overload)."""
+    out = {}
+    for boost, steps in ((1.0, 50), (2.0, 50), (2.0, 5000)):
+        clk = FakeClock()
+        bes = [StepLog(clk) for _ in range(3)]
+        reqs = _large_pair(steps)
+        assert S.work(reqs[1]) < 2.0 if steps == 50 else S.work(reqs[1]) > 2.0
+        S.Server(bes, clock=clk, sleep=clk.sleep, classify=S.cost_class, queue_boost=boost).run(reqs)
+        out[(boost, steps)] = bes[2].steps[0]   # the first resident's first quantum, request 1 queued
+    assert abs(out[(2.0, 50)] - 2 * out[(1.0, 50)]) <= 1   # quanta are rounded budgets / step cost
+    assert out[(2.0, 5000)] == out[(1.0, 50)]
