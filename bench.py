@@ -660,7 +660,7 @@ def run_step(args, world, rank):
     pair_ms = phase[3] / max(1, args.profile_steps)
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    # pair tile (the dominant kernel): the survey's FP32 view is the headline
+    # pair tile (the dominant kernel): the FP32 view is the headline
     # roofline -- 9 flops per pair test (dot product, P22, uniform conversion,
     # compare) against n_SM x 128 FP32 lanes x 2 x f_SM.  Beside it, the units
     # that bind this integer kernel: the 32x32->64 multiply pipe (one multiply

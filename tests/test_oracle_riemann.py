@@ -14,8 +14,8 @@ import physics as PH
 def test_ideal_solver_invariants():
     eL, eR = 16.204, 6.637
     e, v, vsh = PH.ideal_riemann(eL, eR)
-    # survey-independent invariants: jump conditions hold, plateau between the
-    # two states, shock faster than sound, slower than light
+    # invariants of the exact solution: jump conditions hold, plateau between
+    # the two states, shock faster than sound, slower than light
     T00, T0x, Txx = PH._fluid_T(e, v)
     assert abs(vsh * (T00 - eR) - T0x) < 1e-12 * eL
     assert abs(vsh * T0x - (Txx - eR / 3)) < 1e-9 * eL
